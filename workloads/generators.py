@@ -1,0 +1,242 @@
+"""Seeded instance generators (no PDBO arithmetic lives here).
+
+Every generator takes an integer ``seed`` and draws from numpy's PCG64 keyed by
+``(seed, tag)``, where the tag separates the kinds of instance, so the same seed gives the
+same instance on every machine.
+
+Instance recipes (the paper's Gset and CNF sets are not available, so these synthetic
+families stand in for its workloads, with the same sizes and weight alphabets):
+
+* dense QUBO: a symmetric integer matrix M with entries uniform in [lo, hi]; the diagonal
+  becomes the linear term (``c = diag M``) and ``Q = M - diag(M)``, so that
+  ``F(x) = x^T Q x + c^T x`` equals ``x^T M x`` on binary points.  Optional density masks
+  off-diagonal pairs symmetrically.
+* Max-Cut: an undirected weighted graph W (Erdos-Renyi, 2-D torus, or random d-regular
+  from the pairing model) written as the QUBO ``Q = W`` (stored in both directions) and
+  ``c = -W 1``, so that ``F(x) = -cut(x)`` (paper section 4.1 and the minimisation form in
+  section 4.4).
+* MIS: ``F(x) = -sum x_i + lambda * sum_{(i,j) in E} x_i x_j`` with lambda = 4 (paper,
+  appendix on MIS), i.e. ``Q_ij = Q_ji = lambda/2`` on edges and ``c = -1``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+_TAG_DENSE = 11
+_TAG_ER = 12
+_TAG_TORUS = 13
+_TAG_REGULAR = 14
+_TAG_HETERO = 15
+_TAG_MIS = 16
+
+
+def _rng(seed: int, tag: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64([int(seed) & (2**63 - 1), tag]))
+
+
+# ----------------------------------------------------------------------------------------
+# dense QUBO
+# ----------------------------------------------------------------------------------------
+def dense_qubo(n: int, seed: int = 0, lo: int = -100, hi: int = 100, density: float = 1.0,
+               rng: np.random.Generator | None = None):
+    """Return ``(Q, c)``: ``Q`` int32 n x n symmetric with zero diagonal, ``c`` int32 n.
+
+    ``M`` is symmetric with every upper-triangle entry (diagonal included) uniform in
+    ``[lo, hi]``; pairs ``i < j`` are kept with probability ``density``; ``c = diag(M)``.
+    """
+    if not (-128 <= lo <= hi <= 127):
+        raise ValueError("dense_qubo draws int8 entries; use lo, hi within [-128, 127]")
+    if rng is None:
+        rng = _rng(seed, _TAG_DENSE)
+    R = rng.integers(lo, hi + 1, size=(n, n), dtype=np.int8)
+    if density < 1.0:
+        keep = np.empty((n, n), dtype=bool)
+        blk = 2048
+        thr = np.uint32(min(int(density * 2**32), 2**32 - 1))
+        for r0 in range(0, n, blk):
+            r1 = min(n, r0 + blk)
+            keep[r0:r1] = rng.integers(0, 2**32, size=(r1 - r0, n), dtype=np.uint32) < thr
+        R[~keep] = 0
+        del keep
+    M = np.triu(R)
+    M += np.triu(R, 1).T          # disjoint supports: no int8 overflow
+    del R
+    c = np.diagonal(M).astype(np.int32).copy()
+    np.fill_diagonal(M, 0)
+    Q = M.astype(np.int32)
+    return Q, c
+
+
+def heterogeneous_qubos(count: int, seed: int = 0, n_lo: int = 500, n_hi: int = 20000,
+                        dens_lo: float = 0.01, dens_hi: float = 1.0, lo: int = -100, hi: int = 100):
+    """``count`` dense QUBOs with n ~ U{n_lo..n_hi} and density ~ U[dens_lo, dens_hi]."""
+    rng = _rng(seed, _TAG_HETERO)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        d = float(rng.uniform(dens_lo, dens_hi))
+        out.append(dense_qubo(n, lo=lo, hi=hi, density=d, rng=rng))
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# graphs (edge lists with i < j) and their CSR / QUBO forms
+# ----------------------------------------------------------------------------------------
+def _pm1(rng, m):
+    return np.where(rng.integers(0, 2, size=m) == 1, 1, -1).astype(np.int32)
+
+
+def maxcut_er(n: int, mean_degree: float = 6.0, seed: int = 0, weights: str = "pm1"):
+    """Erdos-Renyi G(n, p) with p = mean_degree/(n-1); weights +-1 (or 1). Returns (i, j, w)."""
+    rng = _rng(seed, _TAG_ER)
+    p = mean_degree / (n - 1)
+    iu, ju = np.triu_indices(n, 1)
+    keep = rng.random(iu.size) < p
+    i, j = iu[keep].astype(np.int32), ju[keep].astype(np.int32)
+    w = _pm1(rng, i.size) if weights == "pm1" else np.ones(i.size, np.int32)
+    return i, j, w
+
+
+def maxcut_torus(rows: int = 100, cols: int = 100, seed: int = 0, weights: str = "pm1"):
+    """Periodic rows x cols grid (4 neighbours per vertex, 2*rows*cols edges)."""
+    rng = _rng(seed, _TAG_TORUS)
+    v = np.arange(rows * cols, dtype=np.int64).reshape(rows, cols)
+    right = np.roll(v, -1, axis=1)
+    down = np.roll(v, -1, axis=0)
+    a = np.concatenate([v.ravel(), v.ravel()])
+    b = np.concatenate([right.ravel(), down.ravel()])
+    i = np.minimum(a, b).astype(np.int32)
+    j = np.maximum(a, b).astype(np.int32)
+    w = _pm1(rng, i.size) if weights == "pm1" else np.ones(i.size, np.int32)
+    return i, j, w
+
+
+def _regular_edges(n: int, d: int, rng: np.random.Generator, max_tries: int = 10000):
+    """Random simple d-regular graph: pairing model, rejecting loops and multi-edges."""
+    if (n * d) % 2:
+        raise ValueError("n*d must be even")
+    stubs = np.repeat(np.arange(n, dtype=np.int64), d)
+    for _ in range(max_tries):
+        perm = rng.permutation(stubs)
+        a, b = perm[0::2], perm[1::2]
+        if np.any(a == b):
+            continue
+        lo_, hi_ = np.minimum(a, b), np.maximum(a, b)
+        key = lo_ * n + hi_
+        if np.unique(key).size != key.size:
+            continue
+        order = np.argsort(key)
+        return lo_[order].astype(np.int32), hi_[order].astype(np.int32)
+    raise RuntimeError("pairing model did not produce a simple graph")
+
+
+def maxcut_regular(n: int = 20000, d: int = 4, seed: int = 0, weights: str = "unit"):
+    """Random d-regular graph (pairing model with rejection); unit weights by default."""
+    rng = _rng(seed, _TAG_REGULAR)
+    i, j = _regular_edges(n, d, rng)
+    w = _pm1(rng, i.size) if weights == "pm1" else np.ones(i.size, np.int32)
+    return i, j, w
+
+
+def csr_from_edges(n: int, i, j, w):
+    """Symmetric CSR (both directions, columns sorted within a row) of the edge list."""
+    rows = np.concatenate([i, j]).astype(np.int64)
+    cols = np.concatenate([j, i]).astype(np.int64)
+    vals = np.concatenate([w, w]).astype(np.int32)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr, cols.astype(np.int32), vals
+
+
+def maxcut_qubo(n: int, i, j, w):
+    """Max-Cut as QUBO: ``Q = W`` in CSR (both directions) and ``c = -W 1``."""
+    rowptr, col, val = csr_from_edges(n, i, j, w)
+    c = np.zeros(n, dtype=np.int64)
+    np.add.at(c, i, w)
+    np.add.at(c, j, w)
+    return rowptr, col, val, (-c).astype(np.int32)
+
+
+def mis_regular(n: int, d: int, seed: int = 0, lam: int = 4):
+    """MIS on a random d-regular graph as QUBO: CSR ``Q`` (lam/2 both ways) and ``c = -1``."""
+    if lam % 2:
+        raise ValueError("lam must be even so that Q stays integral")
+    rng = _rng(seed, _TAG_MIS)
+    i, j = _regular_edges(n, d, rng)
+    rowptr, col, val = csr_from_edges(n, i, j, np.full(i.size, lam // 2, np.int32))
+    return rowptr, col, val, -np.ones(n, dtype=np.int32), (i, j)
+
+
+def dense_from_csr(n: int, rowptr, col, val):
+    """Dense int32 copy of a CSR matrix (small n only)."""
+    Q = np.zeros((n, n), dtype=np.int32)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    np.add.at(Q, (rows, col), val)
+    return Q
+
+
+# ----------------------------------------------------------------------------------------
+# hyper-parameters
+# ----------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class GdaParams:
+    """Hyper-parameters of one batched PDBO run (names follow Algorithm 1 and App. C)."""
+    restarts: int          # B
+    iters: int             # T_max
+    alpha: float           # primal step
+    beta: float            # dual step
+    ybar: float            # y^0 = ybar * 1
+    delta: float = 0.01    # tolerance of the perturbation rule (value not given in the paper)
+    grad_tol: float = 0.02  # gradient threshold of the perturbation rule (2*delta in Alg. 1)
+    eval_every: int = 10   # K: rounding + exact objective every K iterations and at T
+    seed: int = 0
+
+    def asdict(self):
+        return dataclasses.asdict(self)
+
+
+def graph_params(kind: str = "maxcut", restarts: int = 100, iters: int = 1000,
+                 delta: float = 0.01, eval_every: int = 10, seed: int = 0) -> GdaParams:
+    """The paper's hyper-parameter table (App. C.1): Max-Cut ybar=6, alpha=beta=0.025;
+    MIS ybar=5, alpha=beta=0.02; the gradient threshold is 2*delta as in Algorithm 1."""
+    table = {"maxcut": (6.0, 0.025, 0.025), "mis": (5.0, 0.02, 0.02)}
+    ybar, a, b = table[kind]
+    return GdaParams(restarts=restarts, iters=iters, alpha=a, beta=b, ybar=ybar, delta=delta,
+                     grad_tol=2 * delta, eval_every=eval_every, seed=seed)
+
+
+def spectral_scale(Q) -> float:
+    """Semicircle estimate of |lambda_min| of the symmetric part of Q (zero diagonal):
+    2 * ||Q_sym||_F / sqrt(n), with Q_sym = (Q + Q^T)/2 off the diagonal."""
+    Q = np.asarray(Q)
+    n = Q.shape[0]
+    ss = 0.0
+    blk = 1024
+    for r0 in range(0, n, blk):
+        r1 = min(n, r0 + blk)
+        S = Q[r0:r1].astype(np.float64) + Q[:, r0:r1].T.astype(np.float64)
+        S[np.arange(r1 - r0), np.arange(r0, r1)] = 0.0
+        ss += float(np.sum(S * S)) * 0.25
+    return 2.0 * math.sqrt(ss) / math.sqrt(n)
+
+
+def dense_params(Q, restarts: int, iters: int, delta: float = 0.01, eval_every: int = 50,
+                 seed: int = 0, lam_hat: float | None = None) -> GdaParams:
+    """Hyper-parameters for dense integer QUBO, carried over from the paper's Max-Cut regime.
+
+    The paper tunes (ybar, alpha, beta) for graphs only.  The map
+    (A, c', ybar, alpha, beta, tol) -> (sA, sc', s ybar, alpha/s, s beta, s tol) leaves every
+    primal iterate unchanged, so with s = lam_hat/4 (lam_hat estimating |lambda_min|) the
+    Max-Cut values ybar=6, alpha=beta=0.025 keep ybar at 1.5x |lambda_min|, i.e. the convex
+    start of the landscape analysis (section 4.4)."""
+    lam = spectral_scale(Q) if lam_hat is None else lam_hat
+    s = lam / 4.0
+    return GdaParams(restarts=restarts, iters=iters, alpha=0.025 / s, beta=0.025 * s,
+                     ybar=6.0 * s, delta=delta, grad_tol=2 * delta * s, eval_every=eval_every,
+                     seed=seed)
