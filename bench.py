@@ -1,0 +1,341 @@
+"""Throughput of batched PDBO GDA on GB300: restart-iterations/s on dense QUBO n=20,000.
+
+Workload (the headline configuration): dense QUBO, n = 20,000, integer entries uniform in
+[-100, 100] (diagonal = linear term), seed 0; B = 1,024 restarts; BF16 tcgen05 contraction with
+FP32 accumulation and FP32 master iterates; evaluation (rounding + exact int64 objective +
+argmin) every K = 50 iterations.  One step = K GDA iterations + one evaluation.
+
+Reported (one JSON line on rank 0):
+  value       restart-iterations/s with the instance resident in HBM (device events)
+  e2e         the same metric through the public C ABI with host buffers: every step creates
+              the problem from pinned host Q, c (H2D), runs K iterations and reads the best
+              (x*, F*) back (D2H)
+  roofline    the tcgen05 update kernel: 2 n^2 B flop per launch / its average launch time
+              (CUDA events around each launch inside the timed region), against the measured
+              sustained BF16 peak
+  cpu_baseline the FP64 oracle on the host cores, on a bounded sample (restart subset)
+``--impl reference`` times the oracle alone (the reference arm of this comparison).
+Multi-GPU (torchrun): every rank runs its own B restarts (different seeds) of the same instance,
+no collective in the timed loop; value = all ranks' restart-iterations / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_VARS = 20000
+RESTARTS = 1024
+K_EVAL = 50
+METRIC = "GDA restart-iterations/s at n=20k dense QUBO"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------------------------------------
+def oracle_sample(Q, c, p, seconds: float, restarts: int = 16, A=None, cp=None):
+    """Time the FP64 oracle on `restarts` restarts of the workload for about `seconds`."""
+    import oracle as O
+    if A is None:
+        A, cp = O.canonicalize(Q, c)
+    X, _ = O.init_state(Q.shape[0], restarts, p.seed, p.ybar)
+    Y = np.full_like(X, p.ybar)
+    it = 0
+    t0 = time.perf_counter()
+    while True:
+        X, Y, _ = O.gda_step(A, cp, X, Y, p.alpha, p.beta, p.delta, p.grad_tol)
+        it += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and it >= 2:
+            break
+    return restarts * it / el, it, el, A, cp
+
+
+def oracle_threads():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    Q, c = W.dense_qubo(N_VARS, seed=0)
+    p = W.dense_params(Q, restarts=RESTARTS, iters=2000, eval_every=K_EVAL, seed=0)
+    import oracle as O
+    A, cp = O.canonicalize(Q, c)
+    sub = 16
+    X, _ = O.init_state(N_VARS, sub, p.seed, p.ybar)
+    Y = np.full_like(X, p.ybar)
+    for _ in range(args.warmup):
+        X, Y, _ = O.gda_step(A, cp, X, Y, p.alpha, p.beta, p.delta, p.grad_tol)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        X, Y, _ = O.gda_step(A, cp, X, Y, p.alpha, p.beta, p.delta, p.grad_tol)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sub * args.steps / total
+    cores = oracle_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "restart-iterations/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"dense QUBO n={N_VARS}, B={RESTARTS}, BF16 contraction (oracle: FP64)",
+                       "oracle_sample": f"{sub} of {RESTARTS} restarts, one GDA iteration per step"},
+            "cpu_baseline": {"value": value, "unit": "restart-iterations/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sub} restarts x 1 iteration per step, numpy FP64 matmul"},
+            "e2e": {"value": value, "unit": "restart-iterations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2509_21064_gb300 import sbo as S
+    from paper_2509_21064_gb300.build import build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build()
+    S.lib()
+    stream = torch.cuda.Stream(device=dev)
+
+    Q, c = W.dense_qubo(N_VARS, seed=0)
+    p = W.dense_params(Q, restarts=RESTARTS, iters=10**9, eval_every=K_EVAL, seed=rank)
+    prm = S.params(**p.asdict())
+    P = S.Problem.dense(Q, c, precision=S.SBO_BF16, stream=stream)
+    # direct launches, so that every update launch can be bracketed by events on its stream
+    P.set_option(S.SBO_OPT_USE_GRAPH, 0)
+    P.start(prm)
+    info = P.info()
+
+    def step(events=None):
+        for k in range(K_EVAL):
+            if events is not None and k < K_EVAL - 1:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                P.run(1)
+                e1.record(stream)
+                events.append((e0, e1))
+            else:
+                P.run(1)       # the K-th iteration also launches the evaluation kernels
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        sampler = ClockSampler(local)
+        sampler.start()
+        kernel_events = []
+        launches0 = P.launch_count()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            step(kernel_events)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+        launches = P.launch_count() - launches0
+        clocks = sampler.stop()
+        P.sync()
+    ms = t_start.elapsed_time(t_end)
+    upd_ms = [a.elapsed_time(b) for a, b in kernel_events]
+    t_kernel = statistics.mean(upd_ms) * 1e-3
+    # graph-replay form of the same steps (reported beside)
+    P.set_option(S.SBO_OPT_USE_GRAPH, 1)
+    P.start(prm)
+    with torch.cuda.stream(stream):
+        P.run(K_EVAL)
+        torch.cuda.synchronize(dev)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        P.run(K_EVAL * max(2, args.steps // 2))
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+    graph_ms_per_step = g0.elapsed_time(g1) / max(2, args.steps // 2)
+    x_best, F_best, t_best, r_best = P.best()
+    P.close()
+
+    # e2e through the public API with host buffers (pinned), every step: H2D of Q, c; K
+    # iterations + evaluation; D2H of (x*, F*)
+    Qp = torch.from_numpy(Q).pin_memory()
+    cpin = torch.from_numpy(c).pin_memory()
+    e2e_steps = max(2, min(args.steps, 4))
+    prm_e2e = S.params(**{**p.asdict(), "iters": K_EVAL})
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P2 = S.Problem.dense(Qp.numpy(), cpin.numpy(), precision=S.SBO_BF16, stream=stream)
+        P2.gda(prm_e2e)
+        xb, Fb, tb, rb = P2.best()
+        P2.close()
+    e2e_s = time.perf_counter() - t0
+    h2d = Q.nbytes + c.nbytes
+    d2h = N_VARS + 8 * 3
+
+    # max over ranks
+    sec = ms * 1e-3
+    if world > 1:
+        tt = torch.tensor([sec, e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        sec, e2e_s = float(tt[0]), float(tt[1])
+    total_ri = RESTARTS * K_EVAL * args.steps * world
+    value = total_ri / sec
+    e2e_value = RESTARTS * K_EVAL * e2e_steps * world / e2e_s
+
+    pk, src = peaks()
+    flops = 2.0 * N_VARS * N_VARS * RESTARTS
+    achieved = flops / t_kernel / 1e12
+    peak = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
+    line = {
+        "metric": METRIC, "value": value, "unit": "restart-iterations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"dense QUBO n={N_VARS}, entries U[-100,100], B={RESTARTS} restarts, "
+                               f"K={K_EVAL} iterations + 1 evaluation per step",
+                   "n": N_VARS, "restarts": RESTARTS, "eval_every": K_EVAL, "tile_n": info["tile_n"],
+                   "kernel": "tcgen05 BF16 (FP32 accumulate, FP32 master x, y)",
+                   "l2": "inputs larger than L2 (A is 800 MB BF16)",
+                   "graph_replay_ms_per_step": graph_ms_per_step,
+                   "best_F_after_run": F_best,
+                   "parallelism": f"replicas x{world} (restarts sharded by seed)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_tc<256, EPI_UPDATE>", "launch_ms": t_kernel * 1e3,
+                     "peak_source": f"{src} bf16_tflops_sustained"},
+        "e2e": {"value": e2e_value, "unit": "restart-iterations/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, it, el, _, _ = oracle_sample(Q, c, p, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "restart-iterations/s", "cores": oracle_threads(),
+                                "kind": "oracle",
+                                "sample": f"16 of {RESTARTS} restarts x {it} iterations ({el:.1f} s), numpy FP64"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * sbo.h -- C ABI of libsbo, a GB300 (sm_103a) implementation of the batched primal-dual
+ * gradient descent-ascent of PDBO ("Smoothing Binary Optimization: A Primal-Dual
+ * Perspective", arXiv 2509.21064).
+ *
+ * Problem (Eq. 1 with the QUBO objective):   min_{x in {0,1}^n}  F(x) = x^T Q x + c^T x.
+ * The library works on the multilinear form of F (Prop. 2.4):
+ *     f(x) = 1/2 x^T A x + c'^T x,   A_ij = Q_ij + Q_ji (i != j), A_ii = 0,   c' = c + diag(Q),
+ * and on the Lagrangian L(x, y) = f(x) + sum_i y_i g(x_i) with g(x) = x^2 - x (section 3.1,
+ * section 4.2).  One iteration of Algorithm 1 for every restart r and coordinate i:
+ *     d_i = (A x)_i + c'_i + y_i (2 x_i - 1)
+ *     if |x_i - 1/2| <= delta and |d_i| <= grad_tol and y_i <= 0:  x_i <- 1/2 -/+ delta
+ *     else                                                          x_i <- clip(x_i - alpha d_i, 0, 1)
+ *     y_i <- y_i + beta (x_i^2 - x_i)              (old x_i: simultaneous updates, Eq. 5)
+ * B restarts run together; every K iterations (and at T) each restart is rounded to
+ * b = [x > 1/2], F(b) is evaluated exactly in int64, and the best candidate is retained
+ * (section 4.2).  x^0 ~ Uniform([0,1]^n) and y^0 = ybar (App. C.1).
+ *
+ * Conventions for every call:
+ *   - Every call returns an sbo_status and never aborts, throws or exits; the message of the
+ *     last failure on the calling thread is available from sbo_last_error().
+ *   - Host input arrays are owned by the caller and are copied (or fully consumed) before the
+ *     call returns.  Host output arrays are allocated by the caller.  "_dev" arguments are
+ *     device pointers owned by the caller.
+ *   - A problem handle owns all device memory it allocates, until sbo_destroy.
+ *   - Work is enqueued on the stream given at creation (a cudaStream_t passed as void*;
+ *     NULL means the legacy default stream).  Calls that return results to the host
+ *     synchronise that stream first.
+ *   - Integer data: Q, c are int32.  The exactness rules below are checked at creation and
+ *     violations return SBO_ERANGE.
+ */
+#ifndef SBO_H_
+#define SBO_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sbo_status {
+  SBO_OK = 0,
+  SBO_EINVAL = 1,     /* invalid argument (null pointer, bad size, malformed CSR, bad parameter) */
+  SBO_ENOMEM = 2,     /* device or host allocation failed */
+  SBO_ECUDA = 3,      /* a CUDA runtime/driver call failed, or no usable device */
+  SBO_ETIMEOUT = 4,   /* a bounded device-side wait gave up; the kernel returned early */
+  SBO_ENOTREADY = 5,  /* results requested before any evaluation took place */
+  SBO_ERANGE = 6,     /* data not exactly representable at the requested precision */
+  SBO_EDEVICE = 7     /* the device reported an inconsistent state (bounds check failed) */
+} sbo_status;
+
+typedef enum sbo_precision {
+  SBO_FP32 = 0,       /* A stored FP32, x operand FP32, FP32 accumulation (CUDA cores) */
+  SBO_BF16 = 1,       /* A stored BF16 (|A_ij| <= 256), x operand BF16 (RN from the FP32
+                         master), FP32 accumulation; dense: tcgen05 tensor cores */
+  SBO_FP8_E4M3 = 2    /* sparse only: weights stored E4M3 (|A_ij| <= 16), x operand BF16,
+                         FP32 accumulation */
+} sbo_precision;
+
+typedef struct sbo_problem sbo_problem;  /* opaque, library-owned */
+
+/* Hyper-parameters of one batched run (Algorithm 1; App. C.1). */
+typedef struct sbo_gda_params {
+  int32_t restarts;    /* B >= 1 */
+  int32_t eval_every;  /* K >= 1: rounding + exact objective at t = K, 2K, ... and at t = iters */
+  int64_t iters;       /* T >= 0 */
+  double alpha;        /* primal step, > 0 */
+  double beta;         /* dual step, >= 0 */
+  double ybar;         /* y^0 = ybar * 1 */
+  double delta;        /* perturbation tolerance, 0 <= delta < 0.5 */
+  double grad_tol;     /* gradient threshold of the perturbation rule (Algorithm 1: 2*delta) */
+  uint64_t seed;       /* x^0_{r,i} = top 24 bits of SplitMix64 output r*2^32+i, times 2^-24 */
+} sbo_gda_params;
+
+/* ---- creation ------------------------------------------------------------------------
+ * sbo_create_dense: Q is n*n row-major int32 on the host; c is n int32 on the host or NULL
+ * (zero).  precision: SBO_FP32 or SBO_BF16.  Requires 1 <= n <= 65536, every
+ * |A_ij| <= 256 (BF16) or <= 2^24 (FP32), every row sum sum_j |A_ij| < 2^24 (exact FP32
+ * accumulation of A b for the objective), and |c'_i| < 2^31.  A is canonicalised on the
+ * device (Prop. 2.4).  stream: cudaStream_t or NULL.  On success *out receives the handle.
+ */
+sbo_status sbo_create_dense(int64_t n, const int32_t* Q, const int32_t* c, int32_t precision,
+                            void* stream, sbo_problem** out);
+
+/* sbo_create_csr: Q in CSR on the host: rowptr[n+1] (int64, rowptr[0]=0, non-decreasing,
+ * rowptr[n]=nnz), col[nnz] (int32 in [0,n)), val[nnz] (int32); duplicates are summed.
+ * c as above.  precision: SBO_FP32, SBO_BF16 or SBO_FP8_E4M3 (weight storage).  A = Q + Q^T
+ * with zero diagonal is formed on the host.  Requires 1 <= n < 2^31 and the exactness
+ * rules above (|A_ij| <= 16 for E4M3). */
+sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                          const int32_t* val, const int32_t* c, int32_t precision,
+                          void* stream, sbo_problem** out);
+
+/* ---- the batched GDA run ----------------------------------------------------------------
+ * sbo_gda_start: (re)initialises the run: allocates the state for B = prm->restarts,
+ * x^0 from x0 (host, B*n float32 row-major [r][i], values in [0,1]) or, when x0 is NULL,
+ * from the SplitMix64 rule of prm->seed; y^0 = ybar; clears every best.  Asynchronous.
+ * sbo_gda_run: enqueues `iters` more iterations (the iteration counter continues), with
+ * evaluations at t = K, 2K, ... and t = prm->iters.  Asynchronous.
+ * sbo_gda: start (x0 = NULL) + run(prm->iters) + synchronise.  A handle may run again:
+ * each start begins afresh. */
+sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float* x0);
+sbo_status sbo_gda_run(sbo_problem* p, int64_t iters);
+sbo_status sbo_gda(sbo_problem* p, const sbo_gda_params* prm);
+
+/* sbo_sync: waits for the problem's stream; returns SBO_ETIMEOUT / SBO_EDEVICE if a kernel
+ * raised the device error word since the last sync (the word is then cleared). */
+sbo_status sbo_sync(sbo_problem* p);
+
+/* ---- results (all synchronise first) ---------------------------------------------------
+ * sbo_eval: exact F of `count` binary vectors bits[count*n] (host, 0/1 bytes), into F[count]
+ * (host int64), computed on the device with the same kernels as the run's evaluations. */
+sbo_status sbo_eval(sbo_problem* p, int64_t count, const uint8_t* bits, int64_t* F);
+
+/* sbo_best: global best over all evaluations so far: lexicographic minimum of (F, t, r).
+ * x_out (host, n bytes, may be NULL), F_out, iter_out (t), restart_out (r) may be NULL.
+ * SBO_ENOTREADY before the first evaluation. */
+sbo_status sbo_best(sbo_problem* p, uint8_t* x_out, int64_t* F_out, int64_t* iter_out,
+                    int32_t* restart_out);
+
+/* sbo_restart_best: per-restart best F and the earliest t that reached it (host arrays of
+ * B entries; INT64_MAX / -1 for a restart not yet evaluated). */
+sbo_status sbo_restart_best(sbo_problem* p, int64_t* F, int64_t* t);
+
+/* sbo_state: FP32 copies of the current iterates, X and Y (host, B*n each, [r][i]). */
+sbo_status sbo_state(sbo_problem* p, float* X, float* Y);
+
+/* sbo_trace: min_r F at every evaluation so far, in order (host int64[cap]); *count gets
+ * the number of evaluations (may exceed cap; only the first cap are written). */
+sbo_status sbo_trace(sbo_problem* p, int64_t* minF, int64_t cap, int64_t* count);
+
+/* ---- differentiation -----------------------------------------------------------------------
+ * sbo_lagrangian: value and gradients of the Lagrangian (section 3.1) at B points:
+ *     L[r] = 1/2 x_r^T A x_r + c'^T x_r + sum_i y_ri (x_ri^2 - x_ri)
+ *     GX[r,i] = (A x_r)_i + c'_i + y_ri (2 x_ri - 1),   GY[r,i] = x_ri^2 - x_ri
+ * X_dev, Y_dev: device float32 [B][n] row-major (caller-owned).  gout_dev (device float32 [B],
+ * may be NULL = all ones) scales row r of GX and GY (the adjoint of a per-restart upstream
+ * gradient).  L_dev (B), GX_dev, GY_dev (B*n) are device float32 outputs; any may be NULL.  A x is recomputed on every
+ * call (nothing is cached between calls), with the contraction of the problem's precision.
+ * stream: cudaStream_t or NULL; the call is asynchronous on it.  Scratch of B*n*2 bytes is
+ * kept by the handle for the BF16 operand. */
+sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const float* Y_dev,
+                          const float* gout_dev, float* L_dev, float* GX_dev, float* GY_dev,
+                          void* stream);
+
+/* ---- execution options -------------------------------------------------------------------
+ * sbo_set_option: selects execution details; values take effect at the next sbo_gda_start.
+ *   SBO_OPT_KERNEL:     0 auto, 1 SIMT FP32 (plain form), 2 tcgen05 (BF16 dense),
+ *                       3 tiny-n single-CTA loop (n <= 64, FP32)
+ *   SBO_OPT_USE_GRAPH:  1 (default) replay blocks of K iterations from a CUDA graph; 0 launch
+ *                       every kernel directly
+ *   SBO_OPT_TILE_N:     restarts per tensor-core tile: 0 auto, 64, 128 or 256
+ *   SBO_OPT_TIMEOUT_US: budget in microseconds of every bounded device-side wait (default
+ *                       4,000,000); on expiry the kernel returns early and sbo_sync reports
+ *                       SBO_ETIMEOUT */
+enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4 };
+sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
+
+/* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL),
+ * the tile width and the iteration counter t; any pointer may be NULL. */
+sbo_status sbo_info(const sbo_problem* p, int64_t* n, int32_t* restarts, int32_t* kernel,
+                    int32_t* tile_n, int64_t* t);
+
+/* Kernel launches enqueued by this handle since creation (every kernel of the library). */
+int64_t sbo_launch_count(const sbo_problem* p);
+
+void sbo_destroy(sbo_problem* p);      /* NULL-safe; synchronises the stream first */
+const char* sbo_last_error(void);      /* thread-local; "" when the last call succeeded */
+const char* sbo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBO_H_ */

@@ -1,0 +1,887 @@
+// C ABI of libsbo (declared in include/sbo.h): validation, device memory, kernel selection,
+// the iteration schedule with its evaluation points, CUDA-graph replay of evaluation blocks,
+// and result read-back.  Every entry point catches its own failures and returns a status.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sbo_internal.h"
+
+using namespace sbo;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sbo_status fail(sbo_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+sbo_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SBO_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SBO_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+}  // namespace
+
+struct sbo_problem {
+  int64_t n = 0;
+  int fmt = FMT_DENSE;
+  int prec = SBO_FP32;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  int sms = 0;
+  // dense
+  void* A = nullptr;
+  int64_t lda = 0;
+  int a_type = OP_F32;
+  // CSR
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  void* val = nullptr;
+  int val_type = 0;
+  int64_t nnz = 0;
+  // linear term
+  float* cp = nullptr;
+  int64_t* cp64 = nullptr;
+  uint32_t* err = nullptr;
+  // options
+  int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0;
+  int64_t opt_timeout_us = 4000000;
+  // run
+  bool started = false;
+  sbo_gda_params prm{};
+  int kernel = KER_AUTO, layout = LAYOUT_RN, op_type = OP_F32, tile_n = 0;
+  int B = 0;
+  int64_t ld = 0;
+  int64_t t = 0;          // iterations completed
+  int64_t t_last_eval = 0;
+  int cur = 0;            // operand buffer holding x^t
+  float* Xm = nullptr;    // FP32 master (null when the operand is the FP32 master)
+  float* Y = nullptr;
+  void* Xop[2] = {nullptr, nullptr};
+  void* bits = nullptr;
+  long long *bestF = nullptr, *bestT = nullptr, *evalF = nullptr, *trace = nullptr, *n_evals = nullptr,
+            *t_last = nullptr, *sel = nullptr;
+  unsigned long long* F2 = nullptr;
+  uint8_t *bestBits = nullptr, *improved = nullptr;
+  int64_t trace_cap = 0;
+  int64_t n_evals_host = 0;
+  TcPlan plan{};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // Lagrangian scratch (BF16 operand)
+  void* lag_op = nullptr;
+  size_t lag_cap = 0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+void free_run(sbo_problem* p) {
+  for (auto& g : p->gexec)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  dfree(p->Xm);
+  dfree(p->Y);
+  dfree(p->Xop[0]);
+  dfree(p->Xop[1]);
+  dfree(p->bits);
+  dfree(p->bestF);
+  dfree(p->bestT);
+  dfree(p->evalF);
+  dfree(p->trace);
+  dfree(p->n_evals);
+  dfree(p->t_last);
+  dfree(p->sel);
+  dfree(p->F2);
+  dfree(p->bestBits);
+  dfree(p->improved);
+  p->started = false;
+}
+
+void free_all(sbo_problem* p) {
+  free_run(p);
+  dfree(p->A);
+  dfree(p->rowptr);
+  dfree(p->col);
+  dfree(p->val);
+  dfree(p->cp);
+  dfree(p->cp64);
+  dfree(p->err);
+  dfree(p->lag_op);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  p->cap_stream = nullptr;
+}
+
+sbo_status init_common(sbo_problem* p, void* stream) {
+  p->stream = static_cast<cudaStream_t>(stream);
+  int dev = 0;
+  SBO_CUDA(cudaGetDevice(&dev));
+  SBO_CUDA(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev));
+  SBO_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  SBO_CUDA(dalloc(&p->err, 1));
+  SBO_CUDA(cudaMemsetAsync(p->err, 0, sizeof(uint32_t), p->stream));
+  return SBO_OK;
+}
+
+EpiArgs base_args(const sbo_problem* p) {
+  EpiArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = (int)p->n;
+  a.B = p->B;
+  a.ld = p->ld;
+  a.alpha = (float)p->prm.alpha;
+  a.beta = (float)p->prm.beta;
+  a.delta = (float)p->prm.delta;
+  a.grad_tol = (float)p->prm.grad_tol;
+  a.cp = p->cp;
+  a.cp64 = p->cp64;
+  a.Xm = p->Xm;
+  a.Y = p->Y;
+  a.F2 = p->F2;
+  a.err = p->err;
+  return a;
+}
+
+uint64_t timeout_ns(const sbo_problem* p) { return (uint64_t)p->opt_timeout_us * 1000ull; }
+
+// One contraction launch with the given epilogue on the run's kernel.
+cudaError_t contract(sbo_problem* p, const EpiArgs& a, int mode, int which_x, cudaStream_t s) {
+  ++p->launches;
+  switch (p->kernel) {
+    case KER_SIMT: return launch_simt(static_cast<const float*>(p->A), p->lda, a, mode, s);
+    case KER_TC: return launch_tc(p->plan, which_x, nullptr, a, mode, timeout_ns(p), s);
+    case KER_CSR: return launch_csr(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, mode, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// x^t -> x^{t+1}; optionally writes the candidate bits of x^{t+1}.
+cudaError_t enqueue_step(sbo_problem* p, bool write_bits, cudaStream_t s) {
+  EpiArgs a = base_args(p);
+  a.Xin = p->Xop[p->cur];
+  a.Xout = p->Xop[p->cur ^ 1];
+  a.bits_out = write_bits ? p->bits : nullptr;
+  cudaError_t e = contract(p, a, EPI_UPDATE, p->cur, s);
+  p->cur ^= 1;
+  return e;
+}
+
+// Exact objective of the bits written by the last step, then best bookkeeping.
+cudaError_t enqueue_eval(sbo_problem* p, int64_t add, cudaStream_t s) {
+  EpiArgs a = base_args(p);
+  a.Xin = p->bits;
+  cudaError_t e = contract(p, a, EPI_EVAL, 2, s);
+  if (e != cudaSuccess) return e;
+  e = launch_eval_compare(p->F2, p->bestF, p->bestT, p->improved, p->evalF, p->B, p->t_last, add, s);
+  if (e != cudaSuccess) return e;
+  e = launch_copy_best(p->bits, p->op_type, p->bestBits, p->improved, (int)p->n, p->B, p->ld, p->layout, s);
+  if (e != cudaSuccess) return e;
+  e = launch_eval_finalize(p->F2, p->evalF, p->trace, p->n_evals, p->trace_cap, p->B, p->t_last, add, s);
+  p->launches += 3;
+  return e;
+}
+
+int64_t next_eval_after(const sbo_problem* p, int64_t t) {
+  const int64_t K = p->prm.eval_every;
+  int64_t nx = (t / K + 1) * K;
+  if (p->prm.iters > t && p->prm.iters < nx) nx = p->prm.iters;
+  return nx;
+}
+
+sbo_status run_direct(sbo_problem* p, int64_t steps, bool eval_at_end) {
+  for (int64_t s = 0; s < steps; ++s) {
+    const bool last = s + 1 == steps;
+    cudaError_t e = enqueue_step(p, last && eval_at_end, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "GDA step launch");
+  }
+  p->t += steps;
+  if (eval_at_end) {
+    cudaError_t e = enqueue_eval(p, p->t - p->t_last_eval, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "evaluation launch");
+    p->t_last_eval = p->t;
+    ++p->n_evals_host;
+  }
+  return SBO_OK;
+}
+
+// Capture K iterations + the evaluation, starting from operand buffer `parity`, into a graph.
+sbo_status capture_block(sbo_problem* p, int parity) {
+  const int64_t K = p->prm.eval_every;
+  const int saved_cur = p->cur;
+  const int64_t saved_launches = p->launches;
+  p->cur = parity;
+  cudaGraph_t g = nullptr;
+  SBO_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  for (int64_t s = 0; s < K && err == cudaSuccess; ++s) err = enqueue_step(p, s + 1 == K, p->cap_stream);
+  if (err == cudaSuccess) err = enqueue_eval(p, K, p->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
+  p->cur = saved_cur;
+  p->launches = saved_launches;
+  if (err != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(err, "launch during graph capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  cudaError_t e3 = cudaGraphInstantiate(&p->gexec[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) return cuda_fail(e3, "cudaGraphInstantiate");
+  return SBO_OK;
+}
+
+sbo_status run_tiny(sbo_problem* p, int64_t steps) {
+  TinyArgs a;
+  a.n = (int)p->n;
+  a.B = p->B;
+  a.ld = p->ld;
+  a.A = static_cast<const float*>(p->A);
+  a.lda = p->lda;
+  a.cp = p->cp;
+  a.cp64 = p->cp64;
+  a.X = p->Xm;
+  a.Y = p->Y;
+  a.alpha = (float)p->prm.alpha;
+  a.beta = (float)p->prm.beta;
+  a.delta = (float)p->prm.delta;
+  a.grad_tol = (float)p->prm.grad_tol;
+  a.t0 = p->t;
+  a.steps = steps;
+  a.K = p->prm.eval_every;
+  a.T = p->prm.iters;
+  a.bestF = p->bestF;
+  a.bestT = p->bestT;
+  a.bestBits = p->bestBits;
+  a.trace = p->trace;
+  a.e0 = p->n_evals_host;
+  a.trace_cap = p->trace_cap;
+  a.evalF = p->evalF;
+  cudaError_t e = launch_tiny(a, p->stream);
+  ++p->launches;
+  if (e != cudaSuccess) return cuda_fail(e, "tiny-n launch");
+  int64_t ne = 0;
+  for (int64_t t = p->t + 1; t <= p->t + steps; ++t)
+    if (t % p->prm.eval_every == 0 || t == p->prm.iters) { ++ne; p->t_last_eval = t; }
+  p->n_evals_host += ne;
+  p->t += steps;
+  long long ne_dev = (long long)p->n_evals_host, tl = (long long)p->t_last_eval;
+  SBO_CUDA(cudaMemcpyAsync(p->n_evals, &ne_dev, sizeof(long long), cudaMemcpyHostToDevice, p->stream));
+  SBO_CUDA(cudaMemcpyAsync(p->t_last, &tl, sizeof(long long), cudaMemcpyHostToDevice, p->stream));
+  SBO_CUDA(cudaStreamSynchronize(p->stream));  // the host values above must outlive the copies
+  return SBO_OK;
+}
+
+sbo_status check_params(const sbo_gda_params* q) {
+  if (!q) return fail(SBO_EINVAL, "params is NULL");
+  if (q->restarts < 1) return fail(SBO_EINVAL, "restarts must be >= 1");
+  if (q->eval_every < 1) return fail(SBO_EINVAL, "eval_every must be >= 1");
+  if (q->iters < 0) return fail(SBO_EINVAL, "iters must be >= 0");
+  if (!std::isfinite(q->alpha) || q->alpha <= 0) return fail(SBO_EINVAL, "alpha must be finite and > 0");
+  if (!std::isfinite(q->beta) || q->beta < 0) return fail(SBO_EINVAL, "beta must be finite and >= 0");
+  if (!std::isfinite(q->ybar)) return fail(SBO_EINVAL, "ybar must be finite");
+  if (!std::isfinite(q->delta) || q->delta < 0 || q->delta >= 0.5) return fail(SBO_EINVAL, "delta must be in [0, 0.5)");
+  if (!std::isfinite(q->grad_tol) || q->grad_tol < 0) return fail(SBO_EINVAL, "grad_tol must be finite and >= 0");
+  return SBO_OK;
+}
+
+sbo_status read_err(sbo_problem* p) {
+  uint32_t w = 0;
+  SBO_CUDA(cudaMemcpy(&w, p->err, sizeof(w), cudaMemcpyDeviceToHost));
+  if (w) {
+    SBO_CUDA(cudaMemset(p->err, 0, sizeof(uint32_t)));
+    if (w & ERR_TIMEOUT) return fail(SBO_ETIMEOUT, "a bounded device-side wait expired; the kernel returned early");
+    return fail(SBO_EDEVICE, "a device-side bounds check failed (input out of range)");
+  }
+  return SBO_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+const char* sbo_last_error(void) { return g_last_error.c_str(); }
+const char* sbo_version(void) { return "sbo 0.1 (sm_103a)"; }
+
+sbo_status sbo_create_dense(int64_t n, const int32_t* Q, const int32_t* c, int32_t precision, void* stream,
+                            sbo_problem** out) {
+  g_last_error.clear();
+  if (!out) return fail(SBO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!Q) return fail(SBO_EINVAL, "Q is NULL");
+  if (n < 1 || n > 65536) return fail(SBO_EINVAL, "dense n must be in [1, 65536]");
+  if (precision != SBO_FP32 && precision != SBO_BF16)
+    return fail(SBO_EINVAL, "dense problems take SBO_FP32 or SBO_BF16 (an FP8 contraction would need FP8 x)");
+  sbo_problem* p = new (std::nothrow) sbo_problem();
+  if (!p) return fail(SBO_ENOMEM, "host allocation failed");
+  sbo_status st = init_common(p, stream);
+  if (st != SBO_OK) { free_all(p); delete p; return st; }
+  p->n = n;
+  p->fmt = FMT_DENSE;
+  p->prec = precision;
+  p->a_type = precision == SBO_FP32 ? OP_F32 : OP_BF16;
+  p->lda = round_up(n, 8);
+  int32_t *Qd = nullptr, *cd = nullptr;
+  unsigned long long* rowsum = nullptr;
+  uint32_t* rerr = nullptr;
+  auto cleanup_tmp = [&]() { dfree(Qd); dfree(cd); dfree(rowsum); dfree(rerr); };
+  auto bail = [&](sbo_status s) { cleanup_tmp(); free_all(p); delete p; return s; };
+  cudaError_t e;
+  const size_t a_elt = p->a_type == OP_F32 ? 4 : 2;
+  if ((e = cudaMalloc(&p->A, (size_t)n * p->lda * a_elt)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc A"));
+  if ((e = dalloc(&p->cp, n)) != cudaSuccess || (e = dalloc(&p->cp64, n)) != cudaSuccess ||
+      (e = dalloc(&Qd, (size_t)n * n)) != cudaSuccess || (e = dalloc(&rowsum, n)) != cudaSuccess ||
+      (e = dalloc(&rerr, 1)) != cudaSuccess || (c && (e = dalloc(&cd, n)) != cudaSuccess))
+    return bail(e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation failed") : cuda_fail(e, "cudaMalloc"));
+  cudaStream_t s = p->stream;
+  if ((e = cudaMemcpyAsync(Qd, Q, sizeof(int32_t) * n * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return bail(cuda_fail(e, "copy Q"));
+  if (c && (e = cudaMemcpyAsync(cd, c, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return bail(cuda_fail(e, "copy c"));
+  cudaMemsetAsync(rowsum, 0, sizeof(unsigned long long) * n, s);
+  cudaMemsetAsync(rerr, 0, sizeof(uint32_t), s);
+  const int64_t limit = p->a_type == OP_F32 ? (1ll << 24) : 256;
+  if ((e = launch_canon_dense(Qd, cd, n, p->A, p->lda, p->a_type, p->cp, p->cp64, rowsum, rerr, limit, s)) !=
+      cudaSuccess)
+    return bail(cuda_fail(e, "canonicalisation launch"));
+  if ((e = launch_rowsum_check(rowsum, p->cp64, n, rerr, s)) != cudaSuccess) return bail(cuda_fail(e, "row-sum check"));
+  p->launches += 3;
+  uint32_t flags = 0;
+  if ((e = cudaMemcpyAsync(&flags, rerr, sizeof(flags), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return bail(cuda_fail(e, "canonicalisation"));
+  cleanup_tmp();
+  if (flags & 1u) {
+    free_all(p); delete p;
+    return fail(SBO_ERANGE, precision == SBO_BF16 ? "|Q_ij + Q_ji| > 256 is not exact in BF16"
+                                                  : "|Q_ij + Q_ji| > 2^24 is not exact in FP32");
+  }
+  if (flags & 2u) { free_all(p); delete p; return fail(SBO_ERANGE, "a row sum of |A_ij| reaches 2^24 (objective not exact)"); }
+  if (flags & 4u) { free_all(p); delete p; return fail(SBO_ERANGE, "c_i + Q_ii outside the int32 range"); }
+  *out = p;
+  return SBO_OK;
+}
+
+sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const int32_t* val,
+                          const int32_t* c, int32_t precision, void* stream, sbo_problem** out) {
+  g_last_error.clear();
+  if (!out) return fail(SBO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n >= (1ll << 31)) return fail(SBO_EINVAL, "n must be in [1, 2^31)");
+  if (nnz < 0) return fail(SBO_EINVAL, "nnz must be >= 0");
+  if (!rowptr || (nnz > 0 && (!col || !val))) return fail(SBO_EINVAL, "rowptr/col/val is NULL");
+  if (precision != SBO_FP32 && precision != SBO_BF16 && precision != SBO_FP8_E4M3)
+    return fail(SBO_EINVAL, "unknown precision");
+  if (rowptr[0] != 0 || rowptr[n] != nnz) return fail(SBO_EINVAL, "rowptr[0] must be 0 and rowptr[n] must be nnz");
+  for (int64_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return fail(SBO_EINVAL, "rowptr is not non-decreasing");
+  // A = Q + Q^T off the diagonal, c' = c + diag(Q)  (Prop. 2.4), built as sorted triples
+  std::vector<int64_t> cp(n, 0);
+  if (c)
+    for (int64_t i = 0; i < n; ++i) cp[i] = c[i];
+  struct Trip { int32_t i, j; int64_t v; };
+  std::vector<Trip> tr;
+  tr.reserve((size_t)2 * nnz);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int32_t j = col[e];
+      if (j < 0 || j >= n) return fail(SBO_EINVAL, "column index out of range");
+      if (j == i) { cp[i] += val[e]; continue; }
+      tr.push_back({(int32_t)i, j, (int64_t)val[e]});
+      tr.push_back({j, (int32_t)i, (int64_t)val[e]});
+    }
+  std::sort(tr.begin(), tr.end(), [](const Trip& a, const Trip& b) { return a.i != b.i ? a.i < b.i : a.j < b.j; });
+  std::vector<int32_t> rp(n + 1, 0), cc;
+  std::vector<int64_t> vv;
+  cc.reserve(tr.size());
+  vv.reserve(tr.size());
+  for (size_t k = 0; k < tr.size();) {
+    size_t m = k;
+    int64_t s = 0;
+    while (m < tr.size() && tr[m].i == tr[k].i && tr[m].j == tr[k].j) s += tr[m++].v;
+    if (s != 0) { cc.push_back(tr[k].j); vv.push_back(s); rp[tr[k].i + 1]++; }
+    k = m;
+  }
+  if (cc.size() >= (size_t)INT32_MAX) return fail(SBO_EINVAL, "too many non-zeros");
+  for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+  const int64_t limit = precision == SBO_FP32 ? (1ll << 24) : precision == SBO_BF16 ? 256 : 16;
+  std::vector<int64_t> rowabs(n, 0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+      const int64_t a = vv[e] < 0 ? -vv[e] : vv[e];
+      if (a > limit) return fail(SBO_ERANGE, "an entry of Q + Q^T is not exact at the requested precision");
+      rowabs[i] += a;
+    }
+  for (int64_t i = 0; i < n; ++i) {
+    if (rowabs[i] >= (1ll << 24)) return fail(SBO_ERANGE, "a row sum of |A_ij| reaches 2^24 (objective not exact)");
+    if (cp[i] >= (1ll << 31) || cp[i] <= -(1ll << 31)) return fail(SBO_ERANGE, "c_i + Q_ii outside the int32 range");
+  }
+  sbo_problem* p = new (std::nothrow) sbo_problem();
+  if (!p) return fail(SBO_ENOMEM, "host allocation failed");
+  sbo_status st = init_common(p, stream);
+  if (st != SBO_OK) { free_all(p); delete p; return st; }
+  p->n = n;
+  p->fmt = FMT_CSR;
+  p->prec = precision;
+  p->nnz = (int64_t)cc.size();
+  auto bail = [&](sbo_status s) { free_all(p); delete p; return s; };
+  // weights in the storage type (exact by the checks above)
+  std::vector<uint8_t> vbytes;
+  size_t velt = 4;
+  if (precision == SBO_FP32) {
+    p->val_type = 0;
+    vbytes.resize(cc.size() * 4);
+    for (size_t k = 0; k < cc.size(); ++k) { float f = (float)vv[k]; std::memcpy(&vbytes[4 * k], &f, 4); }
+  } else if (precision == SBO_BF16) {
+    p->val_type = 1;
+    velt = 2;
+    vbytes.resize(cc.size() * 2);
+    for (size_t k = 0; k < cc.size(); ++k) {
+      __nv_bfloat16 h = __float2bfloat16_rn((float)vv[k]);
+      std::memcpy(&vbytes[2 * k], &h, 2);
+    }
+  } else {
+    p->val_type = 2;
+    velt = 1;
+    vbytes.resize(cc.size());
+    for (size_t k = 0; k < cc.size(); ++k) {
+      __nv_fp8_e4m3 q((float)vv[k]);
+      vbytes[k] = q.__x;
+    }
+  }
+  std::vector<float> cpf(n);
+  for (int64_t i = 0; i < n; ++i) cpf[i] = (float)cp[i];
+  cudaError_t e;
+  if ((e = dalloc(&p->rowptr, n + 1)) != cudaSuccess || (e = dalloc(&p->col, cc.size())) != cudaSuccess ||
+      (e = cudaMalloc(&p->val, std::max<size_t>(1, cc.size() * velt))) != cudaSuccess ||
+      (e = dalloc(&p->cp, n)) != cudaSuccess || (e = dalloc(&p->cp64, n)) != cudaSuccess)
+    return bail(e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation failed") : cuda_fail(e, "cudaMalloc"));
+  if ((e = cudaMemcpy(p->rowptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (!cc.empty() && (e = cudaMemcpy(p->col, cc.data(), sizeof(int32_t) * cc.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (!cc.empty() && (e = cudaMemcpy(p->val, vbytes.data(), vbytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (e = cudaMemcpy(p->cp, cpf.data(), sizeof(float) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->cp64, cp.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(cuda_fail(e, "upload CSR"));
+  *out = p;
+  return SBO_OK;
+}
+
+sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  switch (option) {
+    case SBO_OPT_KERNEL:
+      if (value < 0 || value > 3) return fail(SBO_EINVAL, "kernel option must be 0..3");
+      p->opt_kernel = (int)value;
+      return SBO_OK;
+    case SBO_OPT_USE_GRAPH: p->opt_graph = value != 0; return SBO_OK;
+    case SBO_OPT_TILE_N:
+      if (value != 0 && value != 64 && value != 128 && value != 256) return fail(SBO_EINVAL, "tile_n must be 0, 64, 128 or 256");
+      p->opt_tile_n = (int)value;
+      return SBO_OK;
+    case SBO_OPT_TIMEOUT_US:
+      if (value < 1) return fail(SBO_EINVAL, "timeout must be >= 1 us");
+      p->opt_timeout_us = value;
+      return SBO_OK;
+    default: return fail(SBO_EINVAL, "unknown option");
+  }
+}
+
+sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float* x0) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  sbo_status st = check_params(prm);
+  if (st != SBO_OK) return st;
+  // kernel selection
+  int ker;
+  if (p->fmt == FMT_CSR) {
+    if (p->opt_kernel != KER_AUTO) return fail(SBO_EINVAL, "CSR problems use the CSR kernel only");
+    ker = KER_CSR;
+  } else if (p->opt_kernel != KER_AUTO) {
+    ker = p->opt_kernel;
+    if (ker == KER_TC && p->prec != SBO_BF16) return fail(SBO_EINVAL, "the tcgen05 kernel needs a BF16 problem");
+    if ((ker == KER_SIMT || ker == KER_TINY) && p->prec != SBO_FP32)
+      return fail(SBO_EINVAL, "the SIMT and tiny kernels need an FP32 problem");
+    if (ker == KER_TINY && p->n > 64) return fail(SBO_EINVAL, "the tiny kernel needs n <= 64");
+  } else if (p->prec == SBO_BF16) {
+    ker = KER_TC;
+  } else {
+    ker = p->n <= 64 ? KER_TINY : KER_SIMT;
+  }
+  if (ker == KER_TC && !tc_supported()) return fail(SBO_ECUDA, "tcgen05 path needs a compute capability 10.3 device");
+  free_run(p);
+  p->prm = *prm;
+  p->kernel = ker;
+  p->B = prm->restarts;
+  p->layout = ker == KER_CSR ? LAYOUT_NR : LAYOUT_RN;
+  p->op_type = (p->prec == SBO_FP32) ? OP_F32 : OP_BF16;
+  p->ld = p->layout == LAYOUT_RN ? round_up(p->n, 8) : round_up(p->B, 8);
+  p->t = 0;
+  p->t_last_eval = 0;
+  p->n_evals_host = 0;
+  p->cur = 0;
+  const int64_t rows = p->layout == LAYOUT_RN ? p->B : p->n;
+  const size_t elems = (size_t)rows * p->ld;
+  const size_t op_elt = p->op_type == OP_F32 ? 4 : 2;
+  cudaError_t e = cudaSuccess;
+  const bool need_master = ker == KER_TINY || p->op_type != OP_F32;
+  int64_t evals_T = prm->iters / prm->eval_every + 2;
+  p->trace_cap = evals_T + 4096;
+  auto al = [&](void** q, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(q, bytes ? bytes : 1);
+  };
+  if (need_master) al((void**)&p->Xm, elems * 4);
+  al((void**)&p->Y, elems * 4);
+  if (ker != KER_TINY) {
+    al(&p->Xop[0], elems * op_elt);
+    al(&p->Xop[1], elems * op_elt);
+    al(&p->bits, elems * op_elt);
+  }
+  al((void**)&p->bestF, sizeof(long long) * p->B);
+  al((void**)&p->bestT, sizeof(long long) * p->B);
+  al((void**)&p->evalF, sizeof(long long) * p->B);
+  al((void**)&p->F2, sizeof(unsigned long long) * p->B);
+  al((void**)&p->improved, p->B);
+  al((void**)&p->bestBits, elems);
+  al((void**)&p->trace, sizeof(long long) * p->trace_cap);
+  al((void**)&p->n_evals, sizeof(long long));
+  al((void**)&p->t_last, sizeof(long long));
+  al((void**)&p->sel, sizeof(long long) * 3);
+  if (e != cudaSuccess) {
+    free_run(p);
+    return e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation of the run state failed")
+                                          : cuda_fail(e, "cudaMalloc");
+  }
+  cudaStream_t s = p->stream;
+  // zero every buffer so padding never holds stale values; sentinels for bests and trace
+  if (p->Xm) cudaMemsetAsync(p->Xm, 0, elems * 4, s);
+  cudaMemsetAsync(p->Y, 0, elems * 4, s);
+  for (void* b : {p->Xop[0], p->Xop[1], p->bits})
+    if (b) cudaMemsetAsync(b, 0, elems * op_elt, s);
+  launch_fill_i64(p->bestF, p->B, LLONG_MAX, s);
+  launch_fill_i64(p->bestT, p->B, -1, s);
+  launch_fill_i64(p->trace, p->trace_cap, LLONG_MAX, s);
+  p->launches += 3;
+  cudaMemsetAsync(p->F2, 0, sizeof(unsigned long long) * p->B, s);
+  cudaMemsetAsync(p->bestBits, 0, elems, s);
+  cudaMemsetAsync(p->n_evals, 0, sizeof(long long), s);
+  cudaMemsetAsync(p->t_last, 0, sizeof(long long), s);
+  float* x0d = nullptr;
+  if (x0) {
+    if ((e = dalloc(&x0d, (size_t)p->B * p->n)) != cudaSuccess) { free_run(p); return cuda_fail(e, "cudaMalloc x0"); }
+    if ((e = cudaMemcpyAsync(x0d, x0, sizeof(float) * p->B * p->n, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+      dfree(x0d); free_run(p); return cuda_fail(e, "copy x0");
+    }
+  }
+  e = launch_init_state((int)p->n, p->B, p->ld, p->layout, prm->seed, (float)prm->ybar, x0d, p->Xm,
+                        ker == KER_TINY ? (void*)p->Xm : p->Xop[0], ker == KER_TINY ? OP_F32 : p->op_type, p->Y,
+                        p->err, s);
+  ++p->launches;
+  if (x0d) { cudaStreamSynchronize(s); dfree(x0d); }
+  if (e != cudaSuccess) { free_run(p); return cuda_fail(e, "init launch"); }
+  if (ker == KER_TC) {
+    int tn = p->opt_tile_n;
+    if (tn == 0) {
+      // restarts per tile: the widest tile that still gives every SM a tile, else the widest
+      tn = 256;
+      while (tn > 64 && (int64_t)((p->n + 127) / 128) * ((p->B + tn - 1) / tn) < p->sms) tn /= 2;
+      while (tn > 64 && tn / 2 >= p->B) tn /= 2;
+    }
+    p->tile_n = tn;
+    std::string why;
+    e = tc_make_plan(&p->plan, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, tn, &why);
+    if (e != cudaSuccess) { free_run(p); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
+  } else {
+    p->tile_n = 0;
+  }
+  p->started = true;
+  return SBO_OK;
+}
+
+sbo_status sbo_gda_run(sbo_problem* p, int64_t iters) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  if (!p->started) return fail(SBO_ENOTREADY, "sbo_gda_start has not been called");
+  if (iters < 0) return fail(SBO_EINVAL, "iters must be >= 0");
+  if (iters == 0) return SBO_OK;
+  if (p->kernel == KER_TINY) return run_tiny(p, iters);
+  const int64_t K = p->prm.eval_every;
+  const int64_t t_end = p->t + iters;
+  while (p->t < t_end) {
+    const int64_t nx = next_eval_after(p, p->t);
+    const int64_t stop = std::min(nx, t_end);
+    const int64_t steps = stop - p->t;
+    const bool eval_here = stop == nx;
+    if (p->opt_graph && eval_here && steps == K && p->t % K == 0 && p->t_last_eval == p->t) {
+      const int par = p->cur;
+      if (!p->gexec[par]) {
+        sbo_status st = capture_block(p, par);
+        if (st != SBO_OK) return st;
+      }
+      cudaError_t e = cudaGraphLaunch(p->gexec[par], p->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+      p->launches += K + 4;
+      if (K & 1) p->cur ^= 1;
+      p->t += K;
+      p->t_last_eval = p->t;
+      ++p->n_evals_host;
+    } else {
+      sbo_status st = run_direct(p, steps, eval_here);
+      if (st != SBO_OK) return st;
+    }
+  }
+  return SBO_OK;
+}
+
+sbo_status sbo_sync(sbo_problem* p) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  SBO_CUDA(cudaStreamSynchronize(p->stream));
+  return read_err(p);
+}
+
+sbo_status sbo_gda(sbo_problem* p, const sbo_gda_params* prm) {
+  sbo_status st = sbo_gda_start(p, prm, nullptr);
+  if (st != SBO_OK) return st;
+  st = sbo_gda_run(p, prm->iters);
+  if (st != SBO_OK) return st;
+  return sbo_sync(p);
+}
+
+sbo_status sbo_eval(sbo_problem* p, int64_t count, const uint8_t* bits, int64_t* F) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  if (count < 0 || (count > 0 && (!bits || !F))) return fail(SBO_EINVAL, "bad count or NULL arrays");
+  if (count == 0) return SBO_OK;
+  if (count > (1 << 20)) return fail(SBO_EINVAL, "count too large");
+  for (int64_t k = 0; k < count * p->n; ++k)
+    if (bits[k] > 1) return fail(SBO_EINVAL, "bits must be 0 or 1");
+  cudaStream_t s = p->stream;
+  const int layout = p->fmt == FMT_CSR ? LAYOUT_NR : LAYOUT_RN;
+  const int op = p->prec == SBO_FP32 ? OP_F32 : OP_BF16;
+  const int64_t ld = layout == LAYOUT_RN ? round_up(p->n, 8) : round_up(count, 8);
+  const int64_t rows = layout == LAYOUT_RN ? count : p->n;
+  uint8_t* bd = nullptr;
+  void* opd = nullptr;
+  unsigned long long* f2 = nullptr;
+  auto cleanup = [&]() { dfree(bd); if (opd) cudaFree(opd); opd = nullptr; dfree(f2); };
+  cudaError_t e;
+  if ((e = dalloc(&bd, (size_t)count * p->n)) != cudaSuccess ||
+      (e = cudaMalloc(&opd, (size_t)rows * ld * (op == OP_F32 ? 4 : 2))) != cudaSuccess ||
+      (e = dalloc(&f2, count)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "cudaMalloc (eval)");
+  }
+  cudaMemsetAsync(opd, 0, (size_t)rows * ld * (op == OP_F32 ? 4 : 2), s);
+  cudaMemsetAsync(f2, 0, sizeof(unsigned long long) * count, s);
+  if ((e = cudaMemcpyAsync(bd, bits, (size_t)count * p->n, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "copy bits");
+  }
+  e = launch_bits_to_operand(bd, (int)p->n, (int)count, opd, ld, layout, op, s);
+  ++p->launches;
+  EpiArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = (int)p->n;
+  a.B = (int)count;
+  a.ld = ld;
+  a.cp = p->cp;
+  a.cp64 = p->cp64;
+  a.Xin = opd;
+  a.F2 = f2;
+  a.err = p->err;
+  if (e == cudaSuccess) {
+    ++p->launches;
+    if (p->fmt == FMT_CSR) {
+      e = launch_csr(p->rowptr, p->col, p->val, p->val_type, a, op, EPI_EVAL, s);
+    } else if (p->prec == SBO_FP32) {
+      e = launch_simt(static_cast<const float*>(p->A), p->lda, a, EPI_EVAL, s);
+    } else {
+      TcPlan plan{};
+      std::string why;
+      const int tn = 64;
+      e = tc_make_plan(&plan, p->A, p->lda, (int)p->n, opd, nullptr, nullptr, ld, (int)count, tn, &why);
+      if (e != cudaSuccess) { cleanup(); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
+      e = launch_tc(plan, 0, nullptr, a, EPI_EVAL, timeout_ns(p), s);
+    }
+  }
+  std::vector<unsigned long long> h(count);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), f2, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "evaluation");
+  sbo_status st = read_err(p);
+  if (st != SBO_OK) return st;
+  for (int64_t k = 0; k < count; ++k) F[k] = (int64_t)(long long)h[k] / 2;
+  return SBO_OK;
+}
+
+sbo_status sbo_best(sbo_problem* p, uint8_t* x_out, int64_t* F_out, int64_t* iter_out, int32_t* restart_out) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  if (!p->started || p->n_evals_host == 0) return fail(SBO_ENOTREADY, "no evaluation has taken place yet");
+  cudaStream_t s = p->stream;
+  cudaError_t e = launch_best_select(p->bestF, p->bestT, p->B, p->sel, s);
+  ++p->launches;
+  if (e != cudaSuccess) return cuda_fail(e, "best selection");
+  long long h[3];
+  SBO_CUDA(cudaMemcpyAsync(h, p->sel, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SBO_CUDA(cudaStreamSynchronize(s));
+  sbo_status st = read_err(p);
+  if (st != SBO_OK) return st;
+  if (h[1] < 0 || h[2] < 0 || h[2] >= p->B) return fail(SBO_EDEVICE, "inconsistent best record");
+  if (F_out) *F_out = h[0];
+  if (iter_out) *iter_out = h[1];
+  if (restart_out) *restart_out = (int32_t)h[2];
+  if (x_out) {
+    const int64_t r = h[2];
+    if (p->layout == LAYOUT_RN) {
+      SBO_CUDA(cudaMemcpy(x_out, p->bestBits + r * p->ld, (size_t)p->n, cudaMemcpyDeviceToHost));
+    } else {
+      SBO_CUDA(cudaMemcpy2D(x_out, 1, p->bestBits + r, (size_t)p->ld, 1, (size_t)p->n, cudaMemcpyDeviceToHost));
+    }
+  }
+  return SBO_OK;
+}
+
+sbo_status sbo_restart_best(sbo_problem* p, int64_t* F, int64_t* t) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  if (!p->started) return fail(SBO_ENOTREADY, "sbo_gda_start has not been called");
+  SBO_CUDA(cudaStreamSynchronize(p->stream));
+  if (F) SBO_CUDA(cudaMemcpy(F, p->bestF, sizeof(int64_t) * p->B, cudaMemcpyDeviceToHost));
+  if (t) SBO_CUDA(cudaMemcpy(t, p->bestT, sizeof(int64_t) * p->B, cudaMemcpyDeviceToHost));
+  return read_err(p);
+}
+
+sbo_status sbo_state(sbo_problem* p, float* X, float* Y) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  if (!p->started) return fail(SBO_ENOTREADY, "sbo_gda_start has not been called");
+  cudaStream_t s = p->stream;
+  float* tmp = nullptr;
+  SBO_CUDA(dalloc(&tmp, (size_t)p->B * p->n));
+  const float* xsrc = p->Xm ? p->Xm : static_cast<const float*>(p->Xop[p->cur]);
+  cudaError_t e = cudaSuccess;
+  if (X) {
+    e = launch_gather_state(xsrc, (int)p->n, p->B, p->ld, p->layout, tmp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(X, tmp, sizeof(float) * p->B * p->n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (Y && e == cudaSuccess) {
+    e = launch_gather_state(p->Y, (int)p->n, p->B, p->ld, p->layout, tmp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Y, tmp, sizeof(float) * p->B * p->n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  dfree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "state read-back");
+  return read_err(p);
+}
+
+sbo_status sbo_trace(sbo_problem* p, int64_t* minF, int64_t cap, int64_t* count) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  if (!p->started) return fail(SBO_ENOTREADY, "sbo_gda_start has not been called");
+  SBO_CUDA(cudaStreamSynchronize(p->stream));
+  long long ne = 0;
+  SBO_CUDA(cudaMemcpy(&ne, p->n_evals, sizeof(ne), cudaMemcpyDeviceToHost));
+  if (count) *count = ne;
+  const int64_t m = std::min<int64_t>(std::min<int64_t>(ne, cap), p->trace_cap);
+  if (minF && m > 0) SBO_CUDA(cudaMemcpy(minF, p->trace, sizeof(int64_t) * m, cudaMemcpyDeviceToHost));
+  return read_err(p);
+}
+
+sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const float* Y_dev, const float* gout_dev,
+                          float* L_dev, float* GX_dev, float* GY_dev, void* stream) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  if (B < 1 || !X_dev || !Y_dev) return fail(SBO_EINVAL, "B must be >= 1 and X, Y non-NULL");
+  if (p->fmt != FMT_DENSE) return fail(SBO_EINVAL, "sbo_lagrangian supports dense problems");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  EpiArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = (int)p->n;
+  a.B = B;
+  a.ld = p->n;
+  a.cp = p->cp;
+  a.cp64 = p->cp64;
+  a.Xl = X_dev;
+  a.Yl = Y_dev;
+  a.L = L_dev;
+  a.GX = GX_dev;
+  a.GY = GY_dev;
+  a.gout = gout_dev;
+  a.err = p->err;
+  if (L_dev) SBO_CUDA(cudaMemsetAsync(L_dev, 0, sizeof(float) * B, s));
+  cudaError_t e;
+  if (p->prec == SBO_FP32) {
+    a.Xin = X_dev;
+    e = launch_simt(static_cast<const float*>(p->A), p->lda, a, EPI_LAGR, s);
+    ++p->launches;
+  } else {
+    const int64_t ldx = round_up(p->n, 8);
+    const size_t need = (size_t)B * ldx * 2;
+    if (need > p->lag_cap) {
+      if (p->lag_op) { cudaStreamSynchronize(s); cudaFree(p->lag_op); p->lag_op = nullptr; p->lag_cap = 0; }
+      SBO_CUDA(cudaMalloc(&p->lag_op, need));
+      SBO_CUDA(cudaMemsetAsync(p->lag_op, 0, need, s));
+      p->lag_cap = need;
+    }
+    e = launch_to_operand(X_dev, (int)p->n, B, p->n, p->lag_op, ldx, OP_BF16, s);
+    if (e != cudaSuccess) return cuda_fail(e, "operand conversion");
+    TcPlan plan{};
+    std::string why;
+    int tn = 256;
+    while (tn > 64 && (int64_t)((p->n + 127) / 128) * ((B + tn - 1) / tn) < p->sms) tn /= 2;
+    e = tc_make_plan(&plan, p->A, p->lda, (int)p->n, p->lag_op, nullptr, nullptr, ldx, B, tn, &why);
+    if (e != cudaSuccess) return fail(SBO_ECUDA, "tensor-core plan: " + why);
+    e = launch_tc(plan, 0, nullptr, a, EPI_LAGR, timeout_ns(p), s);
+    p->launches += 2;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "Lagrangian launch");
+  return SBO_OK;
+}
+
+sbo_status sbo_info(const sbo_problem* p, int64_t* n, int32_t* restarts, int32_t* kernel, int32_t* tile_n, int64_t* t) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  if (n) *n = p->n;
+  if (restarts) *restarts = p->B;
+  if (kernel) *kernel = p->kernel;
+  if (tile_n) *tile_n = p->tile_n;
+  if (t) *t = p->t;
+  return SBO_OK;
+}
+
+int64_t sbo_launch_count(const sbo_problem* p) { return p ? p->launches : 0; }
+
+void sbo_destroy(sbo_problem* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->stream);
+  free_all(p);
+  delete p;
+}
+
+}  // extern "C"

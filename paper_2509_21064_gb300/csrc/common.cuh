@@ -1,0 +1,85 @@
+// Shared device-side definitions of libsbo (GB300, sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+namespace sbo {
+
+// Device error word bits (written with atomicOr, read and cleared by sbo_sync).
+enum : uint32_t { ERR_TIMEOUT = 1u, ERR_BOUNDS = 2u };
+
+// Epilogue modes shared by the contraction kernels.
+enum EpiMode : int { EPI_UPDATE = 0, EPI_EVAL = 1, EPI_LAGR = 2 };
+
+// Operand element types of the contraction.
+enum OpType : int { OP_F32 = 0, OP_BF16 = 1 };
+
+// Arguments of the fused GDA / evaluation / Lagrangian epilogue.  Every state array is
+// addressed as [r * ld + i] (dense, restart-major) or [i * ld + r] (CSR, variable-major);
+// the kernels document which.
+struct EpiArgs {
+  int n, B;
+  int64_t ld;              // leading dimension of every state array (elements)
+  float alpha, beta, delta, grad_tol;
+  const float* cp;         // c' (FP32) [n]
+  const int64_t* cp64;     // c' (exact) [n]  (EPI_EVAL)
+  float* Xm;               // FP32 master x, updated in place; null when the operand is FP32
+  float* Y;                // y, updated in place
+  const void* Xin;         // contraction operand x^t (FP32 or BF16), read by every tile
+  void* Xout;              // operand x^{t+1} (ping-pong partner of Xin)
+  void* bits_out;          // if non-null: b = [x^{t+1} > 1/2] in the operand type
+  unsigned long long* F2;  // EPI_EVAL: 2F(b) accumulators per restart (two's complement)
+  const float* Xl;         // EPI_LAGR: x (FP32)
+  const float* Yl;         // EPI_LAGR: y (FP32)
+  float* L;                // EPI_LAGR: value per restart (accumulated with atomics), may be null
+  float* GX;               // EPI_LAGR: dL/dx, may be null
+  float* GY;               // EPI_LAGR: dL/dy, may be null
+  const float* gout;       // EPI_LAGR: per-restart scale of GX, GY (upstream gradient), may be null
+  uint32_t* err;           // device error word
+};
+
+__device__ __forceinline__ float op_load(const void* p, int64_t idx, int type) {
+  if (type == OP_F32) return static_cast<const float*>(p)[idx];
+  return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[idx]);
+}
+__device__ __forceinline__ void op_store(void* p, int64_t idx, float v, int type) {
+  if (type == OP_F32) static_cast<float*>(p)[idx] = v;
+  else static_cast<__nv_bfloat16*>(p)[idx] = __float2bfloat16_rn(v);
+}
+
+// One coordinate of Algorithm 1.  d is dL/dx at (x, y); returns x^{t+1}, writes y^{t+1}.
+__device__ __forceinline__ float pdbo_update(float x, float y, float d, float alpha, float beta,
+                                             float delta, float grad_tol, float* y_next) {
+  const bool stagnating = fabsf(x - 0.5f) <= delta && fabsf(d) <= grad_tol && y <= 0.0f;
+  float xn;
+  if (stagnating) {
+    xn = (x <= 0.5f) ? 0.5f - delta : 0.5f + delta;
+  } else {
+    xn = fminf(fmaxf(x - alpha * d, 0.0f), 1.0f);
+  }
+  *y_next = y + beta * (x * x - x);
+  return xn;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator: output number k of the
+// stream seeded with `seed` is mix(seed + (k+1) * 0x9E3779B97F4A7C15).
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ float uniform24(uint64_t seed, uint64_t r, uint64_t i) {
+  const uint64_t z = splitmix64_at(seed, (r << 32) | i);
+  return static_cast<float>(static_cast<uint32_t>(z >> 40)) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace sbo

@@ -1,0 +1,491 @@
+// Dense contraction on the 5th-generation tensor cores (tcgen05, sm_103a) with the PDBO
+// epilogue fused onto the accumulator tile.
+//
+//   D[i][r] = sum_k A[i][k] * Xb[r][k]           (= (A x_r)_i; A is n x n, Xb is B x n, BF16)
+//
+// A and Xb are both K-major, so one 128-byte swizzle row holds 64 consecutive k of one row
+// (TMA box 64 x rows, SWIZZLE_128B), which is the canonical K-major SW128 layout of a UMMA
+// shared-memory descriptor (8-row atoms of 1024 B, SBO = 1024 B).
+//
+// Persistent, warp-specialised CTA (one per SM, 256 threads):
+//   warp 0      TMA producer: A tile 128 x 64 and X tile tile_n x 64 per stage, mbarrier ring
+//   warp 1      TMEM allocator and single-thread MMA issuer (tcgen05.mma.cta_group::1.kind::f16,
+//               M=128, N=tile_n, K=16, FP32 accumulation in TMEM)
+//   warps 4-7   epilogue warpgroup: tcgen05.ld of the 128 x tile_n accumulator (lane = row i),
+//               one PDBO iteration / exact objective / Lagrangian per element, coalesced along i
+// TMEM holds two accumulators (2 x tile_n columns) so the epilogue of one tile overlaps the
+// main loop of the next.  Tiles are visited m-major with the restart tiles of one row block
+// adjacent, so CTAs that share an A row block run together and A is read from HBM ~once.
+// Every mbarrier wait is bounded by a globaltimer budget: on expiry the kernel raises
+// ERR_TIMEOUT, drains its own copies and MMAs (bounded too), frees TMEM and returns.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "sbo_internal.h"
+
+namespace sbo {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;
+constexpr int TC_SMEM_BUDGET = 196 * 1024;
+constexpr int TC_THREADS = 256;
+
+struct TcParams {
+  CUtensorMap mapA;
+  CUtensorMap mapX;
+  EpiArgs epi;
+  int n, m_tiles, n_tiles, num_tiles, kblocks;
+  uint64_t timeout_ns;
+};
+
+template <int BN>
+struct TcCfg {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;
+  static constexpr int B_BYTES = BN * TC_BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (TC_SMEM_BUDGET - 2048) / STAGE_BYTES > 8 ? 8 : (TC_SMEM_BUDGET - 2048) / STAGE_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /* align */ + 1024 /* barriers */;
+  static constexpr int TMEM_COLS = 2 * BN;
+  // instruction descriptor: D=F32 (bit 4), A=BF16 (bits 7-9), B=BF16 (bits 10-12),
+  // both K-major (bits 15, 16 clear), N>>3 at bit 17, M>>4 at bit 24
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(TC_BM >> 4) << 24);
+};
+
+// ---- PTX wrappers ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the deadline passed or another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t deadline,
+                                          const volatile int* abort_flag) {
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0u) {
+      if (*abort_flag) return false;
+      if (globaltimer_ns() > deadline) return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                   // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                   // SWIZZLE_128B
+  return d;
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int BN, int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ TcParams P) {
+  using C = TcCfg<BN>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte aligned tile area (SWIZZLE_128B atoms), barriers after it
+  uint8_t* tiles = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tiles + C::STAGES * C::STAGE_BYTES);
+  uint64_t* full_bar = bars;                      // [STAGES]
+  uint64_t* empty_bar = bars + C::STAGES;         // [STAGES]
+  uint64_t* tfull_bar = bars + 2 * C::STAGES;     // [2]
+  uint64_t* tempty_bar = bars + 2 * C::STAGES + 2;  // [2]
+  uint64_t* drain_bar = bars + 2 * C::STAGES + 4;   // [1]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 5);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint64_t deadline = globaltimer_ns() + P.timeout_ns;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&tfull_bar[a]), 1);
+      mbar_init(smem_u32(&tempty_bar[a]), 128);
+    }
+    mbar_init(smem_u32(drain_bar), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tma_prefetch_map(&P.mapA);
+    tma_prefetch_map(&P.mapX);
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const volatile int* vabort = abort_flag;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, issued_parity = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < P.num_tiles && ok; tile += gridDim.x) {
+        const int m_tile = tile / P.n_tiles, n_tile = tile % P.n_tiles;
+        for (int kb = 0; kb < P.kblocks; ++kb) {
+          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, deadline, vabort)) { ok = false; break; }
+          const uint32_t fb = smem_u32(&full_bar[stage]);
+          mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
+          uint8_t* sa = tiles + stage * C::STAGE_BYTES;
+          tma_load_2d(smem_u32(sa), &P.mapA, fb, kb * TC_BK, m_tile * TC_BM);
+          tma_load_2d(smem_u32(sa + C::A_BYTES), &P.mapX, fb, kb * TC_BK, n_tile * BN);
+          issued_mask |= 1u << stage;
+          issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+          if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) {
+        atomicOr(P.epi.err, ERR_TIMEOUT);
+        *abort_flag = 1;
+        // drain: every copy this thread issued completes on its full barrier
+        const uint64_t dl2 = globaltimer_ns() + 200000000ull;
+        const int zero = 0;
+        for (int s = 0; s < C::STAGES; ++s)
+          if (issued_mask & (1u << s)) mbar_wait(smem_u32(&full_bar[s]), (issued_parity >> s) & 1u, dl2, &zero);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      bool ok = true, issued_any = false;
+      for (int tile = blockIdx.x; tile < P.num_tiles && ok; tile += gridDim.x) {
+        if (!mbar_wait(smem_u32(&tempty_bar[acc]), acc_phase ^ 1u, deadline, vabort)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        for (int kb = 0; kb < P.kblocks; ++kb) {
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, deadline, vabort)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(tiles + stage * C::STAGE_BYTES);
+          const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            tc_mma(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), C::IDESC,
+                   (kb | kk) != 0 ? 1u : 0u);
+          }
+          issued_any = true;
+          tc_commit(smem_u32(&empty_bar[stage]));
+          if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        tc_commit(smem_u32(&tfull_bar[acc]));
+        if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+      }
+      if (!ok) {
+        atomicOr(P.epi.err, ERR_TIMEOUT);
+        *abort_flag = 1;
+        if (issued_any) {
+          tc_commit(smem_u32(drain_bar));
+          const int zero = 0;
+          mbar_wait(smem_u32(drain_bar), 0, globaltimer_ns() + 200000000ull, &zero);
+        }
+      }
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------------ epilogue warpgroup
+    const int wq = warp & 3;  // TMEM lanes 32*wq .. 32*wq+31
+    const EpiArgs& a = P.epi;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int tile = blockIdx.x; tile < P.num_tiles; tile += gridDim.x) {
+      const int m_tile = tile / P.n_tiles, n_tile = tile % P.n_tiles;
+      if (!mbar_wait(smem_u32(&tfull_bar[acc]), acc_phase, deadline, vabort)) {
+        atomicOr(a.err, ERR_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const int64_t i = (int64_t)m_tile * TC_BM + wq * 32 + lane;
+      const bool row_ok = i < a.n;
+      const float cpi = row_ok ? a.cp[i] : 0.0f;
+      const long long cp2 = (MODE == EPI_EVAL && row_ok) ? 2 * (long long)a.cp64[i] : 0;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float g[32];
+        tmem_ld32(tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc * BN + c0), g);
+        const int64_t rbase = (int64_t)n_tile * BN + c0;
+        if (MODE == EPI_UPDATE) {
+          if (row_ok) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int64_t r = rbase + j;
+              if (r >= a.B) break;
+              const int64_t idx = r * a.ld + i;
+              const float x = a.Xm[idx];
+              const float y = a.Y[idx];
+              const float d = g[j] + cpi + y * (2.0f * x - 1.0f);
+              float yn;
+              const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+              a.Xm[idx] = xn;
+              a.Y[idx] = yn;
+              static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);
+              if (a.bits_out) static_cast<__nv_bfloat16*>(a.bits_out)[idx] = __float2bfloat16_rn(xn > 0.5f ? 1.0f : 0.0f);
+            }
+          }
+        } else if (MODE == EPI_EVAL) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t r = rbase + j;
+            long long v = 0;
+            if (row_ok && r < a.B) {
+              const float b = __bfloat162float(static_cast<const __nv_bfloat16*>(a.Xin)[r * a.ld + i]);
+              if (b != 0.0f) v = (long long)g[j] + cp2;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && r < a.B && v != 0) atomicAdd(&a.F2[r], (unsigned long long)v);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t r = rbase + j;
+            float lv = 0.0f;
+            if (row_ok && r < a.B) {
+              const int64_t idx = r * a.ld + i;
+              const float x = a.Xl[idx], y = a.Yl[idx];
+              const float gx = x * x - x;
+              const float sc = a.gout ? a.gout[r] : 1.0f;
+              if (a.GX) a.GX[idx] = sc * (g[j] + cpi + y * (2.0f * x - 1.0f));
+              if (a.GY) a.GY[idx] = sc * gx;
+              lv = 0.5f * x * g[j] + cpi * x + y * gx;
+            }
+            if (a.L) {
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, o);
+              if (lane == 0 && r < a.B) atomicAdd(&a.L[r], lv);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&tempty_bar[acc]));
+      if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---- host side ---------------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool tc_supported() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3 && get_encode() != nullptr;
+}
+
+static cudaError_t encode_bf16_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t rows, uint64_t ld_elems,
+                                  uint32_t box_rows, std::string* why) {
+  auto fn = get_encode();
+  if (!fn) {
+    if (why) *why = "cuTensorMapEncodeTiled unavailable";
+    return cudaErrorNotSupported;
+  }
+  if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((ld_elems * 2) & 15)) {
+    if (why) *why = "TMA needs a 16-byte aligned base and row pitch";
+    return cudaErrorInvalidValue;
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {ld_elems * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    if (why) *why = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r);
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t tc_make_operand_map(CUtensorMap* m, const void* X, int64_t ldx, int n, int B, int tile_n,
+                                std::string* why) {
+  return encode_bf16_2d(m, X, (uint64_t)n, (uint64_t)B, (uint64_t)ldx, (uint32_t)tile_n, why);
+}
+
+template <int BN, int MODE>
+static cudaError_t set_attr() {
+  return cudaFuncSetAttribute(k_tc<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM);
+}
+
+cudaError_t tc_make_plan(TcPlan* plan, const void* A, int64_t lda, int n, const void* X0, const void* X1,
+                         const void* Xbits, int64_t ldx, int B, int tile_n, std::string* why) {
+  plan->ready = false;
+  if (tile_n != 64 && tile_n != 128 && tile_n != 256) {
+    if (why) *why = "tile_n must be 64, 128 or 256";
+    return cudaErrorInvalidValue;
+  }
+  cudaError_t e = encode_bf16_2d(&plan->mapA, A, (uint64_t)n, (uint64_t)n, (uint64_t)lda, TC_BM, why);
+  if (e != cudaSuccess) return e;
+  const void* xs[3] = {X0, X1, Xbits};
+  for (int k = 0; k < 3; ++k) {
+    if (!xs[k]) continue;
+    e = tc_make_operand_map(&plan->mapX[k], xs[k], ldx, n, B, tile_n, why);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  plan->tile_n = tile_n;
+  plan->m_tiles = (n + TC_BM - 1) / TC_BM;
+  plan->n_tiles = (B + tile_n - 1) / tile_n;
+  plan->num_tiles = plan->m_tiles * plan->n_tiles;
+  plan->grid = plan->num_tiles < sms ? plan->num_tiles : sms;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    cudaError_t r = cudaSuccess;
+    r = r == cudaSuccess ? set_attr<64, EPI_UPDATE>() : r;
+    r = r == cudaSuccess ? set_attr<64, EPI_EVAL>() : r;
+    r = r == cudaSuccess ? set_attr<64, EPI_LAGR>() : r;
+    r = r == cudaSuccess ? set_attr<128, EPI_UPDATE>() : r;
+    r = r == cudaSuccess ? set_attr<128, EPI_EVAL>() : r;
+    r = r == cudaSuccess ? set_attr<128, EPI_LAGR>() : r;
+    r = r == cudaSuccess ? set_attr<256, EPI_UPDATE>() : r;
+    r = r == cudaSuccess ? set_attr<256, EPI_EVAL>() : r;
+    r = r == cudaSuccess ? set_attr<256, EPI_LAGR>() : r;
+    attr_err = r;
+  });
+  if (attr_err != cudaSuccess) {
+    if (why) *why = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(attr_err);
+    return attr_err;
+  }
+  plan->ready = true;
+  return cudaSuccess;
+}
+
+template <int BN, int MODE>
+static cudaError_t launch_tc_t(const TcParams& P, int grid, cudaStream_t s) {
+  k_tc<BN, MODE><<<grid, TC_THREADS, TcCfg<BN>::SMEM, s>>>(P);
+  return cudaGetLastError();
+}
+
+template <int BN>
+static cudaError_t launch_tc_bn(const TcParams& P, int grid, int mode, cudaStream_t s) {
+  if (mode == EPI_UPDATE) return launch_tc_t<BN, EPI_UPDATE>(P, grid, s);
+  if (mode == EPI_EVAL) return launch_tc_t<BN, EPI_EVAL>(P, grid, s);
+  return launch_tc_t<BN, EPI_LAGR>(P, grid, s);
+}
+
+cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_override, const EpiArgs& a,
+                      int mode, uint64_t timeout_ns, cudaStream_t s) {
+  if (!plan.ready) return cudaErrorInvalidValue;
+  TcParams P;
+  P.mapA = plan.mapA;
+  P.mapX = map_override ? *map_override : plan.mapX[which_x];
+  P.epi = a;
+  P.n = a.n;
+  P.m_tiles = (a.n + TC_BM - 1) / TC_BM;
+  P.n_tiles = (a.B + plan.tile_n - 1) / plan.tile_n;
+  P.num_tiles = P.m_tiles * P.n_tiles;
+  P.kblocks = (a.n + TC_BK - 1) / TC_BK;
+  P.timeout_ns = timeout_ns;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = P.num_tiles < sms ? P.num_tiles : sms;
+  switch (plan.tile_n) {
+    case 64: return launch_tc_bn<64>(P, grid, mode, s);
+    case 128: return launch_tc_bn<128>(P, grid, mode, s);
+    default: return launch_tc_bn<256>(P, grid, mode, s);
+  }
+}
+
+}  // namespace sbo

@@ -1,0 +1,87 @@
+// Internal declarations of libsbo: the problem handle and the kernel launchers.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sbo.h"
+#include "common.cuh"
+
+namespace sbo {
+
+enum Format : int { FMT_DENSE = 0, FMT_CSR = 1 };
+enum Kernel : int { KER_AUTO = 0, KER_SIMT = 1, KER_TC = 2, KER_TINY = 3, KER_CSR = 4 };
+enum Layout : int { LAYOUT_RN = 0 /* [r][i] */, LAYOUT_NR = 1 /* [i][r] */ };
+
+// ---- launchers (each returns the launch's cudaError_t) -----------------------------------
+// k_setup.cu
+cudaError_t launch_canon_dense(const int32_t* Qd, const int32_t* cd, int64_t n, void* A, int64_t lda,
+                               int a_type, float* cp, int64_t* cp64, unsigned long long* rowsum,
+                               uint32_t* range_err, int64_t a_limit, cudaStream_t s);
+cudaError_t launch_rowsum_check(const unsigned long long* rowsum, const int64_t* cp64, int64_t n,
+                                uint32_t* range_err, cudaStream_t s);
+cudaError_t launch_init_state(int n, int B, int64_t ld, int layout, uint64_t seed, float ybar,
+                              const float* x0, float* Xm, void* Xop, int op_type, float* Y,
+                              uint32_t* err, cudaStream_t s);
+cudaError_t launch_to_operand(const float* X, int n, int B, int64_t ld_in, void* out, int64_t ld_out,
+                              int op_type, cudaStream_t s);
+cudaError_t launch_bits_to_operand(const uint8_t* bits, int n, int count, void* out, int64_t ld_out,
+                                   int layout, int op_type, cudaStream_t s);
+cudaError_t launch_fill_i64(long long* p, int64_t count, long long v, cudaStream_t s);
+cudaError_t launch_gather_state(const float* src, int n, int B, int64_t ld, int layout, float* dst_rn,
+                                cudaStream_t s);
+// k_simt.cu  (FP32 A, restart-major state)
+cudaError_t launch_simt(const float* A, int64_t lda, const EpiArgs& a, int mode, cudaStream_t s);
+// k_tiny.cu  (whole run in one launch for n <= 64)
+struct TinyArgs {
+  int n, B;
+  int64_t ld;
+  const float* A;          // FP32 [n][lda]
+  int64_t lda;
+  const float* cp;
+  const int64_t* cp64;
+  float* X;                // FP32 [B][ld] master, in place
+  float* Y;
+  float alpha, beta, delta, grad_tol;
+  int64_t t0, steps, K, T; // iterations t0+1 .. t0+steps; evaluate at multiples of K and at T
+  long long* bestF;
+  long long* bestT;
+  uint8_t* bestBits;       // [B][ld]
+  long long* trace;        // min_r F per evaluation, written at trace[e0 + e]
+  int64_t e0, trace_cap;
+  long long* evalF;        // scratch [B], F of the current evaluation
+};
+cudaError_t launch_tiny(const TinyArgs& a, cudaStream_t s);
+// k_csr.cu  (variable-major state)
+cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
+                       const EpiArgs& a, int op_type, int mode, cudaStream_t s);
+// k_best.cu
+cudaError_t launch_eval_compare(const unsigned long long* F2, long long* bestF, long long* bestT,
+                                uint8_t* improved, long long* evalF, int B, long long* t_last,
+                                int64_t add, cudaStream_t s);
+cudaError_t launch_copy_best(const void* bits_op, int op_type, uint8_t* bestBits, const uint8_t* improved,
+                             int n, int B, int64_t ld, int layout, cudaStream_t s);
+cudaError_t launch_eval_finalize(unsigned long long* F2, const long long* evalF, long long* trace,
+                                 long long* n_evals, int64_t trace_cap, int B, long long* t_last, int64_t add,
+                                 cudaStream_t s);
+cudaError_t launch_best_select(const long long* bestF, const long long* bestT, int B,
+                               long long* out3, cudaStream_t s);
+// k_tc.cu  (tcgen05 BF16 contraction with fused epilogue, restart-major state)
+struct TcPlan {
+  CUtensorMap mapA;        // A [n][lda] BF16, box 64 x 128, 128B swizzle
+  CUtensorMap mapX[3];     // operand buffers [B][ld] BF16 (ping, pong, bits), box 64 x tile_n
+  int tile_n;
+  int num_tiles, m_tiles, n_tiles, grid;
+  bool ready;
+};
+bool tc_supported();
+cudaError_t tc_make_plan(TcPlan* plan, const void* A, int64_t lda, int n, const void* X0, const void* X1,
+                         const void* Xbits, int64_t ldx, int B, int tile_n, std::string* why);
+cudaError_t tc_make_operand_map(CUtensorMap* m, const void* X, int64_t ldx, int n, int B, int tile_n,
+                                std::string* why);
+cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_override, const EpiArgs& a,
+                      int mode, uint64_t timeout_ns, cudaStream_t s);
+
+}  // namespace sbo

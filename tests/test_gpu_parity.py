@@ -1,0 +1,300 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Tolerances (normwise per restart and iteration, over the first 50 iterations, where the
+perturbation branch cannot fire because y stays positive):
+  FP32 contraction (SIMT, tiny-n, CSR FP32):        1e-5
+  BF16 / E4M3 contraction (tcgen05, CSR BF16/E4M3):  2e-2
+Objectives, argmins and best records are compared exactly (int64): the oracle recomputes F
+for every candidate the GPU reports.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from paper_2509_21064_gb300 import sbo as S
+from paper_2509_21064_gb300.build import build as build_lib
+from _helpers import gpu_trajectory, normwise, oracle_trajectory, to_gda_params
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+TOL_MIXED = 2e-2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib()
+    S.lib()
+
+
+def _check_traj(gx, gy, ox, oy, tol):
+    ex = normwise(gx, ox).max()
+    ey = normwise(gy, oy).max()
+    assert ex <= tol and ey <= tol, (ex, ey)
+    return ex, ey
+
+
+def _check_evals_exact(Q, c, gx_traj, trace, K):
+    """trace[e] (min_r F at t = (e+1)K) equals the oracle's min_r F of the GPU's own candidates."""
+    for e, Fmin in enumerate(trace):
+        t = (e + 1) * K
+        if t >= len(gx_traj):
+            break
+        bits = O.round_bits(gx_traj[t])
+        F = O.objective_batch(Q, c, bits)
+        assert int(F.min()) == int(Fmin), (t, int(F.min()), int(Fmin))
+
+
+# --------------------------------------------------------------------------------------------
+def test_initial_state_is_the_oracle_generator_bit_for_bit():
+    Q, c = W.dense_qubo(40, seed=3)
+    for prec, kernel in ((S.SBO_FP32, S.KERNEL_SIMT), (S.SBO_FP32, S.KERNEL_TINY), (S.SBO_BF16, S.KERNEL_TC)):
+        with S.Problem.dense(Q, c, precision=prec) as P:
+            P.set_option(S.SBO_OPT_KERNEL, kernel)
+            P.start(S.params(37, 0, 0.1, 0.1, 2.5, seed=1234))
+            X, Y = P.state()
+        X0, _ = O.init_state(40, 37, 1234, 2.5)
+        assert np.array_equal(X.astype(np.float64), X0)
+        assert np.all(Y == 2.5)
+
+
+def test_tiny_n20_dense_qubo_parity_and_best():
+    """Dense QUBO n=20, 32 restarts, 1000 iterations, FP32 (single-launch tiny-n kernel)."""
+    Q, c = W.dense_qubo(20, seed=0)
+    p = W.dense_params(Q, restarts=32, iters=1000, eval_every=10, seed=0)
+    prm = to_gda_params(p)
+    with S.Problem.dense(Q, c, precision=S.SBO_FP32) as P:
+        assert P.info()["n"] == 20
+        gx, gy = gpu_trajectory(P, prm, 50)
+        assert P.info()["kernel"] == S.KERNEL_TINY
+        ox, oy, _ = oracle_trajectory(Q, c, p, 50)
+        _check_traj(gx, gy, ox, oy, TOL_FP32)
+        _check_evals_exact(Q, c, gx, P.trace(), p.eval_every)
+        # the full run in one call
+        P.gda(prm)
+        x_star, F_star, t_star, r_star = P.best()
+        Fr, tr = P.restart_best()
+    assert O.objective(Q, c, x_star) == F_star
+    order = sorted((int(Fr[r]), int(tr[r]), r) for r in range(32))
+    assert (F_star, t_star, r_star) == order[0]
+    best, _ = O.brute_force(Q, c)
+    out = O.run(Q, c, **p.asdict())
+    assert F_star >= best
+    assert abs(F_star - out["F_star"]) <= 1e-3 * abs(out["F_star"])
+
+
+@pytest.mark.parametrize("n,B", [(200, 70), (129, 3)])
+def test_simt_fp32_parity_graph_and_direct(n, B):
+    Q, c = W.dense_qubo(n, seed=n)
+    p = W.dense_params(Q, restarts=B, iters=200, eval_every=10, seed=7)
+    prm = to_gda_params(p)
+    with S.Problem.dense(Q, c, precision=S.SBO_FP32) as P:
+        P.set_option(S.SBO_OPT_KERNEL, S.KERNEL_SIMT)
+        gx, gy = gpu_trajectory(P, prm, 50)
+        ox, oy, _ = oracle_trajectory(Q, c, p, 50)
+        _check_traj(gx, gy, ox, oy, TOL_FP32)
+        _check_evals_exact(Q, c, gx, P.trace(), p.eval_every)
+        # graph replay gives the same bits as direct launches
+        P.start(prm)
+        P.run(50)
+        X, Y = P.state()
+        assert np.array_equal(X, gx[50]) and np.array_equal(Y, gy[50])
+        P.set_option(S.SBO_OPT_USE_GRAPH, 0)
+        P.start(prm)
+        P.run(50)
+        X2, Y2 = P.state()
+        assert np.array_equal(X2, gx[50]) and np.array_equal(Y2, gy[50])
+
+
+@pytest.mark.parametrize("n,B,tile", [(300, 100, 0), (260, 300, 256), (333, 129, 128), (64, 17, 64)])
+def test_tcgen05_bf16_parity(n, B, tile):
+    Q, c = W.dense_qubo(n, seed=n + 1)
+    p = W.dense_params(Q, restarts=B, iters=200, eval_every=10, seed=11)
+    prm = to_gda_params(p)
+    with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
+        P.set_option(S.SBO_OPT_TILE_N, tile)
+        gx, gy = gpu_trajectory(P, prm, 50)
+        info = P.info()
+        assert info["kernel"] == S.KERNEL_TC
+        if tile:
+            assert info["tile_n"] == tile
+        ox, oy, _ = oracle_trajectory(Q, c, p, 50)
+        _check_traj(gx, gy, ox, oy, TOL_MIXED)
+        _check_evals_exact(Q, c, gx, P.trace(), p.eval_every)
+        P.start(prm)
+        P.run(50)
+        X, Y = P.state()
+        assert np.array_equal(X, gx[50]) and np.array_equal(Y, gy[50])
+
+
+def test_tcgen05_contraction_is_exact_on_bf16_representable_inputs():
+    """With x on a 1/256 grid (exact in BF16) the only error left is FP32 accumulation."""
+    import torch
+    n, B = 1000, 200
+    Q, c = W.dense_qubo(n, seed=5)
+    A, cp = O.canonicalize(Q, c)
+    rng = np.random.default_rng(0)
+    X = rng.integers(0, 257, size=(B, n)) / 256.0
+    Y = rng.normal(scale=100.0, size=(B, n))
+    L_o, GX_o, GY_o = O.lagrangian(A, cp, X, Y.astype(np.float32).astype(np.float64))
+    for prec in (S.SBO_BF16, S.SBO_FP32):
+        with S.Problem.dense(Q, c, precision=prec) as P:
+            Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+            Yt = torch.tensor(Y, dtype=torch.float32, device="cuda")
+            L = torch.empty(B, device="cuda")
+            GX = torch.empty_like(Xt)
+            GY = torch.empty_like(Xt)
+            S.sbo_lagrangian(P.h, B, Xt.data_ptr(), Yt.data_ptr(), None, L.data_ptr(), GX.data_ptr(), GY.data_ptr(),
+                             torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            assert normwise(GX.cpu().numpy(), GX_o).max() <= 1e-5
+            assert normwise(GY.cpu().numpy(), GY_o).max() <= 1e-6
+            assert np.max(np.abs(L.cpu().numpy() - L_o) / np.abs(L_o)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,tol", [(S.SBO_FP32, TOL_FP32), (S.SBO_BF16, TOL_MIXED), (S.SBO_FP8_E4M3, TOL_MIXED)])
+def test_csr_maxcut_parity(prec, tol):
+    """Max-Cut as QUBO on an Erdos-Renyi graph (n=2000, mean degree 6, +-1 weights), B=256."""
+    n = 2000
+    i, j, w = W.maxcut_er(n, 6.0, seed=0)
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    Qd = W.dense_from_csr(n, rowptr, col, val)
+    p = W.graph_params("maxcut", restarts=256, iters=2000, eval_every=10, seed=0)
+    prm = to_gda_params(p)
+    with S.Problem.csr(n, rowptr, col, val, c, precision=prec) as P:
+        gx, gy = gpu_trajectory(P, prm, 50)
+        assert P.info()["kernel"] == S.KERNEL_CSR
+        ox, oy, _ = oracle_trajectory(Qd, c, p, 50)
+        _check_traj(gx, gy, ox, oy, tol)
+        _check_evals_exact(Qd, c, gx, P.trace(), p.eval_every)
+        P.start(prm)
+        P.run(50)
+        X, Y = P.state()
+        assert np.array_equal(X, gx[50]) and np.array_equal(Y, gy[50])
+        x_star, F_star, t_star, r_star = P.best()
+    cut = sum(int(ww) for a, b, ww in zip(i, j, w) if x_star[a] != x_star[b])
+    assert F_star == -cut
+
+
+def test_csr_torus_e4m3_matches_fp32_form():
+    """100x100 torus, +-1 weights: E4M3 weights are exact, so the E4M3 run (BF16 x operand)
+    stays within the mixed tolerance of the FP32 form, and its objectives are exact."""
+    i, j, w = W.maxcut_torus(100, 100, seed=0)
+    n = 10000
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    p = W.graph_params("maxcut", restarts=512, iters=100, eval_every=50, seed=1)
+    prm = to_gda_params(p)
+    with S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32) as P32, \
+            S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP8_E4M3) as P8:
+        P32.start(prm)
+        P32.run(20)
+        P8.start(prm)
+        P8.run(20)
+        X32, _ = P32.state()
+        X8, _ = P8.state()
+        assert normwise(X8, X32).max() <= TOL_MIXED
+        P8.run(80)
+        x_star, F_star, _, _ = P8.best()
+    cut = int(np.sum(w * (x_star[i] != x_star[j])))
+    assert F_star == -cut
+
+
+@pytest.mark.parametrize("fmt", ["dense32", "dense16", "csr"])
+def test_eval_is_exact_at_worst_case_magnitudes(fmt):
+    n = 700
+    rng = np.random.default_rng(1)
+    M = np.where(rng.integers(0, 2, size=(n, n)) == 1, 100, -100)
+    M = np.triu(M) + np.triu(M, 1).T
+    c = np.diagonal(M).astype(np.int32).copy()
+    Q = (M - np.diag(np.diagonal(M))).astype(np.int32)
+    bits = rng.integers(0, 2, size=(9, n)).astype(np.uint8)
+    bits[0] = 1
+    bits[1] = 0
+    if fmt == "csr":
+        rows, cols = np.nonzero(Q)
+        rowptr = np.zeros(n + 1, np.int64)
+        np.add.at(rowptr, rows + 1, 1)
+        P = S.Problem.csr(n, np.cumsum(rowptr), cols.astype(np.int32), Q[rows, cols], c, precision=S.SBO_BF16)
+    else:
+        P = S.Problem.dense(Q, c, precision=S.SBO_FP32 if fmt == "dense32" else S.SBO_BF16)
+    with P:
+        F = P.eval(bits)
+    assert F.tolist() == O.objective_batch(Q, c, bits).tolist()
+
+
+def test_range_checks_reject_inexact_data():
+    Q = np.zeros((8, 8), np.int32)
+    Q[0, 1] = 200
+    Q[1, 0] = 100                      # A_01 = 300 > 256: not exact in BF16
+    with pytest.raises(S.SboError) as e:
+        S.Problem.dense(Q, None, precision=S.SBO_BF16)
+    assert e.value.status == S.SBO_ERANGE
+    S.Problem.dense(Q, None, precision=S.SBO_FP32).close()
+
+
+def test_maxcut_half_point_gradient_is_exactly_zero_on_gpu():
+    """Example in section 3.2: x = 1/2 is stationary for every y."""
+    import torch
+    n = 300
+    i, j, w = W.maxcut_er(n, 6.0, seed=2)
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    Qd = W.dense_from_csr(n, rowptr, col, val)
+    for prec in (S.SBO_FP32, S.SBO_BF16):
+        with S.Problem.dense(Qd, c, precision=prec) as P:
+            X = torch.full((5, n), 0.5, device="cuda")
+            Y = torch.randn(5, n, device="cuda") * 10
+            GX = torch.empty_like(X)
+            S.sbo_lagrangian(P.h, 5, X.data_ptr(), Y.data_ptr(), None, None, GX.data_ptr(), None,
+                             torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            assert torch.all(GX == 0).item()
+
+
+def test_autograd_function_matches_the_oracle_gradient():
+    import torch
+    from paper_2509_21064_gb300.autograd import lagrangian
+    n, B = 256, 12
+    Q, c = W.dense_qubo(n, seed=9)
+    A, cp = O.canonicalize(Q, c)
+    rng = np.random.default_rng(3)
+    X = rng.random((B, n)).astype(np.float32)
+    Y = rng.normal(scale=50.0, size=(B, n)).astype(np.float32)
+    w = rng.normal(size=B).astype(np.float32)
+    L_o, GX_o, GY_o = O.lagrangian(A, cp, X.astype(np.float64), Y.astype(np.float64))
+    with S.Problem.dense(Q, c, precision=S.SBO_FP32) as P:
+        Xt = torch.tensor(X, device="cuda", requires_grad=True)
+        Yt = torch.tensor(Y, device="cuda", requires_grad=True)
+        L = lagrangian(Xt, Yt, P)
+        (L * torch.tensor(w, device="cuda")).sum().backward()
+        assert np.max(np.abs(L.detach().cpu().numpy() - L_o) / np.abs(L_o)) <= 1e-5
+        assert normwise(Xt.grad.cpu().numpy(), w[:, None] * GX_o).max() <= 1e-6
+        assert normwise(Yt.grad.cpu().numpy(), w[:, None] * GY_o).max() <= 1e-6
+
+
+def test_full_size_dense_n20000_sampled_restarts():
+    """Dense QUBO n=20000, 1024 restarts (the headline launch configuration): three BF16
+    iterations, then restarts 0, 517 and 1023 against the oracle run on those restarts alone
+    (restarts are independent), and their exact objectives at t=3."""
+    n, B = 20000, 1024
+    Q, c = W.dense_qubo(n, seed=0)
+    p = W.dense_params(Q, restarts=B, iters=2000, eval_every=3, seed=0)
+    prm = to_gda_params(p)
+    with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
+        P.start(prm)
+        P.run(3)
+        X, Y = P.state()
+        Fr, tr = P.restart_best()
+        assert P.info()["tile_n"] in (64, 128, 256)
+    sample = [0, 517, 1023]
+    A, cp = O.canonicalize(Q, c)
+    del Q
+    X0, _ = O.init_state(n, B, p.seed, p.ybar)
+    ox, oy, _ = oracle_trajectory(None, None, p, 3, X0=X0[sample], A=A, cp=cp)
+    assert normwise(X[sample], ox[3]).max() <= TOL_MIXED
+    assert normwise(Y[sample], oy[3]).max() <= TOL_MIXED
+    Qs = W.dense_qubo(n, seed=0)[0]
+    for k, r in enumerate(sample):
+        b = O.round_bits(X[r])
+        assert tr[r] == 3
+        assert Fr[r] == O.objective(Qs, c, b)
