@@ -143,6 +143,21 @@ sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const f
                           const float* gout_dev, float* L_dev, float* GX_dev, float* GY_dev,
                           void* stream);
 
+/* sbo_lagrangian_noalloc: the same computation and arguments as sbo_lagrangian, for callers
+ * that cannot allocate device memory -- code running inside a CUDA stream capture (where
+ * cudaMalloc is not allowed), processes whose device memory belongs to a framework's pool or a
+ * fixed budget, and loops that cannot absorb cudaMalloc's implicit synchronisation.  The paper
+ * has no counterpart: this is a property of the library, not of the method.  It calls no
+ * cudaMalloc/cudaFree or other allocating routine; for BF16 problems it stages the BF16 copy
+ * of X in one fixed 16 MiB device array that every GPU loading the library holds until the
+ * process exits, so it requires B * round_up(n, 8) * 2 <= 16 MiB and returns SBO_EINVAL
+ * otherwise (FP32 problems need no scratch and have no limit).  The first call on a device,
+ * with that device current, looks up the array's address; make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on the GPU race. */
+sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev, const float* Y_dev,
+                                  const float* gout_dev, float* L_dev, float* GX_dev, float* GY_dev,
+                                  void* stream);
+
 /* ---- execution options -------------------------------------------------------------------
  * sbo_set_option: selects execution details; values take effect at the next sbo_gda_start.
  *   SBO_OPT_KERNEL:     0 auto, 1 SIMT FP32 (plain form), 2 tcgen05 (BF16 dense),

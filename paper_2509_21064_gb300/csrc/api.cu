@@ -885,3 +885,25 @@ void sbo_destroy(sbo_problem* p) {
 }
 
 }  // extern "C"
+
+// ---- internal accessors for entry points defined in other translation units ---------------
+namespace sbo {
+
+bool dense_view(sbo_problem* p, DenseView* v) {
+  if (!p || p->fmt != FMT_DENSE) return false;
+  v->n = p->n;
+  v->prec = p->prec;
+  v->A = p->A;
+  v->lda = p->lda;
+  v->cp = p->cp;
+  v->cp64 = p->cp64;
+  v->err = p->err;
+  v->timeout_ns = timeout_ns(p);
+  v->sms = p->sms;
+  v->launches = &p->launches;
+  return true;
+}
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace sbo

@@ -84,4 +84,21 @@ cudaError_t tc_make_operand_map(CUtensorMap* m, const void* X, int64_t ldx, int 
 cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_override, const EpiArgs& a,
                       int mode, uint64_t timeout_ns, cudaStream_t s);
 
+// api.cu: read-only view of a dense problem and the thread-local error message, for entry
+// points defined outside api.cu.
+struct DenseView {
+  int64_t n;
+  int prec;
+  const void* A;
+  int64_t lda;
+  const float* cp;
+  const int64_t* cp64;
+  uint32_t* err;
+  uint64_t timeout_ns;
+  int sms;
+  int64_t* launches;
+};
+bool dense_view(sbo_problem* p, DenseView* v);
+void set_last_error(const std::string& msg);
+
 }  // namespace sbo

@@ -24,7 +24,7 @@ KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR = 0, 1, 2, 3, 4
 
 # every symbol include/sbo.h declares
 EXPORTS = ["sbo_create_dense", "sbo_create_csr", "sbo_gda_start", "sbo_gda_run", "sbo_gda", "sbo_sync",
-           "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace", "sbo_lagrangian",
+           "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace", "sbo_lagrangian", "sbo_lagrangian_noalloc",
            "sbo_set_option", "sbo_info", "sbo_launch_count", "sbo_destroy", "sbo_last_error", "sbo_version"]
 
 
@@ -74,6 +74,7 @@ def lib():
         "sbo_state": (st, [_P, _F32P, _F32P]),
         "sbo_trace": (st, [_P, _I64P, ctypes.c_int64, _I64P]),
         "sbo_lagrangian": (st, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P]),
+        "sbo_lagrangian_noalloc": (st, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P]),
         "sbo_set_option": (st, [_P, ctypes.c_int32, ctypes.c_int64]),
         "sbo_info": (st, [_P, _I64P, _I32P, _I32P, _I32P, _I64P]),
         "sbo_launch_count": (ctypes.c_int64, [_P]),
@@ -195,6 +196,12 @@ def sbo_lagrangian(h, B, X_ptr, Y_ptr, gout_ptr=None, L_ptr=None, GX_ptr=None, G
     """Device-pointer call (ints from ``tensor.data_ptr()``)."""
     _check(lib().sbo_lagrangian(h, int(B), X_ptr, Y_ptr, gout_ptr, L_ptr, GX_ptr, GY_ptr, _stream(stream)),
            "sbo_lagrangian")
+
+
+def sbo_lagrangian_noalloc(h, B, X_ptr, Y_ptr, gout_ptr=None, L_ptr=None, GX_ptr=None, GY_ptr=None, stream=None):
+    """As sbo_lagrangian, without any device allocation (fixed 16 MiB scratch; see sbo.h)."""
+    _check(lib().sbo_lagrangian_noalloc(h, int(B), X_ptr, Y_ptr, gout_ptr, L_ptr, GX_ptr, GY_ptr,
+                                        _stream(stream)), "sbo_lagrangian_noalloc")
 
 
 def sbo_set_option(h, option, value):
