@@ -195,6 +195,7 @@ def run_ours(args):
     S.lib()
     stream = torch.cuda.Stream(device=dev)
 
+    N_VARS, RESTARTS = args.n, args.restarts
     Q, c = W.dense_qubo(N_VARS, seed=0)
     p = W.dense_params(Q, restarts=RESTARTS, iters=10**9, eval_every=K_EVAL, seed=rank)
     prm = S.params(**p.asdict())
@@ -255,6 +256,12 @@ def run_ours(args):
     graph_ms_per_step = g0.elapsed_time(g1) / max(2, args.steps // 2)
     x_best, F_best, t_best, r_best = P.best()
     P.close()
+    if args.kernel_only:
+        if rank == 0:
+            print(json.dumps({"n": N_VARS, "restarts": RESTARTS, "ms_per_step": ms / args.steps,
+                              "update_launch_ms": t_kernel * 1e3, "graph_ms_per_step": graph_ms_per_step,
+                              "tflops": 2.0 * N_VARS * N_VARS * RESTARTS / t_kernel / 1e12}), flush=True)
+        return 0
 
     # e2e through the public API with host buffers (pinned), every step: H2D of Q, c; K
     # iterations + evaluation; D2H of (x*, F*)
@@ -329,6 +336,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_VARS, help="variables (profiling cases only)")
+    ap.add_argument("--restarts", type=int, default=RESTARTS, help="restarts (profiling cases only)")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time the device loop only (no e2e, no CPU baseline): for profiling cases")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

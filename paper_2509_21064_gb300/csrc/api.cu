@@ -69,7 +69,7 @@ struct sbo_problem {
   int64_t* cp64 = nullptr;
   uint32_t* err = nullptr;
   // options
-  int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0;
+  int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0, opt_split_k = 16;
   int64_t opt_timeout_us = 4000000;
   // run
   bool started = false;
@@ -91,6 +91,8 @@ struct sbo_problem {
   int64_t trace_cap = 0;
   int64_t n_evals_host = 0;
   TcPlan plan{};
+  float* tc_ws = nullptr;      // split-K partial tiles of the tcgen05 contraction
+  int* tc_ctr = nullptr;       // split-K arrival counters (zero between launches)
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   // Lagrangian scratch (BF16 operand)
   void* lag_op = nullptr;
@@ -118,6 +120,8 @@ void free_run(sbo_problem* p) {
   dfree(p->F2);
   dfree(p->bestBits);
   dfree(p->improved);
+  dfree(p->tc_ws);
+  dfree(p->tc_ctr);
   p->started = false;
 }
 
@@ -501,6 +505,10 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       if (value != 0 && value != 64 && value != 128 && value != 256) return fail(SBO_EINVAL, "tile_n must be 0, 64, 128 or 256");
       p->opt_tile_n = (int)value;
       return SBO_OK;
+    case SBO_OPT_SPLIT_K:
+      if (value < 0 || value > 64) return fail(SBO_EINVAL, "split-K factor must be in [0, 64]");
+      p->opt_split_k = (int)value;
+      return SBO_OK;
     case SBO_OPT_TIMEOUT_US:
       if (value < 1) return fail(SBO_EINVAL, "timeout must be >= 1 us");
       p->opt_timeout_us = value;
@@ -613,6 +621,19 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
     std::string why;
     e = tc_make_plan(&p->plan, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, tn, &why);
     if (e != cudaSuccess) { free_run(p); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
+    if (p->opt_split_k >= 2) {
+      // split-K workspace: one partial tile per CTA, arrival counters per tail tile slice
+      if ((e = dalloc(&p->tc_ws, (size_t)p->sms * tn * 128)) != cudaSuccess ||
+          (e = dalloc(&p->tc_ctr, (size_t)p->sms * TC_WS_COUNTERS_PER_TILE)) != cudaSuccess) {
+        free_run(p);
+        return e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation of the split-K workspace failed")
+                                              : cuda_fail(e, "cudaMalloc");
+      }
+      cudaMemsetAsync(p->tc_ctr, 0, sizeof(int) * p->sms * TC_WS_COUNTERS_PER_TILE, s);
+      p->plan.ws = p->tc_ws;
+      p->plan.counters = p->tc_ctr;
+      p->plan.max_splits = p->opt_split_k;
+    }
   } else {
     p->tile_n = 0;
   }

@@ -7,12 +7,13 @@
 // (TMA box 64 x rows, SWIZZLE_128B), which is the canonical K-major SW128 layout of a UMMA
 // shared-memory descriptor (8-row atoms of 1024 B, SBO = 1024 B).
 //
-// Persistent, warp-specialised CTA (one per SM, 256 threads):
+// Persistent, warp-specialised CTA (one per SM, 384 threads):
 //   warp 0      TMA producer: A tile 128 x 64 and X tile tile_n x 64 per stage, mbarrier ring
 //   warp 1      TMEM allocator and single-thread MMA issuer (tcgen05.mma.cta_group::1.kind::f16,
 //               M=128, N=tile_n, K=16, FP32 accumulation in TMEM)
-//   warps 4-7   epilogue warpgroup: tcgen05.ld of the 128 x tile_n accumulator (lane = row i),
-//               one PDBO iteration / exact objective / Lagrangian per element, coalesced along i
+//   warps 4-11  two epilogue warpgroups (half of the columns each): tcgen05.ld of the
+//               128 x tile_n accumulator (lane = row i), one PDBO iteration / exact objective /
+//               Lagrangian per element, loads batched per 32-column chunk, coalesced along i
 // TMEM holds two accumulators (2 x tile_n columns) so the epilogue of one tile overlaps the
 // main loop of the next.  Tiles are visited m-major with the restart tiles of one row block
 // adjacent, so CTAs that share an A row block run together and A is read from HBM ~once.
@@ -29,13 +30,19 @@ namespace sbo {
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;
 constexpr int TC_SMEM_BUDGET = 196 * 1024;
-constexpr int TC_THREADS = 256;
+constexpr int TC_MIN_KB_PER_SPLIT = 8;  // a split-K unit covers at least 8 k-blocks (512 of K)
+constexpr int TC_THREADS = 384;   // warps 0-3: producer, MMA, 2 idle; warps 4-11: epilogue
 
 struct TcParams {
   CUtensorMap mapA;
   CUtensorMap mapX;
   EpiArgs epi;
   int n, m_tiles, n_tiles, num_tiles, kblocks;
+  int dp_tiles;    // tiles computed whole, round-robin over the grid
+  int splits;      // split-K factor of the remaining (tail) tiles
+  int sk_units;    // (num_tiles - dp_tiles) * splits, one per CTA
+  float* ws;       // split-K partial tiles [sk_units][BN][128] (scratch)
+  int* counters;   // arrivals per (tail tile, epilogue warp slice), zero between launches (scratch)
   uint64_t timeout_ns;
 };
 
@@ -89,6 +96,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
   }
   return true;
 }
+// Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast to the whole warp.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, uint64_t deadline,
+                                               const volatile int* abort_flag, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = mbar_wait(bar, parity, deadline, abort_flag) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
@@ -139,6 +153,122 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Work list of one CTA: data-parallel tiles blockIdx.x, blockIdx.x + G, ... below dp_tiles
+// (whole K each), then at most one split-K unit of the tail tiles (unit u = blockIdx.x covers
+// k-blocks [s KB/S, (s+1) KB/S) of tail tile u / S, s = u % S).
+struct TcWork {
+  int tile, kb0, kb1, unit;  // unit < 0: whole tile
+};
+__device__ __forceinline__ bool tc_work(const TcParams& P, int j, TcWork& w) {
+  const int G = gridDim.x, c = blockIdx.x;
+  const int ndp = c < P.dp_tiles ? (P.dp_tiles - c + G - 1) / G : 0;
+  if (j < ndp) {
+    w.tile = c + j * G;
+    w.kb0 = 0;
+    w.kb1 = P.kblocks;
+    w.unit = -1;
+    return true;
+  }
+  if (j == ndp && c < P.sk_units) {
+    const int s = c % P.splits;
+    w.tile = P.dp_tiles + c / P.splits;
+    w.kb0 = (int)((int64_t)s * P.kblocks / P.splits);
+    w.kb1 = (int)((int64_t)(s + 1) * P.kblocks / P.splits);
+    w.unit = c;
+    return true;
+  }
+  return false;
+}
+
+// ---- epilogue pieces --------------------------------------------------------------------------
+// Global loads one 32-column chunk needs before the accumulator is read.
+template <int MODE>
+__device__ __forceinline__ void epi_load(const EpiArgs& a, int64_t i, bool row_ok, int64_t rbase, float (&u)[32],
+                                         float (&v)[32]) {
+  if (MODE == EPI_UPDATE) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int64_t r = rbase + j;
+      const bool ok = row_ok && r < a.B;
+      const int64_t idx = r * a.ld + i;
+      u[j] = ok ? a.Xm[idx] : 0.0f;
+      v[j] = ok ? a.Y[idx] : 0.0f;
+    }
+  } else if (MODE == EPI_EVAL) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int64_t r = rbase + j;
+      const bool ok = row_ok && r < a.B;
+      u[j] = ok ? __bfloat162float(static_cast<const __nv_bfloat16*>(a.Xin)[r * a.ld + i]) : 0.0f;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int64_t r = rbase + j;
+      const bool ok = row_ok && r < a.B;
+      const int64_t idx = r * a.ld + i;
+      u[j] = ok ? a.Xl[idx] : 0.0f;
+      v[j] = ok ? a.Yl[idx] : 0.0f;
+    }
+  }
+}
+
+// One chunk of the epilogue given the accumulator values g (= (A x_r)_i for 32 restarts r).
+template <int MODE>
+__device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_ok, float cpi, long long cp2,
+                                          int64_t rbase, int lane, const float (&g)[32], const float (&u)[32],
+                                          const float (&v)[32]) {
+  if (MODE == EPI_UPDATE) {
+    if (row_ok) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t r = rbase + j;
+        if (r < a.B) {
+          const int64_t idx = r * a.ld + i;
+          const float x = u[j], y = v[j];
+          const float d = g[j] + cpi + y * (2.0f * x - 1.0f);
+          float yn;
+          const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+          a.Xm[idx] = xn;
+          a.Y[idx] = yn;
+          static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);
+          if (a.bits_out)
+            static_cast<__nv_bfloat16*>(a.bits_out)[idx] = __float2bfloat16_rn(xn > 0.5f ? 1.0f : 0.0f);
+        }
+      }
+    }
+  } else if (MODE == EPI_EVAL) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int64_t r = rbase + j;
+      long long w = (u[j] != 0.0f) ? (long long)g[j] + cp2 : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+      if (lane == 0 && r < a.B && w != 0) atomicAdd(&a.F2[r], (unsigned long long)w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int64_t r = rbase + j;
+      float lv = 0.0f;
+      if (row_ok && r < a.B) {
+        const int64_t idx = r * a.ld + i;
+        const float x = u[j], y = v[j];
+        const float gx = x * x - x;
+        const float sc = a.gout ? a.gout[r] : 1.0f;
+        if (a.GX) a.GX[idx] = sc * (g[j] + cpi + y * (2.0f * x - 1.0f));
+        if (a.GY) a.GY[idx] = sc * gx;
+        lv = 0.5f * x * g[j] + cpi * x + y * gx;
+      }
+      if (a.L) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, o);
+        if (lane == 0 && r < a.B) atomicAdd(&a.L[r], lv);
+      }
+    }
+  }
+}
+
 template <int BN, int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ TcParams P) {
   using C = TcCfg<BN>;
@@ -165,7 +295,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&tfull_bar[a]), 1);
-      mbar_init(smem_u32(&tempty_bar[a]), 128);
+      mbar_init(smem_u32(&tempty_bar[a]), 256);
     }
     mbar_init(smem_u32(drain_bar), 1);
     *abort_flag = 0;
@@ -193,9 +323,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
       uint32_t phase = 0;
       uint32_t issued_mask = 0, issued_parity = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < P.num_tiles && ok; tile += gridDim.x) {
-        const int m_tile = tile / P.n_tiles, n_tile = tile % P.n_tiles;
-        for (int kb = 0; kb < P.kblocks; ++kb) {
+      TcWork w;
+      for (int j = 0; ok && tc_work(P, j, w); ++j) {
+        const int m_tile = w.tile / P.n_tiles, n_tile = w.tile % P.n_tiles;
+        for (int kb = w.kb0; kb < w.kb1; ++kb) {
           if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, deadline, vabort)) { ok = false; break; }
           const uint32_t fb = smem_u32(&full_bar[stage]);
           mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
@@ -225,11 +356,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
       int acc = 0;
       uint32_t acc_phase = 0;
       bool ok = true, issued_any = false;
-      for (int tile = blockIdx.x; tile < P.num_tiles && ok; tile += gridDim.x) {
+      TcWork w;
+      for (int j = 0; ok && tc_work(P, j, w); ++j) {
         if (!mbar_wait(smem_u32(&tempty_bar[acc]), acc_phase ^ 1u, deadline, vabort)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
-        for (int kb = 0; kb < P.kblocks; ++kb) {
+        for (int kb = w.kb0; kb < w.kb1; ++kb) {
           if (!mbar_wait(smem_u32(&full_bar[stage]), phase, deadline, vabort)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_u32(tiles + stage * C::STAGE_BYTES);
@@ -237,7 +369,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
 #pragma unroll
           for (int kk = 0; kk < TC_BK / 16; ++kk) {
             tc_mma(d_tmem, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), C::IDESC,
-                   (kb | kk) != 0 ? 1u : 0u);
+                   (kb > w.kb0 || kk > 0) ? 1u : 0u);
           }
           issued_any = true;
           tc_commit(smem_u32(&empty_bar[stage]));
@@ -258,83 +390,97 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
       }
     }
   } else if (warp >= 4) {
-    // ------------------------------------------------------------------ epilogue warpgroup
-    const int wq = warp & 3;  // TMEM lanes 32*wq .. 32*wq+31
+    // ------------------------------------------------------------------ epilogue warpgroups
+    // Two warpgroups split the tile's columns; inside a warpgroup, warp w reads TMEM lanes
+    // 32*(w%4) .. +31, i.e. rows i of the tile.  Each 32-column chunk first issues every global
+    // load it needs (so their latencies overlap), then reads the accumulator, then computes and
+    // stores.  A split-K unit writes its partial tile to the workspace instead.  Each warp owns
+    // one slice of the tile (its 32 rows x its warpgroup's columns); the warp that completes a
+    // slice last, over all splits of the tile, sums the slice's partials in split order (the
+    // result does not depend on arrival order) and runs the epilogue on it.  All waits are
+    // warp-uniform and no barrier spans more than one warp, so a timeout cannot strand a warp.
+    constexpr int HALF = BN / 2;
+    const int wg = (warp - 4) >> 2;
+    const int wq = warp & 3;
+    const int slice = wg * 4 + wq;
     const EpiArgs& a = P.epi;
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int tile = blockIdx.x; tile < P.num_tiles; tile += gridDim.x) {
-      const int m_tile = tile / P.n_tiles, n_tile = tile % P.n_tiles;
-      if (!mbar_wait(smem_u32(&tfull_bar[acc]), acc_phase, deadline, vabort)) {
-        atomicOr(a.err, ERR_TIMEOUT);
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      const int64_t i = (int64_t)m_tile * TC_BM + wq * 32 + lane;
+    TcWork w;
+    for (int jw = 0; tc_work(P, jw, w); ++jw) {
+      const int m_tile = w.tile / P.n_tiles, n_tile = w.tile % P.n_tiles;
+      const int row = wq * 32 + lane;
+      const int64_t i = (int64_t)m_tile * TC_BM + row;
       const bool row_ok = i < a.n;
       const float cpi = row_ok ? a.cp[i] : 0.0f;
       const long long cp2 = (MODE == EPI_EVAL && row_ok) ? 2 * (long long)a.cp64[i] : 0;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        float g[32];
-        tmem_ld32(tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc * BN + c0), g);
-        const int64_t rbase = (int64_t)n_tile * BN + c0;
-        if (MODE == EPI_UPDATE) {
-          if (row_ok) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int64_t r = rbase + j;
-              if (r >= a.B) break;
-              const int64_t idx = r * a.ld + i;
-              const float x = a.Xm[idx];
-              const float y = a.Y[idx];
-              const float d = g[j] + cpi + y * (2.0f * x - 1.0f);
-              float yn;
-              const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
-              a.Xm[idx] = xn;
-              a.Y[idx] = yn;
-              static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);
-              if (a.bits_out) static_cast<__nv_bfloat16*>(a.bits_out)[idx] = __float2bfloat16_rn(xn > 0.5f ? 1.0f : 0.0f);
-            }
+      float u[32], v[32], g[32];
+      bool ok = true;
+      if (w.unit < 0) {
+        bool waited = false;
+        for (int c0 = wg * HALF; c0 < (wg + 1) * HALF; c0 += 32) {
+          const int64_t rbase = (int64_t)n_tile * BN + c0;
+          epi_load<MODE>(a, i, row_ok, rbase, u, v);
+          if (!waited) {
+            ok = mbar_wait_warp(smem_u32(&tfull_bar[acc]), acc_phase, deadline, vabort, lane);
+            if (!ok) break;
+            tc_fence_after();
+            waited = true;
           }
-        } else if (MODE == EPI_EVAL) {
+          tmem_ld32(tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc * BN + c0), g);
+          epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v);
+        }
+      } else {
+        ok = mbar_wait_warp(smem_u32(&tfull_bar[acc]), acc_phase, deadline, vabort, lane);
+        if (ok) {
+          tc_fence_after();
+          float* part = P.ws + (size_t)w.unit * BN * TC_BM;  // [column][row]
+          for (int c0 = wg * HALF; c0 < (wg + 1) * HALF; c0 += 32) {
+            tmem_ld32(tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc * BN + c0), g);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t r = rbase + j;
-            long long v = 0;
-            if (row_ok && r < a.B) {
-              const float b = __bfloat162float(static_cast<const __nv_bfloat16*>(a.Xin)[r * a.ld + i]);
-              if (b != 0.0f) v = (long long)g[j] + cp2;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && r < a.B && v != 0) atomicAdd(&a.F2[r], (unsigned long long)v);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t r = rbase + j;
-            float lv = 0.0f;
-            if (row_ok && r < a.B) {
-              const int64_t idx = r * a.ld + i;
-              const float x = a.Xl[idx], y = a.Yl[idx];
-              const float gx = x * x - x;
-              const float sc = a.gout ? a.gout[r] : 1.0f;
-              if (a.GX) a.GX[idx] = sc * (g[j] + cpi + y * (2.0f * x - 1.0f));
-              if (a.GY) a.GY[idx] = sc * gx;
-              lv = 0.5f * x * g[j] + cpi * x + y * gx;
-            }
-            if (a.L) {
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) lv += __shfl_xor_sync(0xffffffffu, lv, o);
-              if (lane == 0 && r < a.B) atomicAdd(&a.L[r], lv);
-            }
+            for (int j = 0; j < 32; ++j) __stcg(part + (size_t)(c0 + j) * TC_BM + row, g[j]);
           }
         }
+      }
+      if (!ok) {
+        if (lane == 0) {
+          atomicOr(a.err, ERR_TIMEOUT);
+          *abort_flag = 1;
+        }
+        break;
       }
       tc_fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
       if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
+      if (w.unit >= 0) {
+        const int tail = w.tile - P.dp_tiles;
+        __threadfence();
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+          int* ctr = P.counters + tail * 8 + slice;
+          last = atomicAdd(ctr, 1) == P.splits - 1;
+          if (last) *ctr = 0;  // ready for the next launch
+          __threadfence();
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        __syncwarp();
+        if (last) {
+          __threadfence();
+          for (int c0 = wg * HALF; c0 < (wg + 1) * HALF; c0 += 32) {
+            const int64_t rbase = (int64_t)n_tile * BN + c0;
+            epi_load<MODE>(a, i, row_ok, rbase, u, v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) g[j] = 0.0f;
+            for (int sp = 0; sp < P.splits; ++sp) {
+              const float* ps = P.ws + (size_t)(tail * P.splits + sp) * BN * TC_BM;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) g[j] += __ldcg(ps + (size_t)(c0 + j) * TC_BM + row);
+            }
+            epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v);
+          }
+        }
+      }
     }
   }
 
@@ -428,6 +574,10 @@ cudaError_t tc_make_plan(TcPlan* plan, const void* A, int64_t lda, int n, const 
   plan->n_tiles = (B + tile_n - 1) / tile_n;
   plan->num_tiles = plan->m_tiles * plan->n_tiles;
   plan->grid = plan->num_tiles < sms ? plan->num_tiles : sms;
+  plan->sms = sms;
+  plan->ws = nullptr;
+  plan->counters = nullptr;
+  plan->max_splits = 0;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
@@ -464,6 +614,26 @@ static cudaError_t launch_tc_bn(const TcParams& P, int grid, int mode, cudaStrea
   return launch_tc_t<BN, EPI_LAGR>(P, grid, s);
 }
 
+TcSchedule tc_schedule(int num_tiles, int kblocks, int sms, bool can_split, int max_splits) {
+  TcSchedule r;
+  r.dp_tiles = num_tiles;
+  r.splits = 1;
+  r.sk_units = 0;
+  r.grid = num_tiles < sms ? num_tiles : sms;
+  const int tail = num_tiles % sms;
+  if (!can_split || tail == 0) return r;
+  int S = sms / tail;
+  const int kcap = kblocks / TC_MIN_KB_PER_SPLIT;
+  if (S > kcap) S = kcap;
+  if (S > max_splits) S = max_splits;
+  if (S < 2) return r;
+  r.dp_tiles = num_tiles - tail;
+  r.splits = S;
+  r.sk_units = tail * S;
+  r.grid = r.dp_tiles > 0 ? sms : r.sk_units;
+  return r;
+}
+
 cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_override, const EpiArgs& a,
                       int mode, uint64_t timeout_ns, cudaStream_t s) {
   if (!plan.ready) return cudaErrorInvalidValue;
@@ -477,10 +647,14 @@ cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_ov
   P.num_tiles = P.m_tiles * P.n_tiles;
   P.kblocks = (a.n + TC_BK - 1) / TC_BK;
   P.timeout_ns = timeout_ns;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = P.num_tiles < sms ? P.num_tiles : sms;
+  const TcSchedule sch = tc_schedule(P.num_tiles, P.kblocks, plan.sms, plan.ws != nullptr && plan.counters != nullptr,
+                                     plan.max_splits);
+  P.dp_tiles = sch.dp_tiles;
+  P.splits = sch.splits;
+  P.sk_units = sch.sk_units;
+  P.ws = plan.ws;
+  P.counters = plan.counters;
+  const int grid = sch.grid;
   switch (plan.tile_n) {
     case 64: return launch_tc_bn<64>(P, grid, mode, s);
     case 128: return launch_tc_bn<128>(P, grid, mode, s);

@@ -73,9 +73,20 @@ struct TcPlan {
   CUtensorMap mapA;        // A [n][lda] BF16, box 64 x 128, 128B swizzle
   CUtensorMap mapX[3];     // operand buffers [B][ld] BF16 (ping, pong, bits), box 64 x tile_n
   int tile_n;
-  int num_tiles, m_tiles, n_tiles, grid;
+  int num_tiles, m_tiles, n_tiles, grid, sms;
+  // split-K of the tiles left over after whole rounds (optional; both null = no splitting)
+  float* ws;               // >= sms * tile_n * 128 floats
+  int* counters;           // >= sms * 8 ints, zero before the first launch
+  int max_splits;
   bool ready;
 };
+// Work split of one launch: dp_tiles whole tiles round-robin, then the remaining tiles in
+// `splits` K-ranges each (sk_units = tail * splits units, one per CTA).
+struct TcSchedule {
+  int dp_tiles, splits, sk_units, grid;
+};
+TcSchedule tc_schedule(int num_tiles, int kblocks, int sms, bool can_split, int max_splits);
+constexpr int TC_WS_COUNTERS_PER_TILE = 8;
 bool tc_supported();
 cudaError_t tc_make_plan(TcPlan* plan, const void* A, int64_t lda, int n, const void* X0, const void* X1,
                          const void* Xbits, int64_t ldx, int B, int tile_n, std::string* why);

@@ -49,7 +49,9 @@ def test_noalloc_matches_allocating_entry_point_twice_in_a_row(prec):
             (L0, GX0, GY0), (L1, GX1, GY1) = outs
             assert _normwise(GX1, GX0) <= TOL, call
             assert _normwise(GY1, GY0) <= TOL, call
-            assert np.max(np.abs(L1 - L0) / np.maximum(np.abs(L0), 1e-30)) <= TOL, call
+            # L sums per-tile partials with float atomics in no fixed order: compare normwise over
+            # the batch, like every other vector in these tests
+            assert np.max(np.abs(L1 - L0)) / np.max(np.abs(L0)) <= TOL, call
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
