@@ -328,6 +328,52 @@ def run_ours(args):
     return 0
 
 
+SPARSE = {
+    # Max-Cut as QUBO: Erdos-Renyi n=2000 (mean degree 6, +-1), 100x100 torus (+-1), random
+    # 4-regular n=20000 (unit weights)
+    "maxcut-er": (lambda: (2000, W.maxcut_er(2000, 6.0, seed=0)), 256),
+    "maxcut-torus": (lambda: (10000, W.maxcut_torus(100, 100, seed=0)), 512),
+    "maxcut-regular": (lambda: (20000, W.maxcut_regular(20000, 4, seed=0)), 512),
+}
+
+
+def run_sparse(args):
+    """Device loop of a sparse Max-Cut workload (profiling and measurement of the CSR kernel)."""
+    import torch
+    from paper_2509_21064_gb300 import sbo as S
+    from paper_2509_21064_gb300.build import build
+    build()
+    S.lib()
+    make, B = SPARSE[args.workload]
+    n, (i, j, w) = make()
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    prec = {"fp32": S.SBO_FP32, "bf16": S.SBO_BF16, "e4m3": S.SBO_FP8_E4M3}[args.precision]
+    p = W.graph_params("maxcut", restarts=B, iters=10**9, eval_every=10, seed=0)
+    stream = torch.cuda.Stream()
+    P = S.Problem.csr(n, rowptr, col, val, c, precision=prec, stream=stream)
+    P.start(S.params(**p.asdict()))
+    K = 10
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            P.run(K)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            P.run(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    P.sync()
+    ms = e0.elapsed_time(e1) / (args.steps * K)
+    per_elem = 16 if prec == S.SBO_FP32 else 22
+    print(json.dumps({"workload": args.workload, "n": n, "restarts": B, "precision": args.precision,
+                      "us_per_iter": ms * 1e3, "restart_iterations_per_s": B / (ms * 1e-3),
+                      "state_gbs": n * B * per_elem / (ms * 1e-3) / 1e9}), flush=True)
+    P.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,6 +384,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_VARS, help="variables (profiling cases only)")
     ap.add_argument("--restarts", type=int, default=RESTARTS, help="restarts (profiling cases only)")
+    ap.add_argument("--workload", default="dense", choices=["dense"] + sorted(SPARSE),
+                    help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
+                    help="weight/operand precision of a sparse workload")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the device loop only (no e2e, no CPU baseline): for profiling cases")
     args = ap.parse_args()
@@ -345,6 +395,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "dense":
+        return run_sparse(args)
     return run_ours(args)
 
 

@@ -165,13 +165,17 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *   SBO_OPT_USE_GRAPH:  1 (default) replay blocks of K iterations from a CUDA graph; 0 launch
  *                       every kernel directly
  *   SBO_OPT_TILE_N:     restarts per tensor-core tile: 0 auto, 64, 128 or 256
+ *   SBO_OPT_AUTOTUNE:   1 (default): with SBO_OPT_TILE_N = 0, sbo_gda_start times the tcgen05
+ *                       update kernel at every tile width on the run's own buffers and keeps
+ *                       the fastest (cached per n, B, SM count); 0: a fixed rule
  *   SBO_OPT_SPLIT_K:    largest split-K factor for the tensor-core tiles left over after whole
  *                       rounds over the SMs (default 16; 0 or 1 disables splitting).  Split
  *                       tiles are summed in a fixed order, so results do not depend on it.
  *   SBO_OPT_TIMEOUT_US: budget in microseconds of every bounded device-side wait (default
  *                       4,000,000); on expiry the kernel returns early and sbo_sync reports
  *                       SBO_ETIMEOUT */
-enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4, SBO_OPT_SPLIT_K = 5 };
+enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4, SBO_OPT_SPLIT_K = 5,
+       SBO_OPT_AUTOTUNE = 6 };
 sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
 
 /* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL),

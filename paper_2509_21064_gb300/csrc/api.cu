@@ -3,6 +3,9 @@
 // and result read-back.  Every entry point catches its own failures and returns a status.
 #include <algorithm>
 #include <climits>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -69,7 +72,7 @@ struct sbo_problem {
   int64_t* cp64 = nullptr;
   uint32_t* err = nullptr;
   // options
-  int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0, opt_split_k = 16;
+  int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0, opt_split_k = 16, opt_autotune = 1;
   int64_t opt_timeout_us = 4000000;
   // run
   bool started = false;
@@ -297,6 +300,80 @@ sbo_status run_tiny(sbo_problem* p, int64_t steps) {
   return SBO_OK;
 }
 
+sbo_status read_err(sbo_problem* p);
+
+// Widest tile that still gives every SM a tile (else the widest), never wider than needed.
+int heuristic_tile(const sbo_problem* p) {
+  int tn = 256;
+  while (tn > 64 && (int64_t)((p->n + 127) / 128) * ((p->B + tn - 1) / tn) < p->sms) tn /= 2;
+  while (tn > 64 && tn / 2 >= p->B) tn /= 2;
+  return tn;
+}
+
+void attach_workspace(sbo_problem* p, TcPlan* plan) {
+  if (p->tc_ws && p->tc_ctr && p->opt_split_k >= 2) {
+    plan->ws = p->tc_ws;
+    plan->counters = p->tc_ctr;
+    plan->max_splits = p->opt_split_k;
+  }
+}
+
+// Autotuner of the tensor-core tile width: times the update kernel for every candidate width on
+// this run's own buffers (called before x^0 is written, so the trial launches only overwrite
+// state that initialisation rewrites) and keeps the fastest.  Results are cached per
+// (n, B, SM count, split-K limit) for the life of the process.
+sbo_status tune_tile(sbo_problem* p, int* out) {
+  static std::mutex mu;
+  static std::map<std::tuple<int64_t, int, int, int>, int> cache;
+  const auto key = std::make_tuple(p->n, p->B, p->sms, p->opt_split_k);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) { *out = it->second; return SBO_OK; }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SBO_CUDA(cudaEventCreate(&e0));
+  SBO_CUDA(cudaEventCreate(&e1));
+  int best = heuristic_tile(p);
+  float best_ms = 1e30f;
+  EpiArgs a = base_args(p);
+  a.Xin = p->Xop[0];
+  a.Xout = p->Xop[1];
+  a.bits_out = nullptr;
+  sbo_status st = SBO_OK;
+  for (int tn : {64, 128, 256}) {
+    if (tn > 64 && tn / 2 >= p->B) continue;
+    TcPlan pl{};
+    std::string why;
+    if (tc_make_plan(&pl, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, tn, &why) !=
+        cudaSuccess)
+      continue;
+    attach_workspace(p, &pl);
+    cudaError_t e = launch_tc(pl, 0, nullptr, a, EPI_UPDATE, timeout_ns(p), p->stream);
+    const int reps = 3;
+    if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch_tc(pl, 0, nullptr, a, EPI_UPDATE, timeout_ns(p), p->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    p->launches += reps + 1;
+    if (e != cudaSuccess) { st = cuda_fail(e, "autotuner launch"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = tn; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SBO_OK) return st;
+  st = read_err(p);
+  if (st != SBO_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best;
+  }
+  *out = best;
+  return SBO_OK;
+}
+
 sbo_status check_params(const sbo_gda_params* q) {
   if (!q) return fail(SBO_EINVAL, "params is NULL");
   if (q->restarts < 1) return fail(SBO_EINVAL, "restarts must be >= 1");
@@ -505,6 +582,7 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       if (value != 0 && value != 64 && value != 128 && value != 256) return fail(SBO_EINVAL, "tile_n must be 0, 64, 128 or 256");
       p->opt_tile_n = (int)value;
       return SBO_OK;
+    case SBO_OPT_AUTOTUNE: p->opt_autotune = value != 0; return SBO_OK;
     case SBO_OPT_SPLIT_K:
       if (value < 0 || value > 64) return fail(SBO_EINVAL, "split-K factor must be in [0, 64]");
       p->opt_split_k = (int)value;
@@ -555,8 +633,9 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
   const size_t op_elt = p->op_type == OP_F32 ? 4 : 2;
   cudaError_t e = cudaSuccess;
   const bool need_master = ker == KER_TINY || p->op_type != OP_F32;
-  int64_t evals_T = prm->iters / prm->eval_every + 2;
-  p->trace_cap = evals_T + 4096;
+  // min-F trace: one entry per evaluation up to T, plus slack for runs continued beyond T
+  const int64_t evals_T = prm->iters / prm->eval_every + 2;
+  p->trace_cap = std::min<int64_t>(evals_T, 1 << 20) + 4096;
   auto al = [&](void** q, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(q, bytes ? bytes : 1);
   };
@@ -596,6 +675,33 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
   cudaMemsetAsync(p->bestBits, 0, elems, s);
   cudaMemsetAsync(p->n_evals, 0, sizeof(long long), s);
   cudaMemsetAsync(p->t_last, 0, sizeof(long long), s);
+  if (ker == KER_TC) {
+    // split-K workspace (sized for the widest tile): one partial tile per CTA, arrival counters
+    // per tail tile slice
+    if (p->opt_split_k >= 2) {
+      if ((e = dalloc(&p->tc_ws, (size_t)p->sms * 256 * 128)) != cudaSuccess ||
+          (e = dalloc(&p->tc_ctr, (size_t)p->sms * TC_WS_COUNTERS_PER_TILE)) != cudaSuccess) {
+        free_run(p);
+        return e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation of the split-K workspace failed")
+                                              : cuda_fail(e, "cudaMalloc");
+      }
+      cudaMemsetAsync(p->tc_ctr, 0, sizeof(int) * p->sms * TC_WS_COUNTERS_PER_TILE, s);
+    }
+    int tn = p->opt_tile_n;
+    std::string why;
+    if (tn == 0 && p->opt_autotune) {
+      sbo_status st2 = tune_tile(p, &tn);   // runs on the zeroed state, before x^0 is written
+      if (st2 != SBO_OK) { free_run(p); return st2; }
+    } else if (tn == 0) {
+      tn = heuristic_tile(p);
+    }
+    p->tile_n = tn;
+    e = tc_make_plan(&p->plan, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, tn, &why);
+    if (e != cudaSuccess) { free_run(p); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
+    attach_workspace(p, &p->plan);
+  } else {
+    p->tile_n = 0;
+  }
   float* x0d = nullptr;
   if (x0) {
     if ((e = dalloc(&x0d, (size_t)p->B * p->n)) != cudaSuccess) { free_run(p); return cuda_fail(e, "cudaMalloc x0"); }
@@ -609,34 +715,6 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
   ++p->launches;
   if (x0d) { cudaStreamSynchronize(s); dfree(x0d); }
   if (e != cudaSuccess) { free_run(p); return cuda_fail(e, "init launch"); }
-  if (ker == KER_TC) {
-    int tn = p->opt_tile_n;
-    if (tn == 0) {
-      // restarts per tile: the widest tile that still gives every SM a tile, else the widest
-      tn = 256;
-      while (tn > 64 && (int64_t)((p->n + 127) / 128) * ((p->B + tn - 1) / tn) < p->sms) tn /= 2;
-      while (tn > 64 && tn / 2 >= p->B) tn /= 2;
-    }
-    p->tile_n = tn;
-    std::string why;
-    e = tc_make_plan(&p->plan, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, tn, &why);
-    if (e != cudaSuccess) { free_run(p); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
-    if (p->opt_split_k >= 2) {
-      // split-K workspace: one partial tile per CTA, arrival counters per tail tile slice
-      if ((e = dalloc(&p->tc_ws, (size_t)p->sms * tn * 128)) != cudaSuccess ||
-          (e = dalloc(&p->tc_ctr, (size_t)p->sms * TC_WS_COUNTERS_PER_TILE)) != cudaSuccess) {
-        free_run(p);
-        return e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation of the split-K workspace failed")
-                                              : cuda_fail(e, "cudaMalloc");
-      }
-      cudaMemsetAsync(p->tc_ctr, 0, sizeof(int) * p->sms * TC_WS_COUNTERS_PER_TILE, s);
-      p->plan.ws = p->tc_ws;
-      p->plan.counters = p->tc_ctr;
-      p->plan.max_splits = p->opt_split_k;
-    }
-  } else {
-    p->tile_n = 0;
-  }
   p->started = true;
   return SBO_OK;
 }

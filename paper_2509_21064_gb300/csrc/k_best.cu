@@ -27,16 +27,19 @@ __global__ void k_eval_compare(const unsigned long long* __restrict__ F2, long l
   improved[r] = better ? 1 : 0;
 }
 
+// 2-D grid: x runs along the contiguous dimension of the layout, y over the other one.
 __global__ void k_copy_best(const void* __restrict__ bits, int op_type, uint8_t* bestBits,
                             const uint8_t* __restrict__ improved, int n, int B, int64_t ld, int layout) {
-  const int64_t total = (int64_t)n * B;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r, i;
-    if (layout == LAYOUT_RN) { r = e / n; i = e % n; } else { i = e / B; r = e % B; }
-    if (!improved[r]) continue;
-    const int64_t idx = layout == LAYOUT_RN ? r * ld + i : i * ld + r;
-    bestBits[idx] = op_load(bits, idx, op_type) != 0.0f ? 1 : 0;
+  const int64_t inner = layout == LAYOUT_RN ? n : B;
+  const int64_t outer = layout == LAYOUT_RN ? B : n;
+  for (int64_t o = blockIdx.y; o < outer; o += gridDim.y) {
+    if (layout == LAYOUT_RN && !improved[o]) continue;   // whole restart row unchanged
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < inner; q += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t r = layout == LAYOUT_RN ? o : q;
+      if (layout == LAYOUT_NR && !improved[r]) continue;
+      const int64_t idx = o * ld + q;
+      bestBits[idx] = op_load(bits, idx, op_type) != 0.0f ? 1 : 0;
+    }
   }
 }
 
@@ -108,10 +111,11 @@ cudaError_t launch_eval_compare(const unsigned long long* F2, long long* bestF, 
 
 cudaError_t launch_copy_best(const void* bits_op, int op_type, uint8_t* bestBits, const uint8_t* improved,
                              int n, int B, int64_t ld, int layout, cudaStream_t s) {
-  const int64_t total = (int64_t)n * B;
-  const int64_t blocks = (total + 255) / 256;
-  k_copy_best<<<(unsigned)(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, s>>>(bits_op, op_type, bestBits,
-                                                                                improved, n, B, ld, layout);
+  const int64_t inner = layout == LAYOUT_RN ? n : B;
+  const int64_t outer = layout == LAYOUT_RN ? B : n;
+  const int64_t bx = (inner + 255) / 256;
+  dim3 grid((unsigned)(bx < 64 ? bx : 64), (unsigned)(outer < 65535 ? outer : 65535));
+  k_copy_best<<<grid, 256, 0, s>>>(bits_op, op_type, bestBits, improved, n, B, ld, layout);
   return cudaGetLastError();
 }
 

@@ -1,11 +1,14 @@
 // Sparse form: CSR SpMM G = A X fused with the PDBO epilogue, for graphs (Max-Cut, MIS).
 //
-// State is variable-major: element (i, r) at [i * ld + r], so the B restarts of one variable
-// are contiguous.  One warp owns one row i of A and a chunk of 32*V restarts: lane l handles
-// restarts rbase + l + 32 v (v < V), so every gather X[j][...] of a neighbour j is a run of
-// 32 consecutive elements per v (one 128-byte line for FP32, 64 bytes for BF16).  Column
-// indices and weights are warp-uniform loads.  Warps stride over rows; in EPI_EVAL each lane
-// keeps per-restart int64 partial sums of 2F across its rows and adds them once at the end.
+// State is variable-major: element (i, r) at [i * ld + r] (ld a multiple of 8), so the B
+// restarts of one variable are contiguous.  One warp owns one row i of A and a chunk of 128*NV
+// restarts; lane l holds the 4 consecutive restarts rbase + 128 v + 4 l .. +3 (v < NV), so each
+// gather X[j][...] of a neighbour j is one 512-byte (FP32) or 256-byte (BF16) run per v.  The
+// row's column indices and weights are loaded 32 at a time, one per lane, and broadcast with
+// shuffles, so the gathers of consecutive neighbours do not wait on each other; the row's own
+// x and y are loaded before the gathers.  Warps stride over rows; in EPI_EVAL every lane keeps
+// per-restart int64 partial sums of 2F over its rows; a block sums its warps' partials in shared
+// memory and adds one value per restart to the global accumulator.
 #include "sbo_internal.h"
 
 namespace sbo {
@@ -20,93 +23,168 @@ __device__ __forceinline__ float load_val(const void* val, int64_t e, int vt) {
   return static_cast<float>(q);
 }
 
-template <int MODE, int V, int OPT>
+// 4 consecutive operand values (FP32: one 16-byte load; BF16: one 8-byte load).
+template <int OPT>
+__device__ __forceinline__ float4 load4(const void* p, int64_t idx) {
+  if (OPT == OP_F32) return __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(p) + idx));
+  const uint2 raw = __ldg(reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(p) + idx));
+  const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+  const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+  return make_float4(__low2float(lo), __high2float(lo), __low2float(hi), __high2float(hi));
+}
+template <int OPT>
+__device__ __forceinline__ void store4(void* p, int64_t idx, float4 v) {
+  if (OPT == OP_F32) {
+    *reinterpret_cast<float4*>(static_cast<float*>(p) + idx) = v;
+  } else {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+    uint2 raw;
+    raw.x = *reinterpret_cast<uint32_t*>(&lo);
+    raw.y = *reinterpret_cast<uint32_t*>(&hi);
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(p) + idx) = raw;
+  }
+}
+__device__ __forceinline__ float comp(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+__device__ __forceinline__ void set_comp(float4& v, int k, float s) {
+  if (k == 0) v.x = s; else if (k == 1) v.y = s; else if (k == 2) v.z = s; else v.w = s;
+}
+
+template <int MODE, int NV, int OPT>
 __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                              const void* __restrict__ val, int vt, EpiArgs a) {
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
   const int64_t warp0 = (int64_t)blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
-  const int64_t rbase = (int64_t)blockIdx.y * 32 * V;
+  const int64_t rbase = (int64_t)blockIdx.y * 128 * NV + 4 * lane;
   const int n = a.n, B = a.B;
   const int64_t ld = a.ld;
   const void* Xin = a.Xin;
-  long long f2[V];
+  long long f2[NV][4];
 #pragma unroll
-  for (int v = 0; v < V; ++v) f2[v] = 0;
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f2[v][k] = 0;
 
   for (int64_t i = warp0; i < n; i += nwarps) {
-    float acc[V];
+    // the row's own state first: independent of the gathers
+    float4 xo[NV], yo[NV];
 #pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = 0.0f;
-    const int e0 = rowptr[i], e1 = rowptr[i + 1];
-    for (int e = e0; e < e1; ++e) {
-      const int64_t j = __ldg(col + e);
-      const float w = load_val(val, e, vt);
-      const int64_t base = j * ld + rbase + lane;
+    for (int v = 0; v < NV; ++v) {
+      const int64_t r0 = rbase + 128 * v;
+      xo[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+      yo[v] = xo[v];
+      if (r0 < B) {
+        const int64_t idx = i * ld + r0;
+        if (MODE == EPI_UPDATE) {
+          xo[v] = a.Xm ? *reinterpret_cast<const float4*>(a.Xm + idx) : load4<OP_F32>(Xin, idx);
+          yo[v] = *reinterpret_cast<const float4*>(a.Y + idx);
+        } else {
+          xo[v] = load4<OPT>(Xin, idx);   // EPI_EVAL: the row's own bits
+        }
+      }
+    }
+    float4 acc[NV];
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        if (rbase + lane + 32 * v < B) {
-          const float xv = OPT == OP_F32 ? __ldg(static_cast<const float*>(Xin) + base + 32 * v)
-                                         : __bfloat162float(static_cast<const __nv_bfloat16*>(Xin)[base + 32 * v]);
-          acc[v] = fmaf(w, xv, acc[v]);
+    for (int v = 0; v < NV; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e0 = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1);
+    for (int eb = e0; eb < e1; eb += 32) {
+      const int k = eb + lane;
+      const int mycol = k < e1 ? __ldg(col + k) : 0;
+      const float myval = k < e1 ? load_val(val, k, vt) : 0.0f;
+      const int cnt = min(32, e1 - eb);
+#pragma unroll 4
+      for (int q = 0; q < cnt; ++q) {
+        const int64_t j = __shfl_sync(0xffffffffu, mycol, q);
+        const float w = __shfl_sync(0xffffffffu, myval, q);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int64_t r0 = rbase + 128 * v;
+          if (r0 < B) {
+            const float4 xv = load4<OPT>(Xin, j * ld + r0);
+            acc[v].x = fmaf(w, xv.x, acc[v].x);
+            acc[v].y = fmaf(w, xv.y, acc[v].y);
+            acc[v].z = fmaf(w, xv.z, acc[v].z);
+            acc[v].w = fmaf(w, xv.w, acc[v].w);
+          }
         }
       }
     }
     const float cpi = a.cp[i];
+    const long long cp2 = MODE == EPI_EVAL ? 2 * (long long)a.cp64[i] : 0;
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const int64_t r = rbase + lane + 32 * v;
-      if (r >= B) continue;
-      const int64_t idx = i * ld + r;
+    for (int v = 0; v < NV; ++v) {
+      const int64_t r0 = rbase + 128 * v;
+      if (r0 >= B) continue;
+      const int64_t idx = i * ld + r0;
       if (MODE == EPI_UPDATE) {
-        const float x = a.Xm ? a.Xm[idx] : static_cast<const float*>(Xin)[idx];
-        const float y = a.Y[idx];
-        const float d = acc[v] + cpi + y * (2.0f * x - 1.0f);
-        float yn;
-        const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
-        if (a.Xm) a.Xm[idx] = xn;
-        op_store(a.Xout, idx, xn, OPT);
-        a.Y[idx] = yn;
-        if (a.bits_out) op_store(a.bits_out, idx, xn > 0.5f ? 1.0f : 0.0f, OPT);
+        float4 xn4, yn4, b4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float x = comp(xo[v], k), y = comp(yo[v], k);
+          const float d = comp(acc[v], k) + cpi + y * (2.0f * x - 1.0f);
+          float yn;
+          const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+          const bool live = r0 + k < B;   // padding restarts keep their zeros
+          set_comp(xn4, k, live ? xn : 0.0f);
+          set_comp(yn4, k, live ? yn : 0.0f);
+          set_comp(b4, k, (live && xn > 0.5f) ? 1.0f : 0.0f);
+        }
+        if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = xn4;
+        store4<OPT>(a.Xout, idx, xn4);
+        *reinterpret_cast<float4*>(a.Y + idx) = yn4;
+        if (a.bits_out) store4<OPT>(a.bits_out, idx, b4);
       } else if (MODE == EPI_EVAL) {
-        const float b = op_load(Xin, idx, OPT);
-        if (b != 0.0f) f2[v] += (long long)acc[v] + 2 * a.cp64[i];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (r0 + k < B && comp(xo[v], k) != 0.0f) f2[v][k] += (long long)comp(acc[v], k) + cp2;
       }
     }
   }
   if (MODE == EPI_EVAL) {
+    // the block's warps cover the same restarts: sum them in shared memory, then one atomic
+    // per restart per block
+    __shared__ unsigned long long red[128 * NV];
+    for (int t = threadIdx.x; t < 128 * NV; t += blockDim.x) red[t] = 0ull;
+    __syncthreads();
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      const int64_t r = rbase + lane + 32 * v;
-      if (r < B && f2[v] != 0) atomicAdd(&a.F2[r], (unsigned long long)f2[v]);
-    }
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (f2[v][k] != 0) atomicAdd(&red[128 * v + 4 * lane + k], (unsigned long long)f2[v][k]);
+    __syncthreads();
+    const int64_t rb = (int64_t)blockIdx.y * 128 * NV;
+    for (int t = threadIdx.x; t < 128 * NV; t += blockDim.x)
+      if (rb + t < B && red[t] != 0ull) atomicAdd(&a.F2[rb + t], red[t]);
   }
 }
 
 template <int MODE, int OPT>
 static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const void* val, int vt,
                                 const EpiArgs& a, cudaStream_t s) {
-  int V = 1;
-  while (V < 8 && 32 * V < a.B) V *= 2;
-  const int64_t chunks = (a.B + 32 * V - 1) / (32 * V);
+  // at most 256 restarts per warp: fewer registers, more warps in flight (this kernel is bound
+  // by memory latency)
+  int NV = 1;
+  while (NV < 2 && 128 * NV < a.B) NV *= 2;
+  const int64_t chunks = (a.B + 128 * NV - 1) / (128 * NV);
   const int warps_per_block = 8;
   int64_t want = (a.n + warps_per_block - 1) / warps_per_block;
-  const int64_t cap = (int64_t)152 * 16 / (chunks > 0 ? chunks : 1) + 1;  // EVAL: bound atomics
-  if (MODE == EPI_EVAL && want > cap) want = cap;
-  if (want > 65535 * 8) want = 65535 * 8;
+  if (MODE == EPI_EVAL) {
+    const int64_t cap = (int64_t)152 * 4 / (chunks > 0 ? chunks : 1) + 1;  // bounds the closing atomics
+    if (want > cap) want = cap;
+  }
+  if (want > 65535) want = 65535;
   dim3 grid((unsigned)want, (unsigned)chunks);
-  switch (V) {
+  switch (NV) {
     case 1: k_csr<MODE, 1, OPT><<<grid, 256, 0, s>>>(rowptr, col, val, vt, a); break;
-    case 2: k_csr<MODE, 2, OPT><<<grid, 256, 0, s>>>(rowptr, col, val, vt, a); break;
-    case 4: k_csr<MODE, 4, OPT><<<grid, 256, 0, s>>>(rowptr, col, val, vt, a); break;
-    default: k_csr<MODE, 8, OPT><<<grid, 256, 0, s>>>(rowptr, col, val, vt, a); break;
+    default: k_csr<MODE, 2, OPT><<<grid, 256, 0, s>>>(rowptr, col, val, vt, a); break;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
                        const EpiArgs& a, int op_type, int mode, cudaStream_t s) {
+  if (a.ld % 8 != 0) return cudaErrorInvalidValue;  // vector accesses need 16-byte rows
   if (mode == EPI_UPDATE) {
     return op_type == OP_F32 ? launch_csr_v<EPI_UPDATE, OP_F32>(rowptr, col, val, val_type, a, s)
                              : launch_csr_v<EPI_UPDATE, OP_BF16>(rowptr, col, val, val_type, a, s);

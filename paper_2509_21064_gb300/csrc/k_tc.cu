@@ -89,7 +89,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
                                           const volatile int* abort_flag) {
   uint32_t spins = 0;
   while (!mbar_try_wait(bar, parity)) {
-    if ((++spins & 255u) == 0u) {
+    if ((++spins & 31u) == 0u) {
       if (*abort_flag) return false;
       if (globaltimer_ns() > deadline) return false;
     }

@@ -1,0 +1,39 @@
+"""Failure detection on the GPU without a fault: every device-side wait of the tcgen05 kernel is
+bounded; with a budget far shorter than the work, the waits give up, the kernel drains its own
+copies and MMAs, frees its tensor memory and returns, and the host reads SBO_ETIMEOUT.  The
+context stays usable: the same handle then runs normally and matches a fresh handle exactly."""
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2509_21064_gb300 import sbo as S
+from paper_2509_21064_gb300.build import build as build_lib
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_waits_report_timeout_and_the_context_survives():
+    build_lib()
+    n, B = 8192, 1024
+    Q, c = W.dense_qubo(n, seed=4)
+    p = W.dense_params(Q, restarts=B, iters=100, eval_every=10, seed=2)
+    prm = S.params(**p.asdict())
+    with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
+        P.set_option(S.SBO_OPT_TILE_N, 128)
+        P.set_option(S.SBO_OPT_TIMEOUT_US, 1)          # 1 us: far below one launch
+        P.start(prm)
+        P.run(3)
+        with pytest.raises(S.SboError) as e:
+            P.sync()
+        assert e.value.status == S.SBO_ETIMEOUT
+        P.sync()                                        # the error word was cleared
+        P.set_option(S.SBO_OPT_TIMEOUT_US, 4_000_000)
+        P.start(prm)
+        P.run(20)
+        X, Y = P.state()
+    with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P2:
+        P2.set_option(S.SBO_OPT_TILE_N, 128)
+        P2.start(prm)
+        P2.run(20)
+        X2, Y2 = P2.state()
+    assert np.array_equal(X, X2) and np.array_equal(Y, Y2)
