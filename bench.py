@@ -374,6 +374,46 @@ def run_sparse(args):
     return 0
 
 
+def run_hetero(args):
+    """Grouped run over 64 dense QUBO instances of uneven size (n ~ U{500..5000}, density ~
+    U[0.01, 1], B = 128 each): one persistent tcgen05 launch per iteration for all of them."""
+    import torch
+    from paper_2509_21064_gb300 import sbo as S
+    from paper_2509_21064_gb300.build import build
+    build()
+    S.lib()
+    insts = W.heterogeneous_qubos(64, seed=0, n_lo=500, n_hi=5000)
+    B, K = 128, 10
+    prms = [S.params(**W.dense_params(Q, restarts=B, iters=10**9, eval_every=K, seed=k).asdict())
+            for k, (Q, c) in enumerate(insts)]
+    stream = torch.cuda.Stream()
+    members = [S.Problem.dense(Q, c, precision=S.SBO_BF16, stream=stream) for Q, c in insts]
+    G = S.Group(members, stream=stream)
+    G.start(prms)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            G.run(K)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            G.run(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    G.sync()
+    ms = e0.elapsed_time(e1) / (args.steps * K)
+    flops = sum(2.0 * Q.shape[0] ** 2 * B for Q, _ in insts)
+    print(json.dumps({"workload": "64 dense QUBO instances, n U{500..5000}, density U[0.01,1], B=128",
+                      "sum_n2": int(sum(Q.shape[0] ** 2 for Q, _ in insts)), "us_per_iter": ms * 1e3,
+                      "restart_iterations_per_s": 64 * B / (ms * 1e-3), "tflops": flops / (ms * 1e-3) / 1e12}),
+          flush=True)
+    G.close()
+    for P in members:
+        P.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,7 +424,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_VARS, help="variables (profiling cases only)")
     ap.add_argument("--restarts", type=int, default=RESTARTS, help="restarts (profiling cases only)")
-    ap.add_argument("--workload", default="dense", choices=["dense"] + sorted(SPARSE),
+    ap.add_argument("--workload", default="dense", choices=["dense", "hetero"] + sorted(SPARSE),
                     help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
                     help="weight/operand precision of a sparse workload")
@@ -395,6 +435,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "hetero":
+        return run_hetero(args)
     if args.workload != "dense":
         return run_sparse(args)
     return run_ours(args)

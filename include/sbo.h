@@ -183,6 +183,26 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
 sbo_status sbo_info(const sbo_problem* p, int64_t* n, int32_t* restarts, int32_t* kernel,
                     int32_t* tile_n, int64_t* t);
 
+/* ---- grouped runs (heterogeneous batches) ---------------------------------------------------
+ * A group advances several dense BF16 problems of different n together: every iteration is
+ * one persistent tcgen05 launch over the tiles of all members (ordered by decreasing n), and
+ * every evaluation one grouped launch plus each member's best bookkeeping (section 4.2 per
+ * member).  Members stay owned by the caller and keep their own state and results: read them
+ * with sbo_best / sbo_state / sbo_trace on each member after sbo_group_sync.
+ * sbo_group_create: count >= 1 distinct dense BF16 problems; stream as for sbo_create_dense.
+ * sbo_group_start: prms[count]; members share iters and eval_every (else SBO_EINVAL); starts
+ *   every member (x^0 from its seed) on the group's tile width.
+ * sbo_group_run / sbo_group_sync: as sbo_gda_run / sbo_sync for the whole group.
+ * sbo_group_set_option: SBO_OPT_USE_GRAPH, SBO_OPT_TILE_N (default 128; before start). */
+typedef struct sbo_group sbo_group;
+sbo_status sbo_group_create(int32_t count, sbo_problem* const* problems, void* stream, sbo_group** out);
+sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms);
+sbo_status sbo_group_run(sbo_group* g, int64_t iters);
+sbo_status sbo_group_sync(sbo_group* g);
+sbo_status sbo_group_set_option(sbo_group* g, int32_t option, int64_t value);
+int64_t sbo_group_launch_count(const sbo_group* g);
+void sbo_group_destroy(sbo_group* g);  /* NULL-safe; does not destroy the members */
+
 /* Kernel launches enqueued by this handle since creation (every kernel of the library). */
 int64_t sbo_launch_count(const sbo_problem* p);
 

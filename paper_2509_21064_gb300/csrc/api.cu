@@ -1006,3 +1006,258 @@ bool dense_view(sbo_problem* p, DenseView* v) {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 }  // namespace sbo
+
+// =============================================================================================
+// Grouped runs: several dense BF16 problems advanced together, one persistent tcgen05 launch
+// per iteration over the tiles of every instance.
+struct sbo_group {
+  std::vector<sbo_problem*> members;  // not owned
+  std::vector<int> order;             // member indices by decreasing n (instance table order)
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int tile_n = 128;
+  TcInst* d_insts = nullptr;
+  int num_tiles = 0;
+  bool started = false;
+  int64_t T = 0, K = 1;
+  int64_t t = 0, t_last_eval = 0, n_evals_host = 0;
+  int cur = 0;
+  int opt_graph = 1;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int64_t launches = 0;
+};
+
+namespace {
+
+void group_free_graphs(sbo_group* g) {
+  for (auto& x : g->gexec)
+    if (x) { cudaGraphExecDestroy(x); x = nullptr; }
+}
+
+cudaError_t group_step(sbo_group* g, bool write_bits, cudaStream_t s) {
+  ++g->launches;
+  const int variant = 2 * g->cur + (write_bits ? 1 : 0);
+  cudaError_t e = launch_tc_group(g->d_insts, (int)g->members.size(), g->num_tiles, g->tile_n, EPI_UPDATE, variant,
+                                  timeout_ns(g->members[0]), s);
+  g->cur ^= 1;
+  return e;
+}
+
+cudaError_t group_eval(sbo_group* g, int64_t add, cudaStream_t s) {
+  cudaError_t e = launch_tc_group(g->d_insts, (int)g->members.size(), g->num_tiles, g->tile_n, EPI_EVAL, 4,
+                                  timeout_ns(g->members[0]), s);
+  ++g->launches;
+  for (sbo_problem* p : g->members) {
+    if (e != cudaSuccess) break;
+    e = launch_eval_compare(p->F2, p->bestF, p->bestT, p->improved, p->evalF, p->B, p->t_last, add, s);
+    if (e == cudaSuccess)
+      e = launch_copy_best(p->bits, p->op_type, p->bestBits, p->improved, (int)p->n, p->B, p->ld, p->layout, s);
+    if (e == cudaSuccess)
+      e = launch_eval_finalize(p->F2, p->evalF, p->trace, p->n_evals, p->trace_cap, p->B, p->t_last, add, s);
+    g->launches += 3;
+  }
+  return e;
+}
+
+sbo_status group_capture(sbo_group* g, int parity) {
+  const int saved = g->cur;
+  const int64_t saved_l = g->launches;
+  g->cur = parity;
+  cudaGraph_t gr = nullptr;
+  SBO_CUDA(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = cudaSuccess;
+  for (int64_t s = 0; s < g->K && err == cudaSuccess; ++s) err = group_step(g, s + 1 == g->K, g->cap_stream);
+  if (err == cudaSuccess) err = group_eval(g, g->K, g->cap_stream);
+  cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &gr);
+  g->cur = saved;
+  g->launches = saved_l;
+  if (err != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    return cuda_fail(err, "launch during graph capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  cudaError_t e3 = cudaGraphInstantiate(&g->gexec[parity], gr, 0);
+  cudaGraphDestroy(gr);
+  if (e3 != cudaSuccess) return cuda_fail(e3, "cudaGraphInstantiate");
+  return SBO_OK;
+}
+
+// Keep every member's own counters in step with the group's (so sbo_best, sbo_state, ... and
+// later single-problem runs see a consistent state).
+void group_sync_members(sbo_group* g) {
+  for (sbo_problem* p : g->members) {
+    p->t = g->t;
+    p->t_last_eval = g->t_last_eval;
+    p->n_evals_host = g->n_evals_host;
+    p->cur = g->cur;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+sbo_status sbo_group_create(int32_t count, sbo_problem* const* problems, void* stream, sbo_group** out) {
+  g_last_error.clear();
+  if (!out) return fail(SBO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !problems) return fail(SBO_EINVAL, "count must be >= 1 and problems non-NULL");
+  for (int32_t k = 0; k < count; ++k) {
+    if (!problems[k]) return fail(SBO_EINVAL, "a member problem is NULL");
+    if (problems[k]->fmt != FMT_DENSE || problems[k]->prec != SBO_BF16)
+      return fail(SBO_EINVAL, "grouped runs take dense BF16 problems");
+    for (int32_t q = 0; q < k; ++q)
+      if (problems[q] == problems[k]) return fail(SBO_EINVAL, "a problem appears twice in the group");
+  }
+  if (!tc_supported()) return fail(SBO_ECUDA, "grouped runs need a compute capability 10.3 device");
+  sbo_group* g = new (std::nothrow) sbo_group();
+  if (!g) return fail(SBO_ENOMEM, "host allocation failed");
+  g->members.assign(problems, problems + count);
+  g->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaStreamCreate"); }
+  *out = g;
+  return SBO_OK;
+}
+
+sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms) {
+  g_last_error.clear();
+  if (!g || !prms) return fail(SBO_EINVAL, "group or params is NULL");
+  const size_t cnt = g->members.size();
+  for (size_t k = 0; k < cnt; ++k) {
+    sbo_status st = check_params(&prms[k]);
+    if (st != SBO_OK) return st;
+    if (prms[k].iters != prms[0].iters || prms[k].eval_every != prms[0].eval_every)
+      return fail(SBO_EINVAL, "members of a group share iters and eval_every");
+  }
+  group_free_graphs(g);
+  if (g->d_insts) { cudaStreamSynchronize(g->stream); cudaFree(g->d_insts); g->d_insts = nullptr; }
+  g->started = false;
+  // start every member on the group's tile width, then build the instance table
+  for (size_t k = 0; k < cnt; ++k) {
+    sbo_problem* p = g->members[k];
+    p->opt_kernel = KER_TC;
+    p->opt_tile_n = g->tile_n;
+    p->opt_split_k = 0;
+    sbo_status st = sbo_gda_start(p, &prms[k], nullptr);
+    if (st != SBO_OK) return st;
+    SBO_CUDA(cudaStreamSynchronize(p->stream));
+  }
+  g->order.resize(cnt);
+  for (size_t k = 0; k < cnt; ++k) g->order[k] = (int)k;
+  std::stable_sort(g->order.begin(), g->order.end(),
+                   [&](int a, int b) { return g->members[a]->n > g->members[b]->n; });
+  std::vector<TcInst> tab(cnt);
+  int tiles = 0;
+  for (size_t q = 0; q < cnt; ++q) {
+    sbo_problem* p = g->members[g->order[q]];
+    TcInst& I = tab[q];
+    std::memset(&I, 0, sizeof(I));
+    I.mapA = p->plan.mapA;
+    for (int k = 0; k < 3; ++k) I.mapX[k] = p->plan.mapX[k];
+    for (int cur = 0; cur < 2; ++cur)
+      for (int wb = 0; wb < 2; ++wb) {
+        EpiArgs a = base_args(p);
+        a.Xin = p->Xop[cur];
+        a.Xout = p->Xop[cur ^ 1];
+        a.bits_out = wb ? p->bits : nullptr;
+        I.epi[2 * cur + wb] = a;
+      }
+    EpiArgs ev = base_args(p);
+    ev.Xin = p->bits;
+    I.epi[4] = ev;
+    I.n_tiles = (p->B + g->tile_n - 1) / g->tile_n;
+    I.kblocks = (int)((p->n + 63) / 64);
+    I.tile_begin = tiles;
+    tiles += (int)((p->n + 127) / 128) * I.n_tiles;
+  }
+  g->num_tiles = tiles;
+  SBO_CUDA(cudaMalloc(&g->d_insts, sizeof(TcInst) * cnt));
+  SBO_CUDA(cudaMemcpy(g->d_insts, tab.data(), sizeof(TcInst) * cnt, cudaMemcpyHostToDevice));
+  g->T = prms[0].iters;
+  g->K = prms[0].eval_every;
+  g->t = g->t_last_eval = g->n_evals_host = 0;
+  g->cur = 0;
+  g->started = true;
+  group_sync_members(g);
+  return SBO_OK;
+}
+
+sbo_status sbo_group_run(sbo_group* g, int64_t iters) {
+  g_last_error.clear();
+  if (!g) return fail(SBO_EINVAL, "group is NULL");
+  if (!g->started) return fail(SBO_ENOTREADY, "sbo_group_start has not been called");
+  if (iters < 0) return fail(SBO_EINVAL, "iters must be >= 0");
+  const int64_t t_end = g->t + iters;
+  while (g->t < t_end) {
+    int64_t nx = (g->t / g->K + 1) * g->K;
+    if (g->T > g->t && g->T < nx) nx = g->T;
+    const int64_t stop = std::min(nx, t_end);
+    const int64_t steps = stop - g->t;
+    const bool eval_here = stop == nx;
+    if (g->opt_graph && eval_here && steps == g->K && g->t % g->K == 0 && g->t_last_eval == g->t) {
+      const int par = g->cur;
+      if (!g->gexec[par]) {
+        sbo_status st = group_capture(g, par);
+        if (st != SBO_OK) return st;
+      }
+      cudaError_t e = cudaGraphLaunch(g->gexec[par], g->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+      g->launches += g->K + 1 + 3 * (int64_t)g->members.size();
+      if (g->K & 1) g->cur ^= 1;
+      g->t += g->K;
+      g->t_last_eval = g->t;
+      ++g->n_evals_host;
+    } else {
+      for (int64_t s = 0; s < steps; ++s) {
+        cudaError_t e = group_step(g, eval_here && s + 1 == steps, g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "grouped step launch");
+      }
+      g->t += steps;
+      if (eval_here) {
+        cudaError_t e = group_eval(g, g->t - g->t_last_eval, g->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "grouped evaluation launch");
+        g->t_last_eval = g->t;
+        ++g->n_evals_host;
+      }
+    }
+  }
+  group_sync_members(g);
+  return SBO_OK;
+}
+
+sbo_status sbo_group_sync(sbo_group* g) {
+  g_last_error.clear();
+  if (!g) return fail(SBO_EINVAL, "group is NULL");
+  SBO_CUDA(cudaStreamSynchronize(g->stream));
+  for (sbo_problem* p : g->members) {
+    sbo_status st = read_err(p);
+    if (st != SBO_OK) return st;
+  }
+  return SBO_OK;
+}
+
+sbo_status sbo_group_set_option(sbo_group* g, int32_t option, int64_t value) {
+  g_last_error.clear();
+  if (!g) return fail(SBO_EINVAL, "group is NULL");
+  if (option == SBO_OPT_USE_GRAPH) { g->opt_graph = value != 0; return SBO_OK; }
+  if (option == SBO_OPT_TILE_N) {
+    if (value != 64 && value != 128 && value != 256) return fail(SBO_EINVAL, "tile_n must be 64, 128 or 256");
+    g->tile_n = (int)value;
+    return SBO_OK;
+  }
+  return fail(SBO_EINVAL, "groups take SBO_OPT_USE_GRAPH and SBO_OPT_TILE_N");
+}
+
+int64_t sbo_group_launch_count(const sbo_group* g) { return g ? g->launches : 0; }
+
+void sbo_group_destroy(sbo_group* g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  group_free_graphs(g);
+  if (g->d_insts) cudaFree(g->d_insts);
+  if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  delete g;
+}
+
+}  // extern "C"

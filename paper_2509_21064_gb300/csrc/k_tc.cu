@@ -44,6 +44,10 @@ struct TcParams {
   float* ws;       // split-K partial tiles [sk_units][BN][128] (scratch)
   int* counters;   // arrivals per (tail tile, epilogue warp slice), zero between launches (scratch)
   uint64_t timeout_ns;
+  // grouped launch over several instances (the maps and epi above are then unused)
+  const TcInst* insts;
+  int n_insts;
+  int epi_variant;  // index into TcInst::epi for this launch
 };
 
 template <int BN>
@@ -158,9 +162,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // k-blocks [s KB/S, (s+1) KB/S) of tail tile u / S, s = u % S).
 struct TcWork {
   int tile, kb0, kb1, unit;  // unit < 0: whole tile
+  int inst;                  // grouped launch: instance of the tile; tile is then local to it
 };
+template <bool GROUPED>
 __device__ __forceinline__ bool tc_work(const TcParams& P, int j, TcWork& w) {
   const int G = gridDim.x, c = blockIdx.x;
+  if (GROUPED) {
+    // tiles of all instances in one list (instances ordered by decreasing n), round-robin
+    const int t = c + j * G;
+    if (t >= P.num_tiles) return false;
+    int k = 0;
+    while (k + 1 < P.n_insts && P.insts[k + 1].tile_begin <= t) ++k;
+    w.inst = k;
+    w.tile = t - P.insts[k].tile_begin;
+    w.kb0 = 0;
+    w.kb1 = P.insts[k].kblocks;
+    w.unit = -1;
+    return true;
+  }
+  w.inst = 0;
   const int ndp = c < P.dp_tiles ? (P.dp_tiles - c + G - 1) / G : 0;
   if (j < ndp) {
     w.tile = c + j * G;
@@ -269,7 +289,7 @@ __device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_
   }
 }
 
-template <int BN, int MODE>
+template <int BN, int MODE, bool GROUPED>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ TcParams P) {
   using C = TcCfg<BN>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -301,8 +321,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tma_prefetch_map(&P.mapA);
-    tma_prefetch_map(&P.mapX);
+    if (!GROUPED) {
+      tma_prefetch_map(&P.mapA);
+      tma_prefetch_map(&P.mapX);
+    }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -324,22 +346,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
       uint32_t issued_mask = 0, issued_parity = 0;
       bool ok = true;
       TcWork w;
-      for (int j = 0; ok && tc_work(P, j, w); ++j) {
-        const int m_tile = w.tile / P.n_tiles, n_tile = w.tile % P.n_tiles;
+      for (int j = 0; ok && tc_work<GROUPED>(P, j, w); ++j) {
+        const int nt = GROUPED ? P.insts[w.inst].n_tiles : P.n_tiles;
+        const CUtensorMap* mapA = GROUPED ? &P.insts[w.inst].mapA : &P.mapA;
+        const CUtensorMap* mapX =
+            GROUPED ? &P.insts[w.inst].mapX[MODE == EPI_EVAL ? 2 : (P.epi_variant >> 1)] : &P.mapX;
+        const int m_tile = w.tile / nt, n_tile = w.tile % nt;
         for (int kb = w.kb0; kb < w.kb1; ++kb) {
           if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, deadline, vabort)) { ok = false; break; }
           const uint32_t fb = smem_u32(&full_bar[stage]);
           mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
           uint8_t* sa = tiles + stage * C::STAGE_BYTES;
-          tma_load_2d(smem_u32(sa), &P.mapA, fb, kb * TC_BK, m_tile * TC_BM);
-          tma_load_2d(smem_u32(sa + C::A_BYTES), &P.mapX, fb, kb * TC_BK, n_tile * BN);
+          tma_load_2d(smem_u32(sa), mapA, fb, kb * TC_BK, m_tile * TC_BM);
+          tma_load_2d(smem_u32(sa + C::A_BYTES), mapX, fb, kb * TC_BK, n_tile * BN);
           issued_mask |= 1u << stage;
           issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
           if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
         }
       }
       if (!ok) {
-        atomicOr(P.epi.err, ERR_TIMEOUT);
+        atomicOr(GROUPED ? P.insts[0].epi[0].err : P.epi.err, ERR_TIMEOUT);
         *abort_flag = 1;
         // drain: every copy this thread issued completes on its full barrier
         const uint64_t dl2 = globaltimer_ns() + 200000000ull;
@@ -357,7 +383,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
       uint32_t acc_phase = 0;
       bool ok = true, issued_any = false;
       TcWork w;
-      for (int j = 0; ok && tc_work(P, j, w); ++j) {
+      for (int j = 0; ok && tc_work<GROUPED>(P, j, w); ++j) {
         if (!mbar_wait(smem_u32(&tempty_bar[acc]), acc_phase ^ 1u, deadline, vabort)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
@@ -380,7 +406,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
         if (++acc == 2) { acc = 0; acc_phase ^= 1u; }
       }
       if (!ok) {
-        atomicOr(P.epi.err, ERR_TIMEOUT);
+        atomicOr(GROUPED ? P.insts[0].epi[0].err : P.epi.err, ERR_TIMEOUT);
         *abort_flag = 1;
         if (issued_any) {
           tc_commit(smem_u32(drain_bar));
@@ -403,12 +429,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
     const int wg = (warp - 4) >> 2;
     const int wq = warp & 3;
     const int slice = wg * 4 + wq;
-    const EpiArgs& a = P.epi;
     int acc = 0;
     uint32_t acc_phase = 0;
     TcWork w;
-    for (int jw = 0; tc_work(P, jw, w); ++jw) {
-      const int m_tile = w.tile / P.n_tiles, n_tile = w.tile % P.n_tiles;
+    for (int jw = 0; tc_work<GROUPED>(P, jw, w); ++jw) {
+      const EpiArgs& a = GROUPED ? P.insts[w.inst].epi[P.epi_variant] : P.epi;
+      const int nt = GROUPED ? P.insts[w.inst].n_tiles : P.n_tiles;
+      const int m_tile = w.tile / nt, n_tile = w.tile % nt;
       const int row = wq * 32 + lane;
       const int64_t i = (int64_t)m_tile * TC_BM + row;
       const bool row_ok = i < a.n;
@@ -548,8 +575,14 @@ cudaError_t tc_make_operand_map(CUtensorMap* m, const void* X, int64_t ldx, int 
 
 template <int BN, int MODE>
 static cudaError_t set_attr() {
-  return cudaFuncSetAttribute(k_tc<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(k_tc<BN, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcCfg<BN>::SMEM);
+  if (e == cudaSuccess && MODE != EPI_LAGR)
+    e = cudaFuncSetAttribute(k_tc<BN, MODE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN>::SMEM);
+  return e;
 }
+
+static cudaError_t ensure_attrs();
 
 cudaError_t tc_make_plan(TcPlan* plan, const void* A, int64_t lda, int n, const void* X0, const void* X1,
                          const void* Xbits, int64_t ldx, int B, int tile_n, std::string* why) {
@@ -578,21 +611,7 @@ cudaError_t tc_make_plan(TcPlan* plan, const void* A, int64_t lda, int n, const 
   plan->ws = nullptr;
   plan->counters = nullptr;
   plan->max_splits = 0;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
-    cudaError_t r = cudaSuccess;
-    r = r == cudaSuccess ? set_attr<64, EPI_UPDATE>() : r;
-    r = r == cudaSuccess ? set_attr<64, EPI_EVAL>() : r;
-    r = r == cudaSuccess ? set_attr<64, EPI_LAGR>() : r;
-    r = r == cudaSuccess ? set_attr<128, EPI_UPDATE>() : r;
-    r = r == cudaSuccess ? set_attr<128, EPI_EVAL>() : r;
-    r = r == cudaSuccess ? set_attr<128, EPI_LAGR>() : r;
-    r = r == cudaSuccess ? set_attr<256, EPI_UPDATE>() : r;
-    r = r == cudaSuccess ? set_attr<256, EPI_EVAL>() : r;
-    r = r == cudaSuccess ? set_attr<256, EPI_LAGR>() : r;
-    attr_err = r;
-  });
+  const cudaError_t attr_err = ensure_attrs();
   if (attr_err != cudaSuccess) {
     if (why) *why = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(attr_err);
     return attr_err;
@@ -603,7 +622,7 @@ cudaError_t tc_make_plan(TcPlan* plan, const void* A, int64_t lda, int n, const 
 
 template <int BN, int MODE>
 static cudaError_t launch_tc_t(const TcParams& P, int grid, cudaStream_t s) {
-  k_tc<BN, MODE><<<grid, TC_THREADS, TcCfg<BN>::SMEM, s>>>(P);
+  k_tc<BN, MODE, false><<<grid, TC_THREADS, TcCfg<BN>::SMEM, s>>>(P);
   return cudaGetLastError();
 }
 
@@ -660,6 +679,56 @@ cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_ov
     case 128: return launch_tc_bn<128>(P, grid, mode, s);
     default: return launch_tc_bn<256>(P, grid, mode, s);
   }
+}
+
+static cudaError_t ensure_attrs() {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    cudaError_t r = cudaSuccess;
+    r = r == cudaSuccess ? set_attr<64, EPI_UPDATE>() : r;
+    r = r == cudaSuccess ? set_attr<64, EPI_EVAL>() : r;
+    r = r == cudaSuccess ? set_attr<64, EPI_LAGR>() : r;
+    r = r == cudaSuccess ? set_attr<128, EPI_UPDATE>() : r;
+    r = r == cudaSuccess ? set_attr<128, EPI_EVAL>() : r;
+    r = r == cudaSuccess ? set_attr<128, EPI_LAGR>() : r;
+    r = r == cudaSuccess ? set_attr<256, EPI_UPDATE>() : r;
+    r = r == cudaSuccess ? set_attr<256, EPI_EVAL>() : r;
+    r = r == cudaSuccess ? set_attr<256, EPI_LAGR>() : r;
+    attr_err = r;
+  });
+  return attr_err;
+}
+
+cudaError_t launch_tc_group(const TcInst* d_insts, int n_insts, int num_tiles, int tile_n, int mode, int epi_variant,
+                            uint64_t timeout_ns, cudaStream_t s) {
+  if (mode != EPI_UPDATE && mode != EPI_EVAL) return cudaErrorInvalidValue;
+  cudaError_t e = ensure_attrs();
+  if (e != cudaSuccess) return e;
+  TcParams P;
+  memset(&P, 0, sizeof(P));
+  P.num_tiles = num_tiles;
+  P.dp_tiles = num_tiles;
+  P.splits = 1;
+  P.timeout_ns = timeout_ns;
+  P.insts = d_insts;
+  P.n_insts = n_insts;
+  P.epi_variant = epi_variant;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = num_tiles < sms ? num_tiles : sms;
+  if (grid < 1) return cudaSuccess;
+#define SBO_GROUP_LAUNCH(BNV)                                                                            \
+  if (mode == EPI_UPDATE) k_tc<BNV, EPI_UPDATE, true><<<grid, TC_THREADS, TcCfg<BNV>::SMEM, s>>>(P);     \
+  else k_tc<BNV, EPI_EVAL, true><<<grid, TC_THREADS, TcCfg<BNV>::SMEM, s>>>(P);
+  switch (tile_n) {
+    case 64: SBO_GROUP_LAUNCH(64); break;
+    case 128: SBO_GROUP_LAUNCH(128); break;
+    default: SBO_GROUP_LAUNCH(256); break;
+  }
+#undef SBO_GROUP_LAUNCH
+  return cudaGetLastError();
 }
 
 }  // namespace sbo

@@ -80,6 +80,19 @@ struct TcPlan {
   int max_splits;
   bool ready;
 };
+// One instance of a grouped launch (several dense problems in one persistent launch).  The
+// table lives in device memory; instances are ordered by decreasing n.
+struct TcInst {
+  CUtensorMap mapA;        // A of this instance
+  CUtensorMap mapX[3];     // operand buffers: ping, pong, bits (box rows = tile_n)
+  EpiArgs epi[5];          // epilogue arguments: [2*cur + write_bits] for updates, [4] evaluations
+  int n_tiles, kblocks;    // restart tiles, k-blocks
+  int tile_begin;          // first tile of this instance in the launch's tile list
+  int pad;
+};
+cudaError_t launch_tc_group(const TcInst* d_insts, int n_insts, int num_tiles, int tile_n, int mode, int epi_variant,
+                            uint64_t timeout_ns, cudaStream_t s);
+
 // Work split of one launch: dp_tiles whole tiles round-robin, then the remaining tiles in
 // `splits` K-ranges each (sk_units = tail * splits units, one per CTA).
 struct TcSchedule {

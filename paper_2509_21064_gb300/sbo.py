@@ -26,7 +26,9 @@ KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR = 0, 1, 2, 3, 4
 # every symbol include/sbo.h declares
 EXPORTS = ["sbo_create_dense", "sbo_create_csr", "sbo_gda_start", "sbo_gda_run", "sbo_gda", "sbo_sync",
            "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace", "sbo_lagrangian", "sbo_lagrangian_noalloc",
-           "sbo_set_option", "sbo_info", "sbo_launch_count", "sbo_destroy", "sbo_last_error", "sbo_version"]
+           "sbo_set_option", "sbo_info", "sbo_launch_count", "sbo_destroy", "sbo_last_error", "sbo_version",
+           "sbo_group_create", "sbo_group_start", "sbo_group_run", "sbo_group_sync", "sbo_group_set_option",
+           "sbo_group_launch_count", "sbo_group_destroy"]
 
 
 class SboError(RuntimeError):
@@ -81,6 +83,13 @@ def lib():
         "sbo_launch_count": (ctypes.c_int64, [_P]),
         "sbo_destroy": (None, [_P]),
         "sbo_last_error": (ctypes.c_char_p, []),
+        "sbo_group_create": (st, [ctypes.c_int32, ctypes.POINTER(_P), _P, ctypes.POINTER(_P)]),
+        "sbo_group_start": (st, [_P, ctypes.POINTER(sbo_gda_params)]),
+        "sbo_group_run": (st, [_P, ctypes.c_int64]),
+        "sbo_group_sync": (st, [_P]),
+        "sbo_group_set_option": (st, [_P, ctypes.c_int32, ctypes.c_int64]),
+        "sbo_group_launch_count": (ctypes.c_int64, [_P]),
+        "sbo_group_destroy": (None, [_P]),
         "sbo_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -300,3 +309,73 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+# ---- grouped runs ----------------------------------------------------------------------------
+def sbo_group_create(problems, stream=None):
+    arr = (_P * len(problems))(*[pr.h if isinstance(pr, Problem) else pr for pr in problems])
+    h = _P()
+    _check(lib().sbo_group_create(len(problems), arr, _stream(stream), ctypes.byref(h)), "sbo_group_create")
+    return h
+
+
+def sbo_group_start(g, prms):
+    arr = (sbo_gda_params * len(prms))(*prms)
+    _check(lib().sbo_group_start(g, arr), "sbo_group_start")
+
+
+def sbo_group_run(g, iters):
+    _check(lib().sbo_group_run(g, int(iters)), "sbo_group_run")
+
+
+def sbo_group_sync(g):
+    _check(lib().sbo_group_sync(g), "sbo_group_sync")
+
+
+def sbo_group_set_option(g, option, value):
+    _check(lib().sbo_group_set_option(g, int(option), int(value)), "sbo_group_set_option")
+
+
+def sbo_group_launch_count(g) -> int:
+    return int(lib().sbo_group_launch_count(g))
+
+
+def sbo_group_destroy(g):
+    if g:
+        lib().sbo_group_destroy(g)
+
+
+class Group:
+    """Owns one group handle over caller-owned :class:`Problem` members."""
+
+    def __init__(self, problems, stream=None):
+        self.problems = list(problems)
+        self.h = sbo_group_create(self.problems, stream)
+
+    def set_option(self, option, value):
+        sbo_group_set_option(self.h, option, value)
+
+    def start(self, prms):
+        sbo_group_start(self.h, prms)
+        for pr, q in zip(self.problems, prms):
+            pr.restarts = q.restarts
+
+    def run(self, iters):
+        sbo_group_run(self.h, iters)
+
+    def sync(self):
+        sbo_group_sync(self.h)
+
+    def launch_count(self):
+        return sbo_group_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            sbo_group_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

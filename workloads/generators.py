@@ -236,6 +236,7 @@ def dense_params(Q, restarts: int, iters: int, delta: float = 0.01, eval_every: 
     Max-Cut values ybar=6, alpha=beta=0.025 keep ybar at 1.5x |lambda_min|, i.e. the convex
     start of the landscape analysis (section 4.4)."""
     lam = spectral_scale(Q) if lam_hat is None else lam_hat
+    lam = max(lam, 1.0)              # an (almost) empty Q keeps finite steps
     s = lam / 4.0
     return GdaParams(restarts=restarts, iters=iters, alpha=0.025 / s, beta=0.025 * s,
                      ybar=6.0 * s, delta=delta, grad_tol=2 * delta * s, eval_every=eval_every,
