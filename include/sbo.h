@@ -164,7 +164,8 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       3 tiny-n single-CTA loop (n <= 64, FP32)
  *   SBO_OPT_USE_GRAPH:  1 (default) replay blocks of K iterations from a CUDA graph; 0 launch
  *                       every kernel directly
- *   SBO_OPT_TILE_N:     restarts per tensor-core tile: 0 auto, 64, 128 or 256
+ *   SBO_OPT_TILE_N:     restarts per tensor-core tile: 0 auto, 64, 128 or 256 (one SM per
+ *                       128-row tile), or 512: CTA pairs (two SMs per 256 x 256 tile)
  *   SBO_OPT_AUTOTUNE:   1 (default): with SBO_OPT_TILE_N = 0, sbo_gda_start times the tcgen05
  *                       update kernel at every tile width on the run's own buffers and keeps
  *                       the fastest (cached per n, B, SM count); 0: a fixed rule

@@ -341,13 +341,15 @@ sbo_status tune_tile(sbo_problem* p, int* out) {
   a.Xout = p->Xop[1];
   a.bits_out = nullptr;
   sbo_status st = SBO_OK;
-  for (int tn : {64, 128, 256}) {
+  for (int tn : {64, 128, 256, 512}) {
     if (tn > 64 && tn / 2 >= p->B) continue;
+    if (tn == 512 && !tc_pair_supported(nullptr)) continue;
     TcPlan pl{};
     std::string why;
-    if (tc_make_plan(&pl, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, tn, &why) !=
-        cudaSuccess)
+    if (tc_make_plan(&pl, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, tn == 512 ? 128 : tn,
+                     &why) != cudaSuccess)
       continue;
+    pl.pair = tn == 512;
     attach_workspace(p, &pl);
     cudaError_t e = launch_tc(pl, 0, nullptr, a, EPI_UPDATE, timeout_ns(p), p->stream);
     const int reps = 3;
@@ -579,7 +581,8 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       return SBO_OK;
     case SBO_OPT_USE_GRAPH: p->opt_graph = value != 0; return SBO_OK;
     case SBO_OPT_TILE_N:
-      if (value != 0 && value != 64 && value != 128 && value != 256) return fail(SBO_EINVAL, "tile_n must be 0, 64, 128 or 256");
+      if (value != 0 && value != 64 && value != 128 && value != 256 && value != 512)
+        return fail(SBO_EINVAL, "tile_n must be 0, 64, 128, 256 or 512 (CTA pairs)");
       p->opt_tile_n = (int)value;
       return SBO_OK;
     case SBO_OPT_AUTOTUNE: p->opt_autotune = value != 0; return SBO_OK;
@@ -695,9 +698,12 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
     } else if (tn == 0) {
       tn = heuristic_tile(p);
     }
+    if (tn == 512 && !tc_pair_supported(nullptr)) tn = 256;
     p->tile_n = tn;
-    e = tc_make_plan(&p->plan, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, tn, &why);
+    e = tc_make_plan(&p->plan, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B,
+                     tn == 512 ? 128 : tn, &why);
     if (e != cudaSuccess) { free_run(p); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
+    p->plan.pair = tn == 512;
     attach_workspace(p, &p->plan);
   } else {
     p->tile_n = 0;

@@ -78,6 +78,7 @@ struct TcPlan {
   float* ws;               // >= sms * tile_n * 128 floats
   int* counters;           // >= sms * 8 ints, zero before the first launch
   int max_splits;
+  bool pair;               // CTA-pair kernel (k_tc2.cu): 256 x 256 tiles; tile_n is then 128
   bool ready;
 };
 // One instance of a grouped launch (several dense problems in one persistent launch).  The
@@ -107,6 +108,10 @@ cudaError_t tc_make_operand_map(CUtensorMap* m, const void* X, int64_t ldx, int 
                                 std::string* why);
 cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_override, const EpiArgs& a,
                       int mode, uint64_t timeout_ns, cudaStream_t s);
+// k_tc2.cu: CTA-pair variant (update and evaluation epilogues)
+bool tc_pair_supported(int* max_clusters);
+cudaError_t launch_tc_pair(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,
+                           cudaStream_t s);
 
 // api.cu: read-only view of a dense problem and the thread-local error message, for entry
 // points defined outside api.cu.

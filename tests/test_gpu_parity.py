@@ -107,7 +107,8 @@ def test_simt_fp32_parity_graph_and_direct(n, B):
         assert np.array_equal(X2, gx[50]) and np.array_equal(Y2, gy[50])
 
 
-@pytest.mark.parametrize("n,B,tile", [(300, 100, 0), (260, 300, 256), (333, 129, 128), (64, 17, 64)])
+@pytest.mark.parametrize("n,B,tile", [(300, 100, 0), (260, 300, 256), (333, 129, 128), (64, 17, 64),
+                                      (300, 100, 512), (600, 520, 512)])
 def test_tcgen05_bf16_parity(n, B, tile):
     Q, c = W.dense_qubo(n, seed=n + 1)
     p = W.dense_params(Q, restarts=B, iters=200, eval_every=10, seed=11)
@@ -128,7 +129,7 @@ def test_tcgen05_bf16_parity(n, B, tile):
         assert np.array_equal(X, gx[50]) and np.array_equal(Y, gy[50])
 
 
-@pytest.mark.parametrize("n,B,tile", [(2048, 256, 256), (1100, 100, 64)])
+@pytest.mark.parametrize("n,B,tile", [(2048, 256, 256), (1100, 100, 64), (2048, 300, 512)])
 def test_tcgen05_split_k_tail_tiles(n, B, tile):
     """Tiles left over after whole rounds over the SMs are split along K; the partials are summed
     in split order by whichever CTA finishes a tile slice last.  Same trajectories (mixed
@@ -310,7 +311,7 @@ def test_full_size_dense_n20000_sampled_restarts():
         P.run(3)
         X, Y = P.state()
         Fr, tr = P.restart_best()
-        assert P.info()["tile_n"] in (64, 128, 256)
+        assert P.info()["tile_n"] in (64, 128, 256, 512)
     sample = [0, 517, 1023]
     A, cp = O.canonicalize(Q, c)
     del Q
