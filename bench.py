@@ -43,6 +43,9 @@ RESTARTS_DEFAULT = RESTARTS
 K_EVAL = 50
 METRIC = "GDA restart-iterations/s at n=20k dense QUBO"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# DRAM bytes (read + write) per launch of the update kernel from one ncu capture of this
+# workload (profiles/k_tc_pair_update_dense_n20000.md); keyed by (tile width, n, restarts)
+MEASURED_TRAFFIC = {(512, 20000, 1024): 1.169377e9 + 0.1809856e9}
 
 
 def peaks():
@@ -360,7 +363,9 @@ def run_ours(args):
                    "best_F_after_run": F_best,
                    "parallelism": f"replicas x{world} (restarts sharded by seed)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": MEASURED_TRAFFIC.get((info["tile_n"], N_VARS, RESTARTS)),
+                     "algorithmic_bytes": 2.0 * N_VARS * N_VARS + 18.0 * N_VARS * RESTARTS + 2.0 * N_VARS * RESTARTS,
                      "kernel": kname, "launch_ms": t_kernel * 1e3,
                      "peak_source": f"{src} bf16_tflops_sustained (kernel timed inside the long run)",
                      "frac_of_burst_peak": achieved / peak_burst},

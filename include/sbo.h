@@ -168,7 +168,10 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       128-row tile), or 512: CTA pairs (two SMs per 256 x 256 tile)
  *   SBO_OPT_AUTOTUNE:   1 (default): with SBO_OPT_TILE_N = 0, sbo_gda_start times the tcgen05
  *                       update kernel at every tile width on the run's own buffers and keeps
- *                       the fastest (cached per n, B, SM count); 0: a fixed rule
+ *                       the fastest; decisions are cached per (device, n, B, SM count) in the
+ *                       process and in the file named by the environment variable
+ *                       SBO_TUNE_CACHE (default ~/.cache/sbo/tile_tuning.txt; "off" disables
+ *                       the file); 0: a fixed rule
  *   SBO_OPT_SPLIT_K:    largest split-K factor for the tensor-core tiles left over after whole
  *                       rounds over the SMs (default 16; 0 or 1 disables splitting).  Split
  *                       tiles are summed in a fixed order, so results do not depend on it.

@@ -3,8 +3,14 @@
 // and result read-back.  Every entry point catches its own failures and returns a status.
 #include <algorithm>
 #include <climits>
+#include <sys/stat.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
 #include <map>
 #include <mutex>
+#include <sstream>
 #include <tuple>
 #include <cmath>
 #include <cstring>
@@ -318,18 +324,71 @@ void attach_workspace(sbo_problem* p, TcPlan* plan) {
   }
 }
 
+// Persistent record of autotuner decisions: one line "<key> <tile>" per tuned shape, in the file
+// named by SBO_TUNE_CACHE ("off" disables it), by default ~/.cache/sbo/tile_tuning.txt.  A
+// later process -- for instance the same program under a profiler, whose per-launch overhead
+// would swamp the trial timings -- then reuses the decision instead of re-measuring.
+std::string tune_cache_path() {
+  const char* e = std::getenv("SBO_TUNE_CACHE");
+  if (e) return (!*e || std::string(e) == "off") ? std::string() : std::string(e);
+  const char* home = std::getenv("HOME");
+  return home && *home ? std::string(home) + "/.cache/sbo/tile_tuning.txt" : std::string();
+}
+
+std::string tune_key(const sbo_problem* p) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown";
+  for (auto& ch : name)
+    if (ch == ' ') ch = '_';
+  std::ostringstream k;
+  k << "v2:" << name << ":sms" << p->sms << ":n" << p->n << ":B" << p->B << ":split" << p->opt_split_k;
+  return k.str();
+}
+
+bool tune_cache_lookup(const std::string& key, int* tile) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return false;
+  std::ifstream f(path);
+  std::string k;
+  int t = 0;
+  bool found = false;
+  while (f >> k >> t)
+    if (k == key && (t == 64 || t == 128 || t == 256 || t == 512)) { *tile = t; found = true; }
+  return found;
+}
+
+void tune_cache_store(const std::string& key, int tile) {
+  const std::string path = tune_cache_path();
+  if (path.empty()) return;
+  // create the parent directories (best effort)
+  for (size_t pos = path.find('/', 1); pos != std::string::npos; pos = path.find('/', pos + 1))
+    mkdir(path.substr(0, pos).c_str(), 0755);
+  std::ofstream f(path, std::ios::app);
+  if (f) f << key << " " << tile << "\n";
+}
+
 // Autotuner of the tensor-core tile width: times the update kernel for every candidate width on
 // this run's own buffers (called before x^0 is written, so the trial launches only overwrite
-// state that initialisation rewrites) and keeps the fastest.  Results are cached per
-// (n, B, SM count, split-K limit) for the life of the process.
+// state that initialisation rewrites) and keeps the fastest.  Decisions are kept for the life of
+// the process and in the persistent record above.
 sbo_status tune_tile(sbo_problem* p, int* out) {
   static std::mutex mu;
-  static std::map<std::tuple<int64_t, int, int, int>, int> cache;
-  const auto key = std::make_tuple(p->n, p->B, p->sms, p->opt_split_k);
+  static std::map<std::string, int> cache;
+  const std::string key = tune_key(p);
   {
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
     if (it != cache.end()) { *out = it->second; return SBO_OK; }
+    int t = 0;
+    if (tune_cache_lookup(key, &t)) {
+      if (t != 512 || tc_pair_supported(nullptr)) {
+        cache[key] = t;
+        *out = t;
+        return SBO_OK;
+      }
+    }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SBO_CUDA(cudaEventCreate(&e0));
@@ -371,6 +430,7 @@ sbo_status tune_tile(sbo_problem* p, int* out) {
   {
     std::lock_guard<std::mutex> lock(mu);
     cache[key] = best;
+    tune_cache_store(key, best);
   }
   *out = best;
   return SBO_OK;
@@ -653,7 +713,7 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
   al((void**)&p->bestT, sizeof(long long) * p->B);
   al((void**)&p->evalF, sizeof(long long) * p->B);
   al((void**)&p->F2, sizeof(unsigned long long) * p->B);
-  al((void**)&p->improved, p->B);
+  al((void**)&p->improved, round_up(p->B, 8));
   al((void**)&p->bestBits, elems);
   al((void**)&p->trace, sizeof(long long) * p->trace_cap);
   al((void**)&p->n_evals, sizeof(long long));
@@ -675,6 +735,7 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
   launch_fill_i64(p->trace, p->trace_cap, LLONG_MAX, s);
   p->launches += 3;
   cudaMemsetAsync(p->F2, 0, sizeof(unsigned long long) * p->B, s);
+  cudaMemsetAsync(p->improved, 0, round_up(p->B, 8), s);
   cudaMemsetAsync(p->bestBits, 0, elems, s);
   cudaMemsetAsync(p->n_evals, 0, sizeof(long long), s);
   cudaMemsetAsync(p->t_last, 0, sizeof(long long), s);

@@ -27,18 +27,36 @@ __global__ void k_eval_compare(const unsigned long long* __restrict__ F2, long l
   improved[r] = better ? 1 : 0;
 }
 
-// 2-D grid: x runs along the contiguous dimension of the layout, y over the other one.
+// 2-D grid: x runs along the contiguous dimension of the layout (4 elements per thread; ld is a
+// multiple of 8 and `improved` is padded to a multiple of 8), y over the other dimension.
+__device__ __forceinline__ float4 op_load4(const void* p, int64_t idx, int type) {
+  if (type == OP_F32) return *reinterpret_cast<const float4*>(static_cast<const float*>(p) + idx);
+  const uint2 raw = *reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(p) + idx);
+  const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+  const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+  return make_float4(__low2float(lo), __high2float(lo), __low2float(hi), __high2float(hi));
+}
+
 __global__ void k_copy_best(const void* __restrict__ bits, int op_type, uint8_t* bestBits,
                             const uint8_t* __restrict__ improved, int n, int B, int64_t ld, int layout) {
   const int64_t inner = layout == LAYOUT_RN ? n : B;
   const int64_t outer = layout == LAYOUT_RN ? B : n;
   for (int64_t o = blockIdx.y; o < outer; o += gridDim.y) {
     if (layout == LAYOUT_RN && !improved[o]) continue;   // whole restart row unchanged
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < inner; q += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t r = layout == LAYOUT_RN ? o : q;
-      if (layout == LAYOUT_NR && !improved[r]) continue;
+    for (int64_t q = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); q < inner;
+         q += 4 * (int64_t)gridDim.x * blockDim.x) {
       const int64_t idx = o * ld + q;
-      bestBits[idx] = op_load(bits, idx, op_type) != 0.0f ? 1 : 0;
+      const float4 v = op_load4(bits, idx, op_type);
+      uchar4 nb = make_uchar4(v.x != 0.f, v.y != 0.f, v.z != 0.f, v.w != 0.f);
+      if (layout == LAYOUT_NR) {
+        const uchar4 imp = *reinterpret_cast<const uchar4*>(improved + q);
+        const uchar4 old = *reinterpret_cast<const uchar4*>(bestBits + idx);
+        nb.x = imp.x ? nb.x : old.x;
+        nb.y = imp.y ? nb.y : old.y;
+        nb.z = imp.z ? nb.z : old.z;
+        nb.w = imp.w ? nb.w : old.w;
+      }
+      *reinterpret_cast<uchar4*>(bestBits + idx) = nb;   // padding columns stay consistent
     }
   }
 }
@@ -113,7 +131,7 @@ cudaError_t launch_copy_best(const void* bits_op, int op_type, uint8_t* bestBits
                              int n, int B, int64_t ld, int layout, cudaStream_t s) {
   const int64_t inner = layout == LAYOUT_RN ? n : B;
   const int64_t outer = layout == LAYOUT_RN ? B : n;
-  const int64_t bx = (inner + 255) / 256;
+  const int64_t bx = (inner + 1023) / 1024;
   dim3 grid((unsigned)(bx < 64 ? bx : 64), (unsigned)(outer < 65535 ? outer : 65535));
   k_copy_best<<<grid, 256, 0, s>>>(bits_op, op_type, bestBits, improved, n, B, ld, layout);
   return cudaGetLastError();

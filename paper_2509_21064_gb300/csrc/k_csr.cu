@@ -170,7 +170,7 @@ static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const
   const int warps_per_block = 8;
   int64_t want = (a.n + warps_per_block - 1) / warps_per_block;
   if (MODE == EPI_EVAL) {
-    const int64_t cap = (int64_t)152 * 4 / (chunks > 0 ? chunks : 1) + 1;  // bounds the closing atomics
+    const int64_t cap = (int64_t)152 * 8 / (chunks > 0 ? chunks : 1) + 1;  // bounds the closing atomics
     if (want > cap) want = cap;
   }
   if (want > 65535) want = 65535;
