@@ -190,6 +190,30 @@ def time_to_target(S, torch, Q, c, seed, stream, dev, target, iters=2000):
     return out
 
 
+def plain_fp32_form(S, torch, Q, c, seed, stream, dev, iters=3):
+    """The plain form on the same instance: FP32 A and x, CUDA-core (SIMT) contraction with the
+    same fused update, one launch per iteration, no CUDA graph."""
+    p = W.dense_params(Q, restarts=RESTARTS_DEFAULT, iters=10**9, eval_every=10**6, seed=seed)
+    P = S.Problem.dense(Q, c, precision=S.SBO_FP32, stream=stream)
+    P.set_option(S.SBO_OPT_KERNEL, S.KERNEL_SIMT)
+    P.set_option(S.SBO_OPT_USE_GRAPH, 0)
+    P.start(S.params(**p.asdict()))
+    with torch.cuda.stream(stream):
+        P.run(1)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.run(iters)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    P.sync()
+    P.close()
+    ms = e0.elapsed_time(e1) / iters
+    return {"value": RESTARTS_DEFAULT / (ms * 1e-3), "unit": "restart-iterations/s", "ms_per_iteration": ms,
+            "form": "FP32 A and x, SIMT contraction + fused update, one launch per iteration, no graph"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -342,6 +366,9 @@ def run_ours(args):
     ttt = None
     if rank == 0 and N_VARS == 20000 and RESTARTS == 1024 and not args.no_time_to_target:
         ttt = time_to_target(S, torch, Q, c, 0, stream, dev, load_target("dense_n20000_b1024_seed0"))
+    plain = None
+    if rank == 0 and N_VARS == 20000 and RESTARTS == 1024 and not args.no_plain_form:
+        plain = plain_fp32_form(S, torch, Q, c, 0, stream, dev)
 
     pk, src = peaks()
     flops = 2.0 * N_VARS * N_VARS * RESTARTS
@@ -376,6 +403,9 @@ def run_ours(args):
     }
     if ttt is not None:
         line["time_to_target"] = ttt
+    if plain is not None:
+        plain["speedup_of_chosen_form"] = (RESTARTS * K_EVAL * args.steps / (ms * 1e-3)) / plain["value"]
+        line["plain_fp32_form"] = plain
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, it, el, _, _ = oracle_sample(Q, c, p, seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "restart-iterations/s", "cores": oracle_threads(),
@@ -484,6 +514,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-target", action="store_true")
+    ap.add_argument("--no-plain-form", action="store_true")
     ap.add_argument("--n", type=int, default=N_VARS, help="variables (profiling cases only)")
     ap.add_argument("--restarts", type=int, default=RESTARTS, help="restarts (profiling cases only)")
     ap.add_argument("--workload", default="dense", choices=["dense", "hetero"] + sorted(SPARSE),
