@@ -42,15 +42,33 @@ sbo_status cuda_fail(cudaError_t e, const char* what) {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the problem's stream) from
+// the device's default pool, which keeps up to SBO_POOL_RETAIN_MB (default 8192) of freed memory
+// for reuse, so creating and destroying problems in a loop does not pay for fresh allocations.
+void configure_pool_once() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t mb = 8192;
+    if (const char* e = std::getenv("SBO_POOL_RETAIN_MB")) mb = std::strtoull(e, nullptr, 10);
+    uint64_t thr = mb << 20;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  });
+}
+
 template <typename T>
-cudaError_t dalloc(T** p, size_t count) {
+cudaError_t dalloc(T** p, size_t count, cudaStream_t s) {
   *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  configure_pool_once();
+  return cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), s);
 }
 template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree(p);
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
   p = nullptr;
 }
 
@@ -103,6 +121,7 @@ struct sbo_problem {
   float* tc_ws = nullptr;      // split-K partial tiles of the tcgen05 contraction
   int* tc_ctr = nullptr;       // split-K arrival counters (zero between launches)
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int64_t graph_blocks_seen = 0;   // eligible K-blocks so far: a graph is captured for the second
   // Lagrangian scratch (BF16 operand)
   void* lag_op = nullptr;
   size_t lag_cap = 0;
@@ -114,36 +133,37 @@ namespace {
 void free_run(sbo_problem* p) {
   for (auto& g : p->gexec)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
-  dfree(p->Xm);
-  dfree(p->Y);
-  dfree(p->Xop[0]);
-  dfree(p->Xop[1]);
-  dfree(p->bits);
-  dfree(p->bestF);
-  dfree(p->bestT);
-  dfree(p->evalF);
-  dfree(p->trace);
-  dfree(p->n_evals);
-  dfree(p->t_last);
-  dfree(p->sel);
-  dfree(p->F2);
-  dfree(p->bestBits);
-  dfree(p->improved);
-  dfree(p->tc_ws);
-  dfree(p->tc_ctr);
+  dfree(p->Xm, p->stream);
+  dfree(p->Y, p->stream);
+  dfree(p->Xop[0], p->stream);
+  dfree(p->Xop[1], p->stream);
+  dfree(p->bits, p->stream);
+  dfree(p->bestF, p->stream);
+  dfree(p->bestT, p->stream);
+  dfree(p->evalF, p->stream);
+  dfree(p->trace, p->stream);
+  dfree(p->n_evals, p->stream);
+  dfree(p->t_last, p->stream);
+  dfree(p->sel, p->stream);
+  dfree(p->F2, p->stream);
+  dfree(p->bestBits, p->stream);
+  dfree(p->improved, p->stream);
+  dfree(p->tc_ws, p->stream);
+  dfree(p->tc_ctr, p->stream);
   p->started = false;
 }
 
 void free_all(sbo_problem* p) {
   free_run(p);
-  dfree(p->A);
-  dfree(p->rowptr);
-  dfree(p->col);
-  dfree(p->val);
-  dfree(p->cp);
-  dfree(p->cp64);
-  dfree(p->err);
-  dfree(p->lag_op);
+  dfree(p->A, p->stream);
+  dfree(p->rowptr, p->stream);
+  dfree(p->col, p->stream);
+  dfree(p->val, p->stream);
+  dfree(p->cp, p->stream);
+  dfree(p->cp64, p->stream);
+  dfree(p->err, p->stream);
+  if (p->lag_op) cudaFree(p->lag_op);   // allocated with cudaMalloc: used on callers' streams
+  p->lag_op = nullptr;
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   p->cap_stream = nullptr;
 }
@@ -154,7 +174,7 @@ sbo_status init_common(sbo_problem* p, void* stream) {
   SBO_CUDA(cudaGetDevice(&dev));
   SBO_CUDA(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev));
   SBO_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
-  SBO_CUDA(dalloc(&p->err, 1));
+  SBO_CUDA(dalloc(&p->err, 1, p->stream));
   SBO_CUDA(cudaMemsetAsync(p->err, 0, sizeof(uint32_t), p->stream));
   return SBO_OK;
 }
@@ -489,16 +509,17 @@ sbo_status sbo_create_dense(int64_t n, const int32_t* Q, const int32_t* c, int32
   int32_t *Qd = nullptr, *cd = nullptr;
   unsigned long long* rowsum = nullptr;
   uint32_t* rerr = nullptr;
-  auto cleanup_tmp = [&]() { dfree(Qd); dfree(cd); dfree(rowsum); dfree(rerr); };
+  cudaStream_t s = p->stream;
+  auto cleanup_tmp = [&]() { dfree(Qd, s); dfree(cd, s); dfree(rowsum, s); dfree(rerr, s); };
   auto bail = [&](sbo_status s) { cleanup_tmp(); free_all(p); delete p; return s; };
   cudaError_t e;
   const size_t a_elt = p->a_type == OP_F32 ? 4 : 2;
-  if ((e = cudaMalloc(&p->A, (size_t)n * p->lda * a_elt)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc A"));
-  if ((e = dalloc(&p->cp, n)) != cudaSuccess || (e = dalloc(&p->cp64, n)) != cudaSuccess ||
-      (e = dalloc(&Qd, (size_t)n * n)) != cudaSuccess || (e = dalloc(&rowsum, n)) != cudaSuccess ||
-      (e = dalloc(&rerr, 1)) != cudaSuccess || (c && (e = dalloc(&cd, n)) != cudaSuccess))
+  configure_pool_once();
+  if ((e = cudaMallocAsync(&p->A, (size_t)n * p->lda * a_elt, s)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc A"));
+  if ((e = dalloc(&p->cp, n, s)) != cudaSuccess || (e = dalloc(&p->cp64, n, s)) != cudaSuccess ||
+      (e = dalloc(&Qd, (size_t)n * n, s)) != cudaSuccess || (e = dalloc(&rowsum, n, s)) != cudaSuccess ||
+      (e = dalloc(&rerr, 1, s)) != cudaSuccess || (c && (e = dalloc(&cd, n, s)) != cudaSuccess))
     return bail(e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation failed") : cuda_fail(e, "cudaMalloc"));
-  cudaStream_t s = p->stream;
   if ((e = cudaMemcpyAsync(Qd, Q, sizeof(int32_t) * n * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return bail(cuda_fail(e, "copy Q"));
   if (c && (e = cudaMemcpyAsync(cd, c, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
@@ -617,11 +638,13 @@ sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const i
   std::vector<float> cpf(n);
   for (int64_t i = 0; i < n; ++i) cpf[i] = (float)cp[i];
   cudaError_t e;
-  if ((e = dalloc(&p->rowptr, n + 1)) != cudaSuccess || (e = dalloc(&p->col, cc.size())) != cudaSuccess ||
-      (e = cudaMalloc(&p->val, std::max<size_t>(1, cc.size() * velt))) != cudaSuccess ||
-      (e = dalloc(&p->cp, n)) != cudaSuccess || (e = dalloc(&p->cp64, n)) != cudaSuccess)
+  cudaStream_t cs = p->stream;
+  if ((e = dalloc(&p->rowptr, n + 1, cs)) != cudaSuccess || (e = dalloc(&p->col, cc.size(), cs)) != cudaSuccess ||
+      (e = cudaMallocAsync(&p->val, std::max<size_t>(1, cc.size() * velt), cs)) != cudaSuccess ||
+      (e = dalloc(&p->cp, n, cs)) != cudaSuccess || (e = dalloc(&p->cp64, n, cs)) != cudaSuccess)
     return bail(e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation failed") : cuda_fail(e, "cudaMalloc"));
-  if ((e = cudaMemcpy(p->rowptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+  if ((e = cudaStreamSynchronize(cs)) != cudaSuccess ||
+      (e = cudaMemcpy(p->rowptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (!cc.empty() && (e = cudaMemcpy(p->col, cc.data(), sizeof(int32_t) * cc.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (!cc.empty() && (e = cudaMemcpy(p->val, vbytes.data(), vbytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
       (e = cudaMemcpy(p->cp, cpf.data(), sizeof(float) * n, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -691,6 +714,7 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
   p->t_last_eval = 0;
   p->n_evals_host = 0;
   p->cur = 0;
+  p->graph_blocks_seen = 0;
   const int64_t rows = p->layout == LAYOUT_RN ? p->B : p->n;
   const size_t elems = (size_t)rows * p->ld;
   const size_t op_elt = p->op_type == OP_F32 ? 4 : 2;
@@ -700,7 +724,7 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
   const int64_t evals_T = prm->iters / prm->eval_every + 2;
   p->trace_cap = std::min<int64_t>(evals_T, 1 << 20) + 4096;
   auto al = [&](void** q, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(q, bytes ? bytes : 1);
+    if (e == cudaSuccess) e = cudaMallocAsync(q, bytes ? bytes : 1, p->stream);
   };
   if (need_master) al((void**)&p->Xm, elems * 4);
   al((void**)&p->Y, elems * 4);
@@ -743,8 +767,8 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
     // split-K workspace (sized for the widest tile): one partial tile per CTA, arrival counters
     // per tail tile slice
     if (p->opt_split_k >= 2) {
-      if ((e = dalloc(&p->tc_ws, (size_t)p->sms * 256 * 128)) != cudaSuccess ||
-          (e = dalloc(&p->tc_ctr, (size_t)p->sms * TC_WS_COUNTERS_PER_TILE)) != cudaSuccess) {
+      if ((e = dalloc(&p->tc_ws, (size_t)p->sms * 256 * 128, s)) != cudaSuccess ||
+          (e = dalloc(&p->tc_ctr, (size_t)p->sms * TC_WS_COUNTERS_PER_TILE, s)) != cudaSuccess) {
         free_run(p);
         return e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation of the split-K workspace failed")
                                               : cuda_fail(e, "cudaMalloc");
@@ -771,16 +795,16 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
   }
   float* x0d = nullptr;
   if (x0) {
-    if ((e = dalloc(&x0d, (size_t)p->B * p->n)) != cudaSuccess) { free_run(p); return cuda_fail(e, "cudaMalloc x0"); }
+    if ((e = dalloc(&x0d, (size_t)p->B * p->n, s)) != cudaSuccess) { free_run(p); return cuda_fail(e, "cudaMalloc x0"); }
     if ((e = cudaMemcpyAsync(x0d, x0, sizeof(float) * p->B * p->n, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
-      dfree(x0d); free_run(p); return cuda_fail(e, "copy x0");
+      dfree(x0d, s); free_run(p); return cuda_fail(e, "copy x0");
     }
   }
   e = launch_init_state((int)p->n, p->B, p->ld, p->layout, prm->seed, (float)prm->ybar, x0d, p->Xm,
                         ker == KER_TINY ? (void*)p->Xm : p->Xop[0], ker == KER_TINY ? OP_F32 : p->op_type, p->Y,
                         p->err, s);
   ++p->launches;
-  if (x0d) { cudaStreamSynchronize(s); dfree(x0d); }
+  if (x0d) { cudaStreamSynchronize(s); dfree(x0d, s); }
   if (e != cudaSuccess) { free_run(p); return cuda_fail(e, "init launch"); }
   p->started = true;
   return SBO_OK;
@@ -800,7 +824,10 @@ sbo_status sbo_gda_run(sbo_problem* p, int64_t iters) {
     const int64_t stop = std::min(nx, t_end);
     const int64_t steps = stop - p->t;
     const bool eval_here = stop == nx;
-    if (p->opt_graph && eval_here && steps == K && p->t % K == 0 && p->t_last_eval == p->t) {
+    const bool eligible = p->opt_graph && eval_here && steps == K && p->t % K == 0 && p->t_last_eval == p->t;
+    // a captured block pays off only when it is replayed: the first eligible block of a run is
+    // launched directly, later ones are replayed from graphs
+    if (eligible && p->graph_blocks_seen++ >= 1) {
       const int par = p->cur;
       if (!p->gexec[par]) {
         sbo_status st = capture_block(p, par);
@@ -852,11 +879,11 @@ sbo_status sbo_eval(sbo_problem* p, int64_t count, const uint8_t* bits, int64_t*
   uint8_t* bd = nullptr;
   void* opd = nullptr;
   unsigned long long* f2 = nullptr;
-  auto cleanup = [&]() { dfree(bd); if (opd) cudaFree(opd); opd = nullptr; dfree(f2); };
+  auto cleanup = [&]() { dfree(bd, s); if (opd) cudaFreeAsync(opd, s); opd = nullptr; dfree(f2, s); };
   cudaError_t e;
-  if ((e = dalloc(&bd, (size_t)count * p->n)) != cudaSuccess ||
-      (e = cudaMalloc(&opd, (size_t)rows * ld * (op == OP_F32 ? 4 : 2))) != cudaSuccess ||
-      (e = dalloc(&f2, count)) != cudaSuccess) {
+  if ((e = dalloc(&bd, (size_t)count * p->n, s)) != cudaSuccess ||
+      (e = cudaMallocAsync(&opd, (size_t)rows * ld * (op == OP_F32 ? 4 : 2), s)) != cudaSuccess ||
+      (e = dalloc(&f2, count, s)) != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "cudaMalloc (eval)");
   }
@@ -948,7 +975,7 @@ sbo_status sbo_state(sbo_problem* p, float* X, float* Y) {
   if (!p->started) return fail(SBO_ENOTREADY, "sbo_gda_start has not been called");
   cudaStream_t s = p->stream;
   float* tmp = nullptr;
-  SBO_CUDA(dalloc(&tmp, (size_t)p->B * p->n));
+  SBO_CUDA(dalloc(&tmp, (size_t)p->B * p->n, s));
   const float* xsrc = p->Xm ? p->Xm : static_cast<const float*>(p->Xop[p->cur]);
   cudaError_t e = cudaSuccess;
   if (X) {
@@ -961,7 +988,7 @@ sbo_status sbo_state(sbo_problem* p, float* X, float* Y) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(Y, tmp, sizeof(float) * p->B * p->n, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
-  dfree(tmp);
+  dfree(tmp, s);
   if (e != cudaSuccess) return cuda_fail(e, "state read-back");
   return read_err(p);
 }
@@ -1011,7 +1038,7 @@ sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const f
     const size_t need = (size_t)B * ldx * 2;
     if (need > p->lag_cap) {
       if (p->lag_op) { cudaStreamSynchronize(s); cudaFree(p->lag_op); p->lag_op = nullptr; p->lag_cap = 0; }
-      SBO_CUDA(cudaMalloc(&p->lag_op, need));
+      SBO_CUDA(cudaMalloc(&p->lag_op, need));   // used on the caller's stream: not stream-ordered
       SBO_CUDA(cudaMemsetAsync(p->lag_op, 0, need, s));
       p->lag_cap = need;
     }

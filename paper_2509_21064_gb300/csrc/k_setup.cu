@@ -5,35 +5,52 @@
 namespace sbo {
 
 // A_ij = Q_ij + Q_ji (i != j), A_ii = 0, written as FP32 or BF16 with leading dimension lda.
-// 32x32 tiles: the transposed tile is staged through shared memory so both reads coalesce.
-// Also accumulates the row sums of |A_ij| (exactness of A b in FP32) and flags entries whose
-// magnitude exceeds a_limit (not exactly representable in the storage type).
+// A block owns 32 rows and CANON_TJ consecutive 32x32 column tiles; each tile's transpose is
+// staged through shared memory so both reads coalesce.  Row sums of |A_ij| (exactness of A b in
+// FP32) accumulate in registers over the block's tiles and are added with one atomic per row per
+// block; entries whose magnitude exceeds a_limit (not exact in the storage type) raise a flag.
+constexpr int CANON_TJ = 16;
+
 __global__ void __launch_bounds__(256) k_canon_dense(const int32_t* __restrict__ Q, int64_t n, void* A,
                                                      int64_t lda, int a_type, unsigned long long* rowsum,
                                                      uint32_t* range_err, int64_t a_limit) {
   __shared__ int32_t tT[32][33];
-  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  const int64_t i0 = (int64_t)blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  // transposed tile: tT[a][b] = Q[j0 + a][i0 + b]
-  for (int a = ty; a < 32; a += 8) {
-    const int64_t r = j0 + a, cidx = i0 + tx;
-    tT[a][tx] = (r < n && cidx < n) ? Q[r * n + cidx] : 0;
-  }
-  __syncthreads();
-  for (int a = ty; a < 32; a += 8) {
-    const int64_t i = i0 + a, j = j0 + tx;
-    int64_t v = 0;
-    if (i < n && j < n && i != j) v = (int64_t)Q[i * n + j] + (int64_t)tT[tx][a];
-    const int64_t av = v < 0 ? -v : v;
-    if (av > a_limit) atomicOr(range_err, 1u);
-    if (i < n && j < lda) {
-      if (a_type == OP_F32) static_cast<float*>(A)[i * lda + j] = (float)v;
-      else static_cast<__nv_bfloat16*>(A)[i * lda + j] = __float2bfloat16_rn((float)v);
+  unsigned long long rs[4] = {0ull, 0ull, 0ull, 0ull};
+  bool over = false;
+  for (int t = 0; t < CANON_TJ; ++t) {
+    const int64_t j0 = ((int64_t)blockIdx.x * CANON_TJ + t) * 32;
+    if (j0 >= lda) break;
+    // transposed tile: tT[a][b] = Q[j0 + a][i0 + b]
+    for (int a = ty; a < 32; a += 8) {
+      const int64_t r = j0 + a, cidx = i0 + tx;
+      tT[a][tx] = (r < n && cidx < n) ? Q[r * n + cidx] : 0;
     }
-    // row sum of |A_ij| over this tile row
-    unsigned long long s = (unsigned long long)av;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (tx == 0 && i < n && s) atomicAdd(&rowsum[i], s);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int a = ty + 8 * k;
+      const int64_t i = i0 + a, j = j0 + tx;
+      int64_t v = 0;
+      if (i < n && j < n && i != j) v = (int64_t)Q[i * n + j] + (int64_t)tT[tx][a];
+      const int64_t av = v < 0 ? -v : v;
+      over |= av > a_limit;
+      if (i < n && j < lda) {
+        if (a_type == OP_F32) static_cast<float*>(A)[i * lda + j] = (float)v;
+        else static_cast<__nv_bfloat16*>(A)[i * lda + j] = __float2bfloat16_rn((float)v);
+      }
+      rs[k] += (unsigned long long)av;
+    }
+    __syncthreads();
+  }
+  if (over) atomicOr(range_err, 1u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    unsigned long long s2 = rs[k];
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    const int64_t i = i0 + ty + 8 * k;
+    if (tx == 0 && i < n && s2) atomicAdd(&rowsum[i], s2);
   }
 }
 
@@ -60,7 +77,7 @@ cudaError_t launch_canon_dense(const int32_t* Qd, const int32_t* cd, int64_t n, 
                                int a_type, float* cp, int64_t* cp64, unsigned long long* rowsum,
                                uint32_t* range_err, int64_t a_limit, cudaStream_t s) {
   const int64_t nb = (n + 31) / 32;
-  const int64_t nbx = (lda + 31) / 32;
+  const int64_t nbx = (lda + 32 * CANON_TJ - 1) / (32 * CANON_TJ);
   dim3 grid((unsigned)nbx, (unsigned)nb), block(32, 8);
   k_canon_dense<<<grid, block, 0, s>>>(Qd, n, A, lda, a_type, rowsum, range_err, a_limit);
   cudaError_t e = cudaGetLastError();
