@@ -505,6 +505,59 @@ def run_hetero(args):
     return 0
 
 
+# Independent-set sizes PDBO reaches on random d-regular graphs in the paper's MIS table (mean
+# over 20 instances, B = 10, RTX 3090, earliest time to best within 180 s): context only.
+PAPER_MIS = {(10000, 3): (4431.9, 0.6), (10000, 100): (603.0, 3.6), (50000, 3): (22127.3, 1.1),
+             (50000, 100): (3006.2, 14.6)}
+
+
+def run_mis(args):
+    """MIS as QUBO (F = -sum x + 4 sum_E x_i x_j) on a random d-regular graph with the paper's
+    MIS hyper-parameters (ybar = 5, alpha = beta = 0.02): best set found, whether it is
+    independent, and the device time until the best candidate was first evaluated."""
+    import torch
+    from paper_2509_21064_gb300 import sbo as S
+    from paper_2509_21064_gb300.build import build
+    build()
+    S.lib()
+    n, d, B, T, K = args.n, args.degree, args.restarts, args.iters, 10
+    rowptr, col, val, c, (ei, ej) = W.mis_regular(n, d, seed=0)
+    prec = {"fp32": S.SBO_FP32, "bf16": S.SBO_BF16, "e4m3": S.SBO_FP8_E4M3}[args.precision]
+    if args.mis_params == "paper":
+        p = W.graph_params("mis", restarts=B, iters=T, eval_every=K, seed=0)
+    else:
+        # the scaling used for dense QUBO: ybar = 1.5 |lambda_min| estimate (convex start)
+        lam = W.csr_spectral_scale(n, rowptr, col, val)
+        p = W.dense_params(None, restarts=B, iters=T, eval_every=K, seed=0, lam_hat=lam)
+    stream = torch.cuda.Stream()
+    P = S.Problem.csr(n, rowptr, col, val, c, precision=prec, stream=stream)
+    P.start(S.params(**p.asdict()))
+    evs = []
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(T // K):
+            P.run(K)
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            evs.append(e)
+        torch.cuda.synchronize()
+    P.sync()
+    x, F, t_best, r_best = P.best()
+    P.close()
+    violations = int(np.sum(x[ei] & x[ej]))
+    size = int(x.sum())
+    paper = PAPER_MIS.get((n, d))
+    print(json.dumps({"workload": f"MIS on a random {d}-regular graph, n={n}, lambda=4", "restarts": B, "iters": T,
+                      "params": args.mis_params, "ybar": p.ybar, "alpha": p.alpha, "beta": p.beta,
+                      "precision": args.precision, "best_F": int(F), "set_size": size, "violations": violations,
+                      "independent": violations == 0, "best_iteration": int(t_best),
+                      "seconds_to_best": e0.elapsed_time(evs[t_best // K - 1]) * 1e-3 if t_best >= K else None,
+                      "seconds_total": e0.elapsed_time(evs[-1]) * 1e-3,
+                      "paper_mean_size_and_seconds_rtx3090": paper}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -517,10 +570,14 @@ def main():
     ap.add_argument("--no-plain-form", action="store_true")
     ap.add_argument("--n", type=int, default=N_VARS, help="variables (profiling cases only)")
     ap.add_argument("--restarts", type=int, default=RESTARTS, help="restarts (profiling cases only)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "hetero"] + sorted(SPARSE),
+    ap.add_argument("--workload", default="dense", choices=["dense", "hetero", "mis"] + sorted(SPARSE),
                     help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
                     help="weight/operand precision of a sparse workload")
+    ap.add_argument("--degree", type=int, default=3, help="MIS workload: graph degree")
+    ap.add_argument("--mis-params", default="paper", choices=["paper", "scaled"],
+                    help="MIS workload: the paper's table (ybar=5, alpha=beta=0.02) or the spectral scaling")
+    ap.add_argument("--iters", type=int, default=3000, help="MIS workload: GDA iterations")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 64, 128, 256, 512],
                     help="tensor-core tile width (0: autotuned); profiling cases only")
     ap.add_argument("--kernel-only", action="store_true",
@@ -532,6 +589,12 @@ def main():
         return run_reference(args)
     if args.workload == "hetero":
         return run_hetero(args)
+    if args.workload == "mis":
+        if args.n == N_VARS:
+            args.n = 10000
+        if args.restarts == RESTARTS:
+            args.restarts = 10
+        return run_mis(args)
     if args.workload != "dense":
         return run_sparse(args)
     return run_ours(args)

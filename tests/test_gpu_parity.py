@@ -324,3 +324,18 @@ def test_full_size_dense_n20000_sampled_restarts():
         b = O.round_bits(X[r])
         assert tr[r] == 3
         assert Fr[r] == O.objective(Qs, c, b)
+
+
+def test_mis_on_regular_graph_exact_objective():
+    """MIS as QUBO (appendix on MIS, lambda = 4) through the sparse path: the reported best is an
+    exact objective of its own bits; an independent best set has F = -|S|."""
+    n, d = 600, 3
+    rowptr, col, val, c, (i, j) = W.mis_regular(n, d, seed=2)
+    p = W.graph_params("mis", restarts=32, iters=1500, eval_every=10, seed=1)
+    with S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP8_E4M3) as P:
+        P.gda(to_gda_params(p))
+        x, F, t, r = P.best()
+    assert O.objective_csr(n, rowptr, col, val, c, x) == F
+    if not np.any(x[i] & x[j]):
+        assert F == -int(x.sum())
+    assert -F > n / 4          # a 3-regular graph on 600 vertices has an independent set > n/4

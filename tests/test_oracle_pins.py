@@ -304,3 +304,14 @@ def test_best_tracking_tie_rules_by_brute_force():
         Fr = min(v for v in allv if v[2] == r)
         assert (out["best_F"][r], out["best_t"][r]) == (Fr[0], Fr[1])
     assert [t for t, _ in out["evals"]] == list(range(7, 300, 7)) + [300]
+
+
+@pytest.mark.parametrize("n,d", [(400, 3), (500, 100)])
+def test_regular_graph_generator_is_simple_and_regular(n, d):
+    """The MIS and Max-Cut stand-ins need simple d-regular graphs (pairing model; edge switches
+    for large d)."""
+    rowptr, col, val, c, (i, j) = W.mis_regular(n, d, seed=5)
+    assert np.all(np.diff(rowptr) == d)
+    assert np.all(i != j)
+    key = np.minimum(i, j).astype(np.int64) * n + np.maximum(i, j)
+    assert np.unique(key).size == key.size == n * d // 2

@@ -14,6 +14,7 @@ from .generators import (  # noqa: F401
     csr_from_edges,
     maxcut_qubo,
     spectral_scale,
+    csr_spectral_scale,
     dense_from_csr,
     dense_params,
     graph_params,

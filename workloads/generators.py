@@ -114,11 +114,66 @@ def maxcut_torus(rows: int = 100, cols: int = 100, seed: int = 0, weights: str =
     return i, j, w
 
 
-def _regular_edges(n: int, d: int, rng: np.random.Generator, max_tries: int = 10000):
-    """Random simple d-regular graph: pairing model, rejecting loops and multi-edges."""
+def _switch_repair(a, b, n, rng, max_steps=None):
+    """Remove loops and multi-edges from a pairing by random edge switches: a bad edge (u, v) and a
+    random edge (w, z) become (u, w), (v, z) when neither new edge is a loop or already present."""
+    a, b = a.copy(), b.copy()
+    m = a.size
+    cnt = {}
+
+    def key(u, v):
+        return (u, v) if u < v else (v, u)
+
+    for k in range(m):
+        kk = key(a[k], b[k])
+        cnt[kk] = cnt.get(kk, 0) + 1
+
+    def is_bad(k):
+        return a[k] == b[k] or cnt[key(a[k], b[k])] > 1
+
+    bad = [k for k in range(m) if is_bad(k)]
+    steps = 0
+    limit = max_steps if max_steps is not None else 200 * m
+    while bad:
+        steps += 1
+        if steps > limit:
+            raise RuntimeError("edge switching did not converge")
+        k = bad[-1]
+        if not is_bad(k):
+            bad.pop()
+            continue
+        q = int(rng.integers(0, m))
+        if q == k:
+            continue
+        u, v, w, z = a[k], b[k], a[q], b[q]
+        e1, e2 = key(u, w), key(v, z)
+        if u == w or v == z or e1 == e2:
+            continue
+        cnt[key(u, v)] -= 1
+        cnt[key(w, z)] -= 1
+        if cnt.get(e1, 0) or cnt.get(e2, 0):
+            cnt[key(u, v)] += 1
+            cnt[key(w, z)] += 1
+            continue
+        a[k], b[k], a[q], b[q] = u, w, v, z
+        cnt[e1] = cnt.get(e1, 0) + 1
+        cnt[e2] = cnt.get(e2, 0) + 1
+        bad.pop()
+    return a, b
+
+
+def _regular_edges(n: int, d: int, rng: np.random.Generator, max_tries: int = 200):
+    """Random simple d-regular graph: pairing model, rejecting loops and multi-edges; when
+    rejection is hopeless (large d), one pairing repaired by random edge switches."""
     if (n * d) % 2:
         raise ValueError("n*d must be even")
     stubs = np.repeat(np.arange(n, dtype=np.int64), d)
+    if d > 8:
+        perm = rng.permutation(stubs)
+        a, b = _switch_repair(perm[0::2], perm[1::2], n, rng)
+        lo_, hi_ = np.minimum(a, b), np.maximum(a, b)
+        order = np.argsort(lo_ * n + hi_)
+        return lo_[order].astype(np.int32), hi_[order].astype(np.int32)
     for _ in range(max_tries):
         perm = rng.permutation(stubs)
         a, b = perm[0::2], perm[1::2]
@@ -223,6 +278,19 @@ def spectral_scale(Q) -> float:
         S = Q[r0:r1].astype(np.float64) + Q[:, r0:r1].T.astype(np.float64)
         S[np.arange(r1 - r0), np.arange(r0, r1)] = 0.0
         ss += float(np.sum(S * S)) * 0.25
+    return 2.0 * math.sqrt(ss) / math.sqrt(n)
+
+
+def csr_spectral_scale(n: int, rowptr, col, val) -> float:
+    """spectral_scale of a CSR Q: 2 ||Q_sym||_F / sqrt(n) (off-diagonal part)."""
+    rows = np.repeat(np.arange(n), np.diff(np.asarray(rowptr)))
+    col = np.asarray(col)
+    off = rows != col
+    sym = {}
+    for r, cc, v in zip(rows[off], col[off], np.asarray(val)[off]):
+        k = (r, cc) if r < cc else (cc, r)
+        sym[k] = sym.get(k, 0) + int(v)
+    ss = sum(2 * (0.5 * v) ** 2 for v in sym.values())
     return 2.0 * math.sqrt(ss) / math.sqrt(n)
 
 
