@@ -15,7 +15,8 @@ Functions and what pins them (tests/test_oracle_*.py, tests/golden/):
 function            follows                                          pinned by
 ==================  ===============================================  ===========================
 canonicalize        Prop. 2.4 (exponents dropped on binary points)   Def. 2.2 expectation by
-                                                                     enumeration; golden file
+ (and _csr)                                                          enumeration; golden file;
+                                                                     dense == CSR form
 objective           Eq. 1 with the QUBO objective                    Max-Cut edge count; MIS
                                                                      count; golden file
 multilinear         Def. 2.2 / Prop. 2.4 closed form                 enumeration; Lemma 2.3
@@ -62,6 +63,20 @@ def canonicalize(Q, c=None):
     np.fill_diagonal(A, 0.0)
     cp = c + np.diagonal(Q)
     return A, cp
+
+
+def canonicalize_csr(n, rowptr, col, val, c=None):
+    """The same multilinear form as ``canonicalize`` for a CSR Q, as a scipy sparse A
+    (A = Q + Q^T off the diagonal, c' = c + diag Q).  scipy is only the storage and the matmul."""
+    import scipy.sparse as sp
+    Qs = sp.csr_matrix((np.asarray(val, dtype=np.float64), np.asarray(col), np.asarray(rowptr)), shape=(n, n))
+    diag = Qs.diagonal()
+    A = (Qs + Qs.T).tolil()
+    A.setdiag(0.0)
+    A = A.tocsr()
+    A.eliminate_zeros()
+    c = np.zeros(n) if c is None else np.asarray(c, dtype=np.float64)
+    return A, c + diag
 
 
 def objective(Q, c, b):
@@ -116,7 +131,7 @@ def lagrangian(A, cp, X, Y):
     """
     X = np.atleast_2d(np.asarray(X, dtype=np.float64))
     Y = np.atleast_2d(np.asarray(Y, dtype=np.float64))
-    AX = X @ A.T
+    AX = np.asarray((A @ X.T).T)          # A dense or scipy sparse
     Lval = 0.5 * np.einsum("ri,ri->r", X, AX) + X @ cp + np.sum(Y * g(X), axis=1)
     GX = AX + cp[None, :] + Y * g_prime(X)
     GY = g(X)

@@ -339,3 +339,57 @@ def test_mis_on_regular_graph_exact_objective():
     if not np.any(x[i] & x[j]):
         assert F == -int(x.sum())
     assert -F > n / 4          # a 3-regular graph on 600 vertices has an independent set > n/4
+
+
+def test_full_size_regular_maxcut_sampled_restarts():
+    """Random 4-regular graph, n = 20,000, unit weights, B = 512 (E4M3 weights, BF16 operand):
+    three iterations, restarts 0, 255 and 511 against the oracle on those restarts alone."""
+    n = 20000
+    i, j, w = W.maxcut_regular(n, 4, seed=0)
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    p = W.graph_params("maxcut", restarts=512, iters=3000, eval_every=3, seed=0)
+    with S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP8_E4M3) as P:
+        P.start(to_gda_params(p))
+        P.run(3)
+        X, Y = P.state()
+        Fr, tr = P.restart_best()
+    sample = [0, 255, 511]
+    A, cp = O.canonicalize_csr(n, rowptr, col, val, c)
+    X0, _ = O.init_state(n, 512, p.seed, p.ybar)
+    ox, oy, _ = oracle_trajectory(None, None, p, 3, X0=X0[sample], A=A, cp=cp)
+    assert normwise(X[sample], ox[3]).max() <= TOL_MIXED
+    assert normwise(Y[sample], oy[3]).max() <= TOL_MIXED
+    for r in sample:
+        assert tr[r] == 3
+        assert Fr[r] == O.objective_csr(n, rowptr, col, val, c, O.round_bits(X[r]))
+
+
+def test_dense_n5000_bf16_lagrangian_and_autograd():
+    """Dense QUBO n = 5,000 (BF16 tensor-core problem): the autograd Function's value and gradients
+    against the FP64 oracle, whose gradient is pinned to central finite differences; inputs on a
+    1/256 grid are exact in BF16, so only FP32 accumulation error remains."""
+    import torch
+    from paper_2509_21064_gb300.autograd import lagrangian
+    n, B = 5000, 8
+    Q, c = W.dense_qubo(n, seed=0)
+    A, cp = O.canonicalize(Q, c)
+    rng = np.random.default_rng(9)
+    X = rng.integers(0, 257, size=(B, n)) / 256.0
+    Y = rng.normal(scale=2000.0, size=(B, n)).astype(np.float32).astype(np.float64)
+    gw = rng.normal(size=B)
+    L_o, GX_o, GY_o = O.lagrangian(A, cp, X, Y)
+    # the oracle gradient against central differences on a few coordinates (L is quadratic in x)
+    h = 1e-3
+    for r, k in ((0, 0), (3, 1234), (7, 4999)):
+        E = np.zeros_like(X)
+        E[r, k] = h
+        fd = (O.lagrangian(A, cp, X + E, Y)[0][r] - O.lagrangian(A, cp, X - E, Y)[0][r]) / (2 * h)
+        assert abs(fd - GX_o[r, k]) <= 1e-6 * max(1.0, abs(GX_o[r, k]))
+    with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
+        Xt = torch.tensor(X, dtype=torch.float32, device="cuda", requires_grad=True)
+        Yt = torch.tensor(Y, dtype=torch.float32, device="cuda", requires_grad=True)
+        L = lagrangian(Xt, Yt, P)
+        (L * torch.tensor(gw, dtype=torch.float32, device="cuda")).sum().backward()
+        assert np.max(np.abs(L.detach().cpu().numpy() - L_o)) / np.max(np.abs(L_o)) <= 1e-5
+        assert normwise(Xt.grad.cpu().numpy(), gw[:, None] * GX_o).max() <= 1e-5
+        assert normwise(Yt.grad.cpu().numpy(), gw[:, None] * GY_o).max() <= 1e-6

@@ -315,3 +315,22 @@ def test_regular_graph_generator_is_simple_and_regular(n, d):
     assert np.all(i != j)
     key = np.minimum(i, j).astype(np.int64) * n + np.maximum(i, j)
     assert np.unique(key).size == key.size == n * d // 2
+
+
+def test_csr_canonical_form_equals_the_dense_one():
+    """canonicalize_csr (scipy storage) gives the same A, c' as canonicalize on the dense Q."""
+    n = 60
+    rng = np.random.default_rng(4)
+    Qd = rng.integers(-5, 6, size=(n, n)) * (rng.random((n, n)) < 0.2)   # non-symmetric, diagonal
+    c = rng.integers(-5, 6, size=n)
+    rows, cols = np.nonzero(Qd)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    A_s, cp_s = O.canonicalize_csr(n, rowptr, cols, Qd[rows, cols], c)
+    A_d, cp_d = O.canonicalize(Qd, c)
+    assert np.array_equal(A_s.toarray(), A_d) and np.array_equal(cp_s, cp_d)
+    X = rng.random((3, n))
+    Y = rng.normal(size=(3, n))
+    for a, b in zip(O.lagrangian(A_s, cp_s, X, Y), O.lagrangian(A_d, cp_d, X, Y)):
+        assert np.allclose(a, b, rtol=1e-13, atol=1e-12)
