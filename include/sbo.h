@@ -100,6 +100,10 @@ sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const i
  * sbo_gda: start (x0 = NULL) + run(prm->iters) + synchronise.  A handle may run again:
  * each start begins afresh. */
 sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float* x0);
+/* sbo_gda_start_xy: as sbo_gda_start, with the initial duals y0 (host, B*n float32 [r][i], finite)
+ * given by the caller instead of ybar (y0 NULL: ybar) -- a warm start, or the continuation of a
+ * run saved with sbo_state.  The paper starts from y0 = ybar * 1 (App. C.1). */
+sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const float* x0, const float* y0);
 sbo_status sbo_gda_run(sbo_problem* p, int64_t iters);
 sbo_status sbo_gda(sbo_problem* p, const sbo_gda_params* prm);
 

@@ -682,6 +682,10 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
 }
 
 sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float* x0) {
+  return sbo_gda_start_xy(p, prm, x0, nullptr);
+}
+
+sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const float* x0, const float* y0) {
   g_last_error.clear();
   if (!p) return fail(SBO_EINVAL, "problem is NULL");
   sbo_status st = check_params(prm);
@@ -794,17 +798,25 @@ sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float*
     p->tile_n = 0;
   }
   float* x0d = nullptr;
-  if (x0) {
-    if ((e = dalloc(&x0d, (size_t)p->B * p->n, s)) != cudaSuccess) { free_run(p); return cuda_fail(e, "cudaMalloc x0"); }
-    if ((e = cudaMemcpyAsync(x0d, x0, sizeof(float) * p->B * p->n, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
-      dfree(x0d, s); free_run(p); return cuda_fail(e, "copy x0");
+  float* y0d = nullptr;
+  if (y0) {
+    for (int64_t k = 0; k < (int64_t)p->B * p->n; ++k)
+      if (!std::isfinite(y0[k])) { free_run(p); return fail(SBO_EINVAL, "y0 holds a non-finite value"); }
+  }
+  for (int q = 0; q < 2; ++q) {
+    const float* src = q == 0 ? x0 : y0;
+    float** dst = q == 0 ? &x0d : &y0d;
+    if (!src) continue;
+    if ((e = dalloc(dst, (size_t)p->B * p->n, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(*dst, src, sizeof(float) * p->B * p->n, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+      dfree(x0d, s); dfree(y0d, s); free_run(p); return cuda_fail(e, "upload of x0 / y0");
     }
   }
-  e = launch_init_state((int)p->n, p->B, p->ld, p->layout, prm->seed, (float)prm->ybar, x0d, p->Xm,
+  e = launch_init_state((int)p->n, p->B, p->ld, p->layout, prm->seed, (float)prm->ybar, x0d, y0d, p->Xm,
                         ker == KER_TINY ? (void*)p->Xm : p->Xop[0], ker == KER_TINY ? OP_F32 : p->op_type, p->Y,
                         p->err, s);
   ++p->launches;
-  if (x0d) { cudaStreamSynchronize(s); dfree(x0d, s); }
+  if (x0d || y0d) { cudaStreamSynchronize(s); dfree(x0d, s); dfree(y0d, s); }
   if (e != cudaSuccess) { free_run(p); return cuda_fail(e, "init launch"); }
   p->started = true;
   return SBO_OK;

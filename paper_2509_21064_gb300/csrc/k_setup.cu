@@ -93,10 +93,10 @@ cudaError_t launch_rowsum_check(const unsigned long long* rowsum, const int64_t*
 }
 
 // x^0 from the caller (host-provided, copied to the device as FP32 [B][n]) or from SplitMix64;
-// y^0 = ybar.  Writes the FP32 master (if any), the contraction operand and y in `layout`.
+// y^0 from the caller or ybar.  Writes the FP32 master (if any), the contraction operand and y in `layout`.
 __global__ void k_init_state(int n, int B, int64_t ld, int layout, uint64_t seed, float ybar,
-                             const float* __restrict__ x0, float* Xm, void* Xop, int op_type, float* Y,
-                             uint32_t* err) {
+                             const float* __restrict__ x0, const float* __restrict__ y0, float* Xm, void* Xop,
+                             int op_type, float* Y, uint32_t* err) {
   const int64_t total = (int64_t)n * B;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -110,17 +110,17 @@ __global__ void k_init_state(int n, int B, int64_t ld, int layout, uint64_t seed
     const int64_t idx = layout == LAYOUT_RN ? r * ld + i : i * ld + r;
     if (Xm) Xm[idx] = x;
     op_store(Xop, idx, x, op_type);
-    Y[idx] = ybar;
+    Y[idx] = y0 ? y0[r * n + i] : ybar;
   }
 }
 
 cudaError_t launch_init_state(int n, int B, int64_t ld, int layout, uint64_t seed, float ybar,
-                              const float* x0, float* Xm, void* Xop, int op_type, float* Y,
+                              const float* x0, const float* y0, float* Xm, void* Xop, int op_type, float* Y,
                               uint32_t* err, cudaStream_t s) {
   const int64_t total = (int64_t)n * B;
   const int64_t blocks = (total + 255) / 256;
   k_init_state<<<(unsigned)(blocks < 152 * 64 ? blocks : 152 * 64), 256, 0, s>>>(
-      n, B, ld, layout, seed, ybar, x0, Xm, Xop, op_type, Y, err);
+      n, B, ld, layout, seed, ybar, x0, y0, Xm, Xop, op_type, Y, err);
   return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ cudaError_t launch_canon_dense(const int32_t* Qd, const int32_t* cd, int64_t n, 
 cudaError_t launch_rowsum_check(const unsigned long long* rowsum, const int64_t* cp64, int64_t n,
                                 uint32_t* range_err, cudaStream_t s);
 cudaError_t launch_init_state(int n, int B, int64_t ld, int layout, uint64_t seed, float ybar,
-                              const float* x0, float* Xm, void* Xop, int op_type, float* Y,
+                              const float* x0, const float* y0, float* Xm, void* Xop, int op_type, float* Y,
                               uint32_t* err, cudaStream_t s);
 cudaError_t launch_to_operand(const float* X, int n, int B, int64_t ld_in, void* out, int64_t ld_out,
                               int op_type, cudaStream_t s);

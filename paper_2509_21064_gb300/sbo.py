@@ -24,7 +24,7 @@ SBO_OPT_KERNEL, SBO_OPT_USE_GRAPH, SBO_OPT_TILE_N, SBO_OPT_TIMEOUT_US, SBO_OPT_S
 KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR = 0, 1, 2, 3, 4
 
 # every symbol include/sbo.h declares
-EXPORTS = ["sbo_create_dense", "sbo_create_csr", "sbo_gda_start", "sbo_gda_run", "sbo_gda", "sbo_sync",
+EXPORTS = ["sbo_create_dense", "sbo_create_csr", "sbo_gda_start", "sbo_gda_start_xy", "sbo_gda_run", "sbo_gda", "sbo_sync",
            "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace", "sbo_lagrangian", "sbo_lagrangian_noalloc",
            "sbo_set_option", "sbo_info", "sbo_launch_count", "sbo_destroy", "sbo_last_error", "sbo_version",
            "sbo_group_create", "sbo_group_start", "sbo_group_run", "sbo_group_sync", "sbo_group_set_option",
@@ -68,6 +68,7 @@ def lib():
         "sbo_create_csr": (st, [ctypes.c_int64, ctypes.c_int64, _I64P, _I32P, _I32P, _I32P, ctypes.c_int32, _P,
                                 ctypes.POINTER(_P)]),
         "sbo_gda_start": (st, [_P, ctypes.POINTER(sbo_gda_params), _F32P]),
+        "sbo_gda_start_xy": (st, [_P, ctypes.POINTER(sbo_gda_params), _F32P, _F32P]),
         "sbo_gda_run": (st, [_P, ctypes.c_int64]),
         "sbo_gda": (st, [_P, ctypes.POINTER(sbo_gda_params)]),
         "sbo_sync": (st, [_P]),
@@ -152,6 +153,13 @@ def sbo_gda_start(h, prm: sbo_gda_params, x0=None):
     x = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float32)
     _check(lib().sbo_gda_start(h, ctypes.byref(prm), None if x is None else _ptr(x, ctypes.c_float)),
            "sbo_gda_start")
+
+
+def sbo_gda_start_xy(h, prm: sbo_gda_params, x0=None, y0=None):
+    x = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float32)
+    y = None if y0 is None else np.ascontiguousarray(y0, dtype=np.float32)
+    _check(lib().sbo_gda_start_xy(h, ctypes.byref(prm), None if x is None else _ptr(x, ctypes.c_float),
+                                  None if y is None else _ptr(y, ctypes.c_float)), "sbo_gda_start_xy")
 
 
 def sbo_gda_run(h, iters):
@@ -258,8 +266,11 @@ class Problem:
     def set_option(self, option, value):
         sbo_set_option(self.h, option, value)
 
-    def start(self, prm: sbo_gda_params, x0=None):
-        sbo_gda_start(self.h, prm, x0)
+    def start(self, prm: sbo_gda_params, x0=None, y0=None):
+        if y0 is None:
+            sbo_gda_start(self.h, prm, x0)
+        else:
+            sbo_gda_start_xy(self.h, prm, x0, y0)
         self.restarts = prm.restarts
 
     def run(self, iters):

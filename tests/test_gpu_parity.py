@@ -393,3 +393,66 @@ def test_dense_n5000_bf16_lagrangian_and_autograd():
         assert np.max(np.abs(L.detach().cpu().numpy() - L_o)) / np.max(np.abs(L_o)) <= 1e-5
         assert normwise(Xt.grad.cpu().numpy(), gw[:, None] * GX_o).max() <= 1e-5
         assert normwise(Yt.grad.cpu().numpy(), gw[:, None] * GY_o).max() <= 1e-6
+
+
+@pytest.mark.parametrize("case", range(3))
+@pytest.mark.parametrize("path", ["tiny", "simt", "tc", "csr32", "csr_bf16"])
+def test_hand_worked_iterations_on_every_kernel(case, path):
+    """The hand-worked Algorithm-1 iterations of tests/golden (perturbation rule with both
+    boundary equalities, active projection, plain steps) reproduced exactly by every kernel:
+    every number is dyadic and exact in FP32 and BF16."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "gda_steps_hand.json")) as f:
+        g = json.load(f)["cases"][case]
+    Q = np.array(g["Q"], dtype=np.int32)
+    c = np.array(g["c"], dtype=np.int32)
+    n = Q.shape[0]
+    T = len(g["x"])
+    prm = S.params(restarts=1, iters=T, alpha=g["alpha"], beta=g["beta"], ybar=g["y0"][0], delta=g["delta"],
+                   grad_tol=g["grad_tol"], eval_every=1000)
+    x0 = np.array(g["x0"], dtype=np.float32)[None, :]
+    y0 = np.array(g["y0"], dtype=np.float32)[None, :]
+    if path.startswith("csr"):
+        rows, cols = np.nonzero(Q)
+        rowptr = np.zeros(n + 1, np.int64)
+        np.add.at(rowptr, rows + 1, 1)
+        P = S.Problem.csr(n, np.cumsum(rowptr), cols.astype(np.int32), Q[rows, cols], c,
+                          precision=S.SBO_FP32 if path == "csr32" else S.SBO_BF16)
+    else:
+        P = S.Problem.dense(Q, c, precision=S.SBO_BF16 if path == "tc" else S.SBO_FP32)
+        P.set_option(S.SBO_OPT_KERNEL, {"tiny": S.KERNEL_TINY, "simt": S.KERNEL_SIMT, "tc": S.KERNEL_TC}[path])
+    with P:
+        P.start(prm, x0, y0)
+        for t in range(T):
+            P.run(1)
+            X, Y = P.state()
+            assert np.array_equal(X[0], np.array(g["x"][t], dtype=np.float32)), (t, X)
+            assert np.array_equal(Y[0], np.array(g["y"][t], dtype=np.float32)), (t, Y)
+
+
+@pytest.mark.parametrize("kind", ["tc", "csr"])
+def test_resume_from_saved_state_is_bit_identical(kind):
+    """Checkpoint/resume: the loop draws no random numbers after x^0, so restarting from a saved
+    (X, Y) with sbo_gda_start_xy continues the trajectory bit for bit."""
+    if kind == "tc":
+        Q, c = W.dense_qubo(700, seed=3)
+        p = W.dense_params(Q, restarts=96, iters=10**6, eval_every=10, seed=4)
+        make = lambda: S.Problem.dense(Q, c, precision=S.SBO_BF16)
+    else:
+        i, j, w = W.maxcut_torus(30, 40, seed=1)
+        rowptr, col, val, c = W.maxcut_qubo(1200, i, j, w)
+        p = W.graph_params("maxcut", restarts=70, iters=10**6, eval_every=10, seed=4)
+        make = lambda: S.Problem.csr(1200, rowptr, col, val, c, precision=S.SBO_BF16)
+    prm = to_gda_params(p)
+    with make() as P:
+        P.start(prm)
+        P.run(40)
+        X40, Y40 = P.state()
+        P.start(prm)
+        P.run(20)
+        X20, Y20 = P.state()
+        P.start(prm, X20, Y20)
+        P.run(20)
+        Xr, Yr = P.state()
+    assert np.array_equal(Xr, X40) and np.array_equal(Yr, Y40)
