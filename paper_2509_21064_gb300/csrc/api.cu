@@ -114,7 +114,8 @@ struct sbo_problem {
   long long *bestF = nullptr, *bestT = nullptr, *evalF = nullptr, *trace = nullptr, *n_evals = nullptr,
             *t_last = nullptr, *sel = nullptr;
   unsigned long long* F2 = nullptr;
-  uint8_t *bestBits = nullptr, *improved = nullptr;
+  uint8_t* bestBits = nullptr;
+  unsigned int* commit_ctr = nullptr;   // arrival counter of the evaluation commit (zero between launches)
   int64_t trace_cap = 0;
   int64_t n_evals_host = 0;
   TcPlan plan{};
@@ -147,7 +148,7 @@ void free_run(sbo_problem* p) {
   dfree(p->sel, p->stream);
   dfree(p->F2, p->stream);
   dfree(p->bestBits, p->stream);
-  dfree(p->improved, p->stream);
+  dfree(p->commit_ctr, p->stream);
   dfree(p->tc_ws, p->stream);
   dfree(p->tc_ctr, p->stream);
   p->started = false;
@@ -222,18 +223,36 @@ cudaError_t enqueue_step(sbo_problem* p, bool write_bits, cudaStream_t s) {
   return e;
 }
 
+CommitArgs commit_args(const sbo_problem* p) {
+  CommitArgs c;
+  std::memset(&c, 0, sizeof(c));
+  c.bits = p->bits;
+  c.op_type = p->op_type;
+  c.layout = p->layout;
+  c.n = (int)p->n;
+  c.B = p->B;
+  c.ld = p->ld;
+  c.bestBits = p->bestBits;
+  c.F2 = p->F2;
+  c.bestF = p->bestF;
+  c.bestT = p->bestT;
+  c.evalF = p->evalF;
+  c.trace = p->trace;
+  c.n_evals = p->n_evals;
+  c.t_last = p->t_last;
+  c.trace_cap = p->trace_cap;
+  c.ctr = p->commit_ctr;
+  return c;
+}
+
 // Exact objective of the bits written by the last step, then best bookkeeping.
 cudaError_t enqueue_eval(sbo_problem* p, int64_t add, cudaStream_t s) {
   EpiArgs a = base_args(p);
   a.Xin = p->bits;
   cudaError_t e = contract(p, a, EPI_EVAL, 2, s);
   if (e != cudaSuccess) return e;
-  e = launch_eval_compare(p->F2, p->bestF, p->bestT, p->improved, p->evalF, p->B, p->t_last, add, s);
-  if (e != cudaSuccess) return e;
-  e = launch_copy_best(p->bits, p->op_type, p->bestBits, p->improved, (int)p->n, p->B, p->ld, p->layout, s);
-  if (e != cudaSuccess) return e;
-  e = launch_eval_finalize(p->F2, p->evalF, p->trace, p->n_evals, p->trace_cap, p->B, p->t_last, add, s);
-  p->launches += 3;
+  e = launch_eval_commit(commit_args(p), add, s);
+  ++p->launches;
   return e;
 }
 
@@ -741,7 +760,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   al((void**)&p->bestT, sizeof(long long) * p->B);
   al((void**)&p->evalF, sizeof(long long) * p->B);
   al((void**)&p->F2, sizeof(unsigned long long) * p->B);
-  al((void**)&p->improved, round_up(p->B, 8));
+  al((void**)&p->commit_ctr, sizeof(unsigned int));
   al((void**)&p->bestBits, elems);
   al((void**)&p->trace, sizeof(long long) * p->trace_cap);
   al((void**)&p->n_evals, sizeof(long long));
@@ -763,7 +782,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   launch_fill_i64(p->trace, p->trace_cap, LLONG_MAX, s);
   p->launches += 3;
   cudaMemsetAsync(p->F2, 0, sizeof(unsigned long long) * p->B, s);
-  cudaMemsetAsync(p->improved, 0, round_up(p->B, 8), s);
+  cudaMemsetAsync(p->commit_ctr, 0, sizeof(unsigned int), s);
   cudaMemsetAsync(p->bestBits, 0, elems, s);
   cudaMemsetAsync(p->n_evals, 0, sizeof(long long), s);
   cudaMemsetAsync(p->t_last, 0, sizeof(long long), s);
@@ -847,7 +866,7 @@ sbo_status sbo_gda_run(sbo_problem* p, int64_t iters) {
       }
       cudaError_t e = cudaGraphLaunch(p->gexec[par], p->stream);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-      p->launches += K + 4;
+      p->launches += K + 2;
       if (K & 1) p->cur ^= 1;
       p->t += K;
       p->t_last_eval = p->t;
@@ -1123,6 +1142,8 @@ struct sbo_group {
   cudaStream_t cap_stream = nullptr;
   int tile_n = 128;
   TcInst* d_insts = nullptr;
+  CommitArgs* d_commit = nullptr;     // per-member evaluation commit arguments
+  int64_t max_n = 0, max_B = 0;
   int num_tiles = 0;
   bool started = false;
   int64_t T = 0, K = 1;
@@ -1153,15 +1174,10 @@ cudaError_t group_eval(sbo_group* g, int64_t add, cudaStream_t s) {
   cudaError_t e = launch_tc_group(g->d_insts, (int)g->members.size(), g->num_tiles, g->tile_n, EPI_EVAL, 4,
                                   timeout_ns(g->members[0]), s);
   ++g->launches;
-  for (sbo_problem* p : g->members) {
-    if (e != cudaSuccess) break;
-    e = launch_eval_compare(p->F2, p->bestF, p->bestT, p->improved, p->evalF, p->B, p->t_last, add, s);
-    if (e == cudaSuccess)
-      e = launch_copy_best(p->bits, p->op_type, p->bestBits, p->improved, (int)p->n, p->B, p->ld, p->layout, s);
-    if (e == cudaSuccess)
-      e = launch_eval_finalize(p->F2, p->evalF, p->trace, p->n_evals, p->trace_cap, p->B, p->t_last, add, s);
-    g->launches += 3;
-  }
+  if (e != cudaSuccess) return e;
+  // members are restart-major: rows are restarts, the contiguous dimension is the variables
+  e = launch_eval_commit_group(g->d_commit, (int)g->members.size(), g->max_n, g->max_B, add, s);
+  ++g->launches;
   return e;
 }
 
@@ -1237,7 +1253,9 @@ sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms) {
       return fail(SBO_EINVAL, "members of a group share iters and eval_every");
   }
   group_free_graphs(g);
-  if (g->d_insts) { cudaStreamSynchronize(g->stream); cudaFree(g->d_insts); g->d_insts = nullptr; }
+  if (g->d_insts || g->d_commit) cudaStreamSynchronize(g->stream);
+  if (g->d_insts) { cudaFree(g->d_insts); g->d_insts = nullptr; }
+  if (g->d_commit) { cudaFree(g->d_commit); g->d_commit = nullptr; }
   g->started = false;
   // start every member on the group's tile width, then build the instance table
   for (size_t k = 0; k < cnt; ++k) {
@@ -1280,6 +1298,15 @@ sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms) {
   g->num_tiles = tiles;
   SBO_CUDA(cudaMalloc(&g->d_insts, sizeof(TcInst) * cnt));
   SBO_CUDA(cudaMemcpy(g->d_insts, tab.data(), sizeof(TcInst) * cnt, cudaMemcpyHostToDevice));
+  std::vector<CommitArgs> ctab(cnt);
+  g->max_n = g->max_B = 0;
+  for (size_t k = 0; k < cnt; ++k) {
+    ctab[k] = commit_args(g->members[k]);
+    g->max_n = std::max<int64_t>(g->max_n, g->members[k]->n);
+    g->max_B = std::max<int64_t>(g->max_B, g->members[k]->B);
+  }
+  SBO_CUDA(cudaMalloc(&g->d_commit, sizeof(CommitArgs) * cnt));
+  SBO_CUDA(cudaMemcpy(g->d_commit, ctab.data(), sizeof(CommitArgs) * cnt, cudaMemcpyHostToDevice));
   g->T = prms[0].iters;
   g->K = prms[0].eval_every;
   g->t = g->t_last_eval = g->n_evals_host = 0;
@@ -1309,7 +1336,7 @@ sbo_status sbo_group_run(sbo_group* g, int64_t iters) {
       }
       cudaError_t e = cudaGraphLaunch(g->gexec[par], g->stream);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-      g->launches += g->K + 1 + 3 * (int64_t)g->members.size();
+      g->launches += g->K + 2;
       if (g->K & 1) g->cur ^= 1;
       g->t += g->K;
       g->t_last_eval = g->t;
@@ -1362,6 +1389,7 @@ void sbo_group_destroy(sbo_group* g) {
   cudaStreamSynchronize(g->stream);
   group_free_graphs(g);
   if (g->d_insts) cudaFree(g->d_insts);
+  if (g->d_commit) cudaFree(g->d_commit);
   if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   delete g;
 }

@@ -1,34 +1,17 @@
 // Best-candidate bookkeeping of the multi-start run (section 4.2: B restarts, best retained).
 //
-// After an evaluation kernel has accumulated 2F(b_r) for every restart r:
-//   k_eval_compare   F_r = 2F/2; strict improvement of restart r's best keeps (F, t) and flags
-//                    the restart, so equal values keep the earliest t
-//   k_copy_best      copies the candidate bits of flagged restarts
-//   k_eval_finalize  min_r F_r into the trace, clears the accumulators, advances t_last
-// k_best_select returns the lexicographic minimum of (F, t, r) over the per-restart bests,
+// After an evaluation kernel has accumulated 2F(b_r) for every restart r, k_eval_commit (one
+// launch) keeps the bits, F and t of every restart whose F strictly improves on its best, so equal
+// values keep the earliest t, appends min_r F_r to the trace, clears the accumulators and advances
+// t_last.  k_best_select returns the lexicographic minimum of (F, t, r) over the per-restart bests,
 // which equals the minimum over every evaluation so far.
+#include <algorithm>
+#include <cstring>
+
 #include "sbo_internal.h"
 
 namespace sbo {
 
-__global__ void k_eval_compare(const unsigned long long* __restrict__ F2, long long* bestF, long long* bestT,
-                               uint8_t* improved, long long* evalF, int B, const long long* t_last,
-                               long long add) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= B) return;
-  const long long F = (long long)F2[r] / 2;
-  const long long t = *t_last + add;
-  evalF[r] = F;
-  const bool better = F < bestF[r];
-  if (better) {
-    bestF[r] = F;
-    bestT[r] = t;
-  }
-  improved[r] = better ? 1 : 0;
-}
-
-// 2-D grid: x runs along the contiguous dimension of the layout (4 elements per thread; ld is a
-// multiple of 8 and `improved` is padded to a multiple of 8), y over the other dimension.
 __device__ __forceinline__ float4 op_load4(const void* p, int64_t idx, int type) {
   if (type == OP_F32) return *reinterpret_cast<const float4*>(static_cast<const float*>(p) + idx);
   const uint2 raw = *reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(p) + idx);
@@ -37,51 +20,90 @@ __device__ __forceinline__ float4 op_load4(const void* p, int64_t idx, int type)
   return make_float4(__low2float(lo), __high2float(lo), __low2float(hi), __high2float(hi));
 }
 
-__global__ void k_copy_best(const void* __restrict__ bits, int op_type, uint8_t* bestBits,
-                            const uint8_t* __restrict__ improved, int n, int B, int64_t ld, int layout) {
-  const int64_t inner = layout == LAYOUT_RN ? n : B;
-  const int64_t outer = layout == LAYOUT_RN ? B : n;
-  for (int64_t o = blockIdx.y; o < outer; o += gridDim.y) {
-    if (layout == LAYOUT_RN && !improved[o]) continue;   // whole restart row unchanged
-    for (int64_t q = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); q < inner;
-         q += 4 * (int64_t)gridDim.x * blockDim.x) {
-      const int64_t idx = o * ld + q;
-      const float4 v = op_load4(bits, idx, op_type);
-      uchar4 nb = make_uchar4(v.x != 0.f, v.y != 0.f, v.z != 0.f, v.w != 0.f);
-      if (layout == LAYOUT_NR) {
-        const uchar4 imp = *reinterpret_cast<const uchar4*>(improved + q);
-        const uchar4 old = *reinterpret_cast<const uchar4*>(bestBits + idx);
-        nb.x = imp.x ? nb.x : old.x;
-        nb.y = imp.y ? nb.y : old.y;
-        nb.z = imp.z ? nb.z : old.z;
-        nb.w = imp.w ? nb.w : old.w;
-      }
-      *reinterpret_cast<uchar4*>(bestBits + idx) = nb;   // padding columns stay consistent
-    }
-  }
+__device__ __forceinline__ bool improves(const CommitArgs& a, int64_t r) {
+  return r < a.B && (long long)a.F2[r] / 2 < a.bestF[r];
 }
 
-__global__ void __launch_bounds__(1024) k_eval_finalize(unsigned long long* F2, const long long* __restrict__ evalF,
-                                                        long long* trace, long long* n_evals, long long trace_cap,
-                                                        int B, long long* t_last, long long add) {
-  __shared__ long long red[32];
+// One launch per evaluation (per group member along z).  Every block copies the candidate bits of
+// the restarts that improve on their best, deciding from F2 and the best records as they were
+// before this evaluation (nothing writes them until every block is done).  The last block to
+// finish (arrival counter, no waiting) then commits: F_r = 2F/2 into evalF, strict improvements
+// into (bestF, bestT) so that equal values keep the earliest t, min_r F_r into the trace, F2 back
+// to zero, t_last advanced, counter back to zero.
+//
+// Threads: `tpr` (a power of two) consecutive threads cover 4·tpr consecutive elements of the
+// contiguous dimension (restarts in the variable-major layout, variables in the restart-major
+// one); a block covers 256 / tpr lines of the other dimension at a time.
+__global__ void __launch_bounds__(256) k_eval_commit(CommitArgs one, const CommitArgs* __restrict__ tab, int tpr,
+                                                     long long add) {
+  const CommitArgs& a = tab ? tab[blockIdx.z] : one;
+  const bool rn = a.layout == LAYOUT_RN;
+  const int64_t inner = rn ? a.n : a.B;
+  const int64_t outer = rn ? a.B : a.n;
+  const int64_t V = (inner + 3) / 4;
+  const int lq = threadIdx.x & (tpr - 1);
+  const int lr = threadIdx.x / tpr;
+  const int rpb = blockDim.x / tpr;
+  if (rn) {
+    for (int64_t o = (int64_t)blockIdx.y * rpb + lr; o < outer; o += (int64_t)gridDim.y * rpb) {
+      if (!improves(a, o)) continue;   // whole restart row unchanged
+      for (int64_t qv = (int64_t)blockIdx.x * tpr + lq; qv < V; qv += (int64_t)gridDim.x * tpr) {
+        const int64_t idx = o * a.ld + 4 * qv;
+        const float4 v = op_load4(a.bits, idx, a.op_type);
+        *reinterpret_cast<uchar4*>(a.bestBits + idx) = make_uchar4(v.x != 0.f, v.y != 0.f, v.z != 0.f, v.w != 0.f);
+      }
+    }
+  } else {
+    for (int64_t qv = (int64_t)blockIdx.x * tpr + lq; qv < V; qv += (int64_t)gridDim.x * tpr) {
+      const int64_t q = 4 * qv;
+      const bool i0 = improves(a, q), i1 = improves(a, q + 1), i2 = improves(a, q + 2), i3 = improves(a, q + 3);
+      if (!(i0 || i1 || i2 || i3)) continue;
+      for (int64_t o = (int64_t)blockIdx.y * rpb + lr; o < outer; o += (int64_t)gridDim.y * rpb) {
+        const int64_t idx = o * a.ld + q;
+        const float4 v = op_load4(a.bits, idx, a.op_type);
+        uchar4 nb = *reinterpret_cast<const uchar4*>(a.bestBits + idx);   // padding restarts keep theirs
+        if (i0) nb.x = v.x != 0.f;
+        if (i1) nb.y = v.y != 0.f;
+        if (i2) nb.z = v.z != 0.f;
+        if (i3) nb.w = v.w != 0.f;
+        *reinterpret_cast<uchar4*>(a.bestBits + idx) = nb;
+      }
+    }
+  }
+  // last-block-done: the block that completes the count commits the evaluation
+  __shared__ int s_last;
+  __shared__ long long red[8];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(a.ctr, 1u) == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const long long t = *a.t_last + add;
   long long m = LLONG_MAX;
-  for (int r = threadIdx.x; r < B; r += blockDim.x) {
-    m = min(m, evalF[r]);
-    F2[r] = 0ull;
+  for (int r = threadIdx.x; r < a.B; r += blockDim.x) {
+    const long long F = (long long)a.F2[r] / 2;
+    a.evalF[r] = F;
+    if (F < a.bestF[r]) {
+      a.bestF[r] = F;
+      a.bestT[r] = t;
+    }
+    a.F2[r] = 0ull;
+    m = min(m, F);
   }
   for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : LLONG_MAX;
-    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) {
-      const long long e = *n_evals;
-      if (e < trace_cap) trace[e] = m;
-      *n_evals = e + 1;
-      *t_last += add;
-    }
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = min(m, red[w]);
+    m = min(m, red[0]);
+    const long long e = *a.n_evals;
+    if (e < a.trace_cap) a.trace[e] = m;
+    *a.n_evals = e + 1;
+    *a.t_last = t;
+    *a.ctr = 0u;
   }
 }
 
@@ -120,27 +142,39 @@ __global__ void __launch_bounds__(1024) k_best_select(const long long* __restric
   }
 }
 
-cudaError_t launch_eval_compare(const unsigned long long* F2, long long* bestF, long long* bestT,
-                                uint8_t* improved, long long* evalF, int B, long long* t_last, int64_t add,
-                                cudaStream_t s) {
-  k_eval_compare<<<(B + 255) / 256, 256, 0, s>>>(F2, bestF, bestT, improved, evalF, B, t_last, add);
+// Grid of the commit kernel: the contiguous dimension in runs of 4·tpr elements (tpr the smallest
+// power of two >= its 4-vectors, at most 256), about four blocks per SM in all.
+static void commit_grid(int64_t inner, int64_t outer, int& tpr, dim3& grid) {
+  const int64_t V = (inner + 3) / 4;
+  tpr = 1;
+  while (tpr < 256 && tpr < V) tpr *= 2;
+  const int rpb = 256 / tpr;
+  int64_t bx = (V + tpr - 1) / tpr;
+  if (bx > 64) bx = 64;
+  int64_t by = (outer + rpb - 1) / rpb;
+  const int64_t cap = std::max<int64_t>(1, 608 / bx);
+  if (by > cap) by = cap;
+  if (by > 65535) by = 65535;
+  grid = dim3((unsigned)bx, (unsigned)std::max<int64_t>(by, 1));
+}
+
+cudaError_t launch_eval_commit(const CommitArgs& a, int64_t add, cudaStream_t s) {
+  int tpr;
+  dim3 grid;
+  commit_grid(a.layout == LAYOUT_RN ? a.n : a.B, a.layout == LAYOUT_RN ? a.B : a.n, tpr, grid);
+  k_eval_commit<<<grid, 256, 0, s>>>(a, nullptr, tpr, (long long)add);
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy_best(const void* bits_op, int op_type, uint8_t* bestBits, const uint8_t* improved,
-                             int n, int B, int64_t ld, int layout, cudaStream_t s) {
-  const int64_t inner = layout == LAYOUT_RN ? n : B;
-  const int64_t outer = layout == LAYOUT_RN ? B : n;
-  const int64_t bx = (inner + 1023) / 1024;
-  dim3 grid((unsigned)(bx < 64 ? bx : 64), (unsigned)(outer < 65535 ? outer : 65535));
-  k_copy_best<<<grid, 256, 0, s>>>(bits_op, op_type, bestBits, improved, n, B, ld, layout);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_eval_finalize(unsigned long long* F2, const long long* evalF, long long* trace,
-                                 long long* n_evals, int64_t trace_cap, int B, long long* t_last, int64_t add,
-                                 cudaStream_t s) {
-  k_eval_finalize<<<1, 1024, 0, s>>>(F2, evalF, trace, n_evals, trace_cap, B, t_last, add);
+cudaError_t launch_eval_commit_group(const CommitArgs* d_tab, int members, int64_t max_inner, int64_t max_outer,
+                                     int64_t add, cudaStream_t s) {
+  int tpr;
+  dim3 grid;
+  commit_grid(max_inner, max_outer, tpr, grid);
+  grid.z = (unsigned)members;
+  CommitArgs none;
+  std::memset(&none, 0, sizeof(none));
+  k_eval_commit<<<grid, 256, 0, s>>>(none, d_tab, tpr, (long long)add);
   return cudaGetLastError();
 }
 

@@ -58,14 +58,19 @@ cudaError_t launch_tiny(const TinyArgs& a, cudaStream_t s);
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
                        const EpiArgs& a, int op_type, int mode, cudaStream_t s);
 // k_best.cu
-cudaError_t launch_eval_compare(const unsigned long long* F2, long long* bestF, long long* bestT,
-                                uint8_t* improved, long long* evalF, int B, long long* t_last,
-                                int64_t add, cudaStream_t s);
-cudaError_t launch_copy_best(const void* bits_op, int op_type, uint8_t* bestBits, const uint8_t* improved,
-                             int n, int B, int64_t ld, int layout, cudaStream_t s);
-cudaError_t launch_eval_finalize(unsigned long long* F2, const long long* evalF, long long* trace,
-                                 long long* n_evals, int64_t trace_cap, int B, long long* t_last, int64_t add,
-                                 cudaStream_t s);
+struct CommitArgs {
+  const void* bits;              // candidate bits of this evaluation (operand type, state layout)
+  int op_type, layout, n, B;
+  int64_t ld;
+  uint8_t* bestBits;             // per-restart best bits, state layout
+  unsigned long long* F2;        // [B] 2F of the candidates (zeroed by the commit)
+  long long *bestF, *bestT, *evalF, *trace, *n_evals, *t_last;
+  long long trace_cap;
+  unsigned int* ctr;             // arrival counter, zero between launches
+};
+cudaError_t launch_eval_commit(const CommitArgs& a, int64_t add, cudaStream_t s);
+cudaError_t launch_eval_commit_group(const CommitArgs* d_tab, int members, int64_t max_inner, int64_t max_outer,
+                                     int64_t add, cudaStream_t s);
 cudaError_t launch_best_select(const long long* bestF, const long long* bestT, int B,
                                long long* out3, cudaStream_t s);
 // k_tc.cu  (tcgen05 BF16 contraction with fused epilogue, restart-major state)
