@@ -446,6 +446,7 @@ def run_sparse(args):
     p = W.graph_params("maxcut", restarts=B, iters=10**9, eval_every=10, seed=0)
     stream = torch.cuda.Stream()
     P = S.Problem.csr(n, rowptr, col, val, c, precision=prec, stream=stream)
+    P.set_option(S.SBO_OPT_PDL, 0 if args.no_pdl else 1)
     P.start(S.params(**p.asdict()))
     K = 10
     with torch.cuda.stream(stream):
@@ -463,7 +464,7 @@ def run_sparse(args):
     ms = e0.elapsed_time(e1) / (args.steps * K)
     per_elem = 16 if prec == S.SBO_FP32 else 22
     print(json.dumps({"workload": args.workload, "n": n, "restarts": B, "precision": args.precision,
-                      "us_per_iter": ms * 1e3, "restart_iterations_per_s": B / (ms * 1e-3),
+                      "pdl": not args.no_pdl, "us_per_iter": ms * 1e3, "restart_iterations_per_s": B / (ms * 1e-3),
                       "state_gbs": n * B * per_elem / (ms * 1e-3) / 1e9}), flush=True)
     P.close()
     return 0
@@ -578,6 +579,8 @@ def main():
                     help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
                     help="weight/operand precision of a sparse workload")
+    ap.add_argument("--no-pdl", action="store_true",
+                    help="sparse workloads: plain stream order instead of programmatic dependent launches")
     ap.add_argument("--degree", type=int, default=3, help="MIS workload: graph degree")
     ap.add_argument("--mis-params", default="paper", choices=["paper", "scaled"],
                     help="MIS workload: the paper's table (ybar=5, alpha=beta=0.02) or the spectral scaling")

@@ -181,9 +181,12 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       tiles are summed in a fixed order, so results do not depend on it.
  *   SBO_OPT_TIMEOUT_US: budget in microseconds of every bounded device-side wait (default
  *                       4,000,000); on expiry the kernel returns early and sbo_sync reports
- *                       SBO_ETIMEOUT */
+ *                       SBO_ETIMEOUT
+ *   SBO_OPT_PDL:        1 (default): the sparse kernel's iterations are launched as programmatic
+ *                       dependents of the previous kernel (the launch of iteration t+1 overlaps
+ *                       iteration t; results identical); 0: plain stream order */
 enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4, SBO_OPT_SPLIT_K = 5,
-       SBO_OPT_AUTOTUNE = 6 };
+       SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7 };
 sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
 
 /* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL),

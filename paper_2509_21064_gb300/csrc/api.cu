@@ -96,7 +96,7 @@ struct sbo_problem {
   int64_t* cp64 = nullptr;
   uint32_t* err = nullptr;
   // options
-  int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0, opt_split_k = 16, opt_autotune = 1;
+  int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0, opt_split_k = 16, opt_autotune = 1, opt_pdl = 1;
   int64_t opt_timeout_us = 4000000;
   // run
   bool started = false;
@@ -207,7 +207,7 @@ cudaError_t contract(sbo_problem* p, const EpiArgs& a, int mode, int which_x, cu
   switch (p->kernel) {
     case KER_SIMT: return launch_simt(static_cast<const float*>(p->A), p->lda, a, mode, s);
     case KER_TC: return launch_tc(p->plan, which_x, nullptr, a, mode, timeout_ns(p), s);
-    case KER_CSR: return launch_csr(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, mode, s);
+    case KER_CSR: return launch_csr(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, mode, p->opt_pdl != 0, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -688,6 +688,7 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       p->opt_tile_n = (int)value;
       return SBO_OK;
     case SBO_OPT_AUTOTUNE: p->opt_autotune = value != 0; return SBO_OK;
+    case SBO_OPT_PDL: p->opt_pdl = value != 0; return SBO_OK;
     case SBO_OPT_SPLIT_K:
       if (value < 0 || value > 64) return fail(SBO_EINVAL, "split-K factor must be in [0, 64]");
       p->opt_split_k = (int)value;
@@ -939,7 +940,7 @@ sbo_status sbo_eval(sbo_problem* p, int64_t count, const uint8_t* bits, int64_t*
   if (e == cudaSuccess) {
     ++p->launches;
     if (p->fmt == FMT_CSR) {
-      e = launch_csr(p->rowptr, p->col, p->val, p->val_type, a, op, EPI_EVAL, s);
+      e = launch_csr(p->rowptr, p->col, p->val, p->val_type, a, op, EPI_EVAL, false, s);
     } else if (p->prec == SBO_FP32) {
       e = launch_simt(static_cast<const float*>(p->A), p->lda, a, EPI_EVAL, s);
     } else {

@@ -66,7 +66,38 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
 #pragma unroll
     for (int k = 0; k < 4; ++k) f2[v][k] = 0;
 
-  for (int64_t i = warp0; i < n; i += nwarps) {
+  // The structure of the warp's first row (constant for the whole run) is read before waiting on
+  // the previous kernel, so its dependent loads (row pointer, then indices and weights) overlap
+  // that kernel's tail under programmatic dependent launch.
+  int64_t i = warp0;
+  int e0 = 0, e1 = 0, col0 = 0;
+  float val0 = 0.0f, cpi = 0.0f;
+  long long cp2 = 0;
+  if (i < n) {
+    e0 = __ldg(rowptr + i);
+    e1 = __ldg(rowptr + i + 1);
+    const int k = e0 + lane;
+    col0 = k < e1 ? __ldg(col + k) : 0;
+    val0 = k < e1 ? load_val(val, k, vt) : 0.0f;
+    cpi = a.cp[i];
+    if (MODE == EPI_EVAL) cp2 = 2 * (long long)a.cp64[i];
+  }
+  // Programmatic dependent launch (a no-op when launched without it): wait until the previous
+  // kernel of the stream has completed and its writes are visible, then let the next one be
+  // scheduled, so that its launch overlaps this kernel instead of following it.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
+  for (; i < n; i += nwarps) {
+    if (i != warp0) {
+      e0 = __ldg(rowptr + i);
+      e1 = __ldg(rowptr + i + 1);
+      const int k = e0 + lane;
+      col0 = k < e1 ? __ldg(col + k) : 0;
+      val0 = k < e1 ? load_val(val, k, vt) : 0.0f;
+      cpi = a.cp[i];
+      if (MODE == EPI_EVAL) cp2 = 2 * (long long)a.cp64[i];
+    }
     // the row's own state first: independent of the gathers
     float4 xo[NV], yo[NV];
 #pragma unroll
@@ -87,11 +118,14 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
     float4 acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int e0 = __ldg(rowptr + i), e1 = __ldg(rowptr + i + 1);
     for (int eb = e0; eb < e1; eb += 32) {
-      const int k = eb + lane;
-      const int mycol = k < e1 ? __ldg(col + k) : 0;
-      const float myval = k < e1 ? load_val(val, k, vt) : 0.0f;
+      int mycol = col0;
+      float myval = val0;
+      if (eb != e0) {
+        const int k = eb + lane;
+        mycol = k < e1 ? __ldg(col + k) : 0;
+        myval = k < e1 ? load_val(val, k, vt) : 0.0f;
+      }
       const int cnt = min(32, e1 - eb);
 #pragma unroll 4
       for (int q = 0; q < cnt; ++q) {
@@ -110,8 +144,6 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
         }
       }
     }
-    const float cpi = a.cp[i];
-    const long long cp2 = MODE == EPI_EVAL ? 2 * (long long)a.cp64[i] : 0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int64_t r0 = rbase + 128 * v;
@@ -161,7 +193,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
 
 template <int MODE, int OPT>
 static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const void* val, int vt,
-                                const EpiArgs& a, cudaStream_t s) {
+                                const EpiArgs& a, bool pdl, cudaStream_t s) {
   // at most 256 restarts per warp: fewer registers, more warps in flight (this kernel is bound
   // by memory latency)
   int NV = 1;
@@ -174,24 +206,29 @@ static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const
     if (want > cap) want = cap;
   }
   if (want > 65535) want = 65535;
-  dim3 grid((unsigned)want, (unsigned)chunks);
-  switch (NV) {
-    case 1: k_csr<MODE, 1, OPT><<<grid, 256, 0, s>>>(rowptr, col, val, vt, a); break;
-    default: k_csr<MODE, 2, OPT><<<grid, 256, 0, s>>>(rowptr, col, val, vt, a); break;
-  }
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)want, (unsigned)chunks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  if (NV == 1) return cudaLaunchKernelEx(&cfg, k_csr<MODE, 1, OPT>, rowptr, col, val, vt, a);
+  return cudaLaunchKernelEx(&cfg, k_csr<MODE, 2, OPT>, rowptr, col, val, vt, a);
 }
 
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
-                       const EpiArgs& a, int op_type, int mode, cudaStream_t s) {
+                       const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s) {
   if (a.ld % 8 != 0) return cudaErrorInvalidValue;  // vector accesses need 16-byte rows
   if (mode == EPI_UPDATE) {
-    return op_type == OP_F32 ? launch_csr_v<EPI_UPDATE, OP_F32>(rowptr, col, val, val_type, a, s)
-                             : launch_csr_v<EPI_UPDATE, OP_BF16>(rowptr, col, val, val_type, a, s);
+    return op_type == OP_F32 ? launch_csr_v<EPI_UPDATE, OP_F32>(rowptr, col, val, val_type, a, pdl, s)
+                             : launch_csr_v<EPI_UPDATE, OP_BF16>(rowptr, col, val, val_type, a, pdl, s);
   }
   if (mode == EPI_EVAL) {
-    return op_type == OP_F32 ? launch_csr_v<EPI_EVAL, OP_F32>(rowptr, col, val, val_type, a, s)
-                             : launch_csr_v<EPI_EVAL, OP_BF16>(rowptr, col, val, val_type, a, s);
+    return op_type == OP_F32 ? launch_csr_v<EPI_EVAL, OP_F32>(rowptr, col, val, val_type, a, pdl, s)
+                             : launch_csr_v<EPI_EVAL, OP_BF16>(rowptr, col, val, val_type, a, pdl, s);
   }
   return cudaErrorInvalidValue;
 }

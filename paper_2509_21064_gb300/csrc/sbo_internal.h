@@ -54,9 +54,9 @@ struct TinyArgs {
   long long* evalF;        // scratch [B], F of the current evaluation
 };
 cudaError_t launch_tiny(const TinyArgs& a, cudaStream_t s);
-// k_csr.cu  (variable-major state)
+// k_csr.cu  (variable-major state); pdl: launch as a programmatic dependent of the previous kernel
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
-                       const EpiArgs& a, int op_type, int mode, cudaStream_t s);
+                       const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s);
 // k_best.cu
 struct CommitArgs {
   const void* bits;              // candidate bits of this evaluation (operand type, state layout)
