@@ -204,7 +204,9 @@ sbo_status sbo_info(const sbo_problem* p, int64_t* n, int32_t* restarts, int32_t
  * sbo_group_start: prms[count]; members share iters and eval_every (else SBO_EINVAL); starts
  *   every member (x^0 from its seed) on the group's tile width.
  * sbo_group_run / sbo_group_sync: as sbo_gda_run / sbo_sync for the whole group.
- * sbo_group_set_option: SBO_OPT_USE_GRAPH, SBO_OPT_TILE_N (default 128; before start). */
+ * sbo_group_set_option: SBO_OPT_USE_GRAPH, SBO_OPT_TILE_N (64, 128 or 256 restarts per tile; default
+ * 0: sbo_group_start times each width on the group's own instance table over a few update launches
+ * and keeps the fastest; set before start). */
 typedef struct sbo_group sbo_group;
 sbo_status sbo_group_create(int32_t count, sbo_problem* const* problems, void* stream, sbo_group** out);
 sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms);

@@ -1141,7 +1141,8 @@ struct sbo_group {
   std::vector<int> order;             // member indices by decreasing n (instance table order)
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
-  int tile_n = 128;
+  int tile_n = 128;           // width in use
+  int opt_tile_n = 0;         // requested width; 0 = autotune at start
   TcInst* d_insts = nullptr;
   CommitArgs* d_commit = nullptr;     // per-member evaluation commit arguments
   int64_t max_n = 0, max_B = 0;
@@ -1216,36 +1217,7 @@ void group_sync_members(sbo_group* g) {
   }
 }
 
-}  // namespace
-
-extern "C" {
-
-sbo_status sbo_group_create(int32_t count, sbo_problem* const* problems, void* stream, sbo_group** out) {
-  g_last_error.clear();
-  if (!out) return fail(SBO_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (count < 1 || !problems) return fail(SBO_EINVAL, "count must be >= 1 and problems non-NULL");
-  for (int32_t k = 0; k < count; ++k) {
-    if (!problems[k]) return fail(SBO_EINVAL, "a member problem is NULL");
-    if (problems[k]->fmt != FMT_DENSE || problems[k]->prec != SBO_BF16)
-      return fail(SBO_EINVAL, "grouped runs take dense BF16 problems");
-    for (int32_t q = 0; q < k; ++q)
-      if (problems[q] == problems[k]) return fail(SBO_EINVAL, "a problem appears twice in the group");
-  }
-  if (!tc_supported()) return fail(SBO_ECUDA, "grouped runs need a compute capability 10.3 device");
-  sbo_group* g = new (std::nothrow) sbo_group();
-  if (!g) return fail(SBO_ENOMEM, "host allocation failed");
-  g->members.assign(problems, problems + count);
-  g->stream = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
-  if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaStreamCreate"); }
-  *out = g;
-  return SBO_OK;
-}
-
-sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms) {
-  g_last_error.clear();
-  if (!g || !prms) return fail(SBO_EINVAL, "group or params is NULL");
+sbo_status group_start_tile(sbo_group* g, const sbo_gda_params* prms, int tile_n) {
   const size_t cnt = g->members.size();
   for (size_t k = 0; k < cnt; ++k) {
     sbo_status st = check_params(&prms[k]);
@@ -1262,7 +1234,7 @@ sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms) {
   for (size_t k = 0; k < cnt; ++k) {
     sbo_problem* p = g->members[k];
     p->opt_kernel = KER_TC;
-    p->opt_tile_n = g->tile_n;
+    p->opt_tile_n = tile_n;
     p->opt_split_k = 0;
     sbo_status st = sbo_gda_start(p, &prms[k], nullptr);
     if (st != SBO_OK) return st;
@@ -1291,12 +1263,13 @@ sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms) {
     EpiArgs ev = base_args(p);
     ev.Xin = p->bits;
     I.epi[4] = ev;
-    I.n_tiles = (p->B + g->tile_n - 1) / g->tile_n;
+    I.n_tiles = (p->B + tile_n - 1) / tile_n;
     I.kblocks = (int)((p->n + 63) / 64);
     I.tile_begin = tiles;
     tiles += (int)((p->n + 127) / 128) * I.n_tiles;
   }
   g->num_tiles = tiles;
+  g->tile_n = tile_n;
   SBO_CUDA(cudaMalloc(&g->d_insts, sizeof(TcInst) * cnt));
   SBO_CUDA(cudaMemcpy(g->d_insts, tab.data(), sizeof(TcInst) * cnt, cudaMemcpyHostToDevice));
   std::vector<CommitArgs> ctab(cnt);
@@ -1315,6 +1288,70 @@ sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms) {
   g->started = true;
   group_sync_members(g);
   return SBO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sbo_status sbo_group_create(int32_t count, sbo_problem* const* problems, void* stream, sbo_group** out) {
+  g_last_error.clear();
+  if (!out) return fail(SBO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !problems) return fail(SBO_EINVAL, "count must be >= 1 and problems non-NULL");
+  for (int32_t k = 0; k < count; ++k) {
+    if (!problems[k]) return fail(SBO_EINVAL, "a member problem is NULL");
+    if (problems[k]->fmt != FMT_DENSE || problems[k]->prec != SBO_BF16)
+      return fail(SBO_EINVAL, "grouped runs take dense BF16 problems");
+    for (int32_t q = 0; q < k; ++q)
+      if (problems[q] == problems[k]) return fail(SBO_EINVAL, "a problem appears twice in the group");
+  }
+  if (!tc_supported()) return fail(SBO_ECUDA, "grouped runs need a compute capability 10.3 device");
+  sbo_group* g = new (std::nothrow) sbo_group();
+  if (!g) return fail(SBO_ENOMEM, "host allocation failed");
+  g->members.assign(problems, problems + count);
+  g->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaStreamCreate"); }
+  *out = g;
+  return SBO_OK;
+}
+
+// Tile width of a group: the one given, or (0) the fastest of the candidates, each timed on the
+// group's own instance table over a few grouped update launches.
+sbo_status sbo_group_start(sbo_group* g, const sbo_gda_params* prms) {
+  g_last_error.clear();
+  if (!g || !prms) return fail(SBO_EINVAL, "group or params is NULL");
+  if (g->opt_tile_n != 0) return group_start_tile(g, prms, g->opt_tile_n);
+  int max_B = 1;
+  for (size_t k = 0; k < g->members.size(); ++k) max_B = std::max(max_B, prms[k].restarts);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SBO_CUDA(cudaEventCreate(&e0));
+  SBO_CUDA(cudaEventCreate(&e1));
+  int best = 128;
+  float best_ms = 1e30f;
+  sbo_status st = SBO_OK;
+  for (int tn : {64, 128, 256}) {
+    if (tn > 64 && tn / 2 >= max_B) continue;
+    st = group_start_tile(g, prms, tn);
+    if (st != SBO_OK) break;
+    const int reps = 3;
+    cudaError_t e = group_step(g, false, g->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = group_step(g, false, g->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { st = cuda_fail(e, "group autotuner launch"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = tn; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SBO_OK) return st;
+  st = read_err(g->members[0]);
+  if (st != SBO_OK) return st;
+  return group_start_tile(g, prms, best);   // fresh state on the chosen width
 }
 
 sbo_status sbo_group_run(sbo_group* g, int64_t iters) {
@@ -1376,8 +1413,9 @@ sbo_status sbo_group_set_option(sbo_group* g, int32_t option, int64_t value) {
   if (!g) return fail(SBO_EINVAL, "group is NULL");
   if (option == SBO_OPT_USE_GRAPH) { g->opt_graph = value != 0; return SBO_OK; }
   if (option == SBO_OPT_TILE_N) {
-    if (value != 64 && value != 128 && value != 256) return fail(SBO_EINVAL, "tile_n must be 64, 128 or 256");
-    g->tile_n = (int)value;
+    if (value != 0 && value != 64 && value != 128 && value != 256)
+      return fail(SBO_EINVAL, "tile_n must be 0 (autotune), 64, 128 or 256");
+    g->opt_tile_n = (int)value;
     return SBO_OK;
   }
   return fail(SBO_EINVAL, "groups take SBO_OPT_USE_GRAPH and SBO_OPT_TILE_N");

@@ -14,7 +14,9 @@ from _helpers import normwise, oracle_trajectory, to_gda_params
 pytestmark = pytest.mark.gpu
 
 
-def test_group_matches_members_run_alone_and_the_oracle():
+@pytest.mark.parametrize("tile", [0, 64])
+def test_group_matches_members_run_alone_and_the_oracle(tile):
+    """tile 0: the group autotunes its width at start; 64: fixed."""
     build_lib()
     insts = W.heterogeneous_qubos(24, seed=3, n_lo=60, n_hi=700)
     Bs = [128] * 20 + [64, 200, 130, 1]
@@ -23,7 +25,11 @@ def test_group_matches_members_run_alone_and_the_oracle():
     members = [S.Problem.dense(Q, c, precision=S.SBO_BF16) for Q, c in insts]
     try:
         with S.Group(members) as G:
+            G.set_option(S.SBO_OPT_TILE_N, tile)
             G.start(prms)
+            chosen = members[0].info()["tile_n"]
+            assert chosen in ((64, 128, 256) if tile == 0 else (tile,))
+            assert all(P.info()["tile_n"] == chosen for P in members)
             G.run(25)                       # two graph-replayed blocks and five direct steps
             G.sync()
             assert G.launch_count() > 0
@@ -32,7 +38,7 @@ def test_group_matches_members_run_alone_and_the_oracle():
             traces = [P.trace() for P in members]
         for k, ((Q, c), prm) in enumerate(zip(insts, prms)):
             with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
-                P.set_option(S.SBO_OPT_TILE_N, 128)
+                P.set_option(S.SBO_OPT_TILE_N, chosen)
                 P.set_option(S.SBO_OPT_SPLIT_K, 0)
                 P.start(prm)
                 P.run(25)

@@ -11,6 +11,7 @@ from .generators import (  # noqa: F401
     maxcut_regular,
     mis_regular,
     heterogeneous_qubos,
+    iter_heterogeneous_qubos,
     csr_from_edges,
     maxcut_qubo,
     spectral_scale,

@@ -70,16 +70,21 @@ def dense_qubo(n: int, seed: int = 0, lo: int = -100, hi: int = 100, density: fl
     return Q, c
 
 
-def heterogeneous_qubos(count: int, seed: int = 0, n_lo: int = 500, n_hi: int = 20000,
-                        dens_lo: float = 0.01, dens_hi: float = 1.0, lo: int = -100, hi: int = 100):
-    """``count`` dense QUBOs with n ~ U{n_lo..n_hi} and density ~ U[dens_lo, dens_hi]."""
+def iter_heterogeneous_qubos(count: int, seed: int = 0, n_lo: int = 500, n_hi: int = 20000,
+                             dens_lo: float = 0.01, dens_hi: float = 1.0, lo: int = -100, hi: int = 100):
+    """Yield ``count`` dense QUBOs ``(Q, c)`` with n ~ U{n_lo..n_hi} and density ~ U[dens_lo,
+    dens_hi], one at a time (at n_hi = 20,000 the whole batch is ~35 GB of int32 on the host)."""
     rng = _rng(seed, _TAG_HETERO)
-    out = []
     for _ in range(count):
         n = int(rng.integers(n_lo, n_hi + 1))
         d = float(rng.uniform(dens_lo, dens_hi))
-        out.append(dense_qubo(n, lo=lo, hi=hi, density=d, rng=rng))
-    return out
+        yield dense_qubo(n, lo=lo, hi=hi, density=d, rng=rng)
+
+
+def heterogeneous_qubos(count: int, seed: int = 0, n_lo: int = 500, n_hi: int = 20000,
+                        dens_lo: float = 0.01, dens_hi: float = 1.0, lo: int = -100, hi: int = 100):
+    """The same instances as ``iter_heterogeneous_qubos``, as a list."""
+    return list(iter_heterogeneous_qubos(count, seed, n_lo, n_hi, dens_lo, dens_hi, lo, hi))
 
 
 # ----------------------------------------------------------------------------------------
