@@ -377,8 +377,12 @@ def run_ours(args):
     achieved = flops / t_kernel / 1e12
     peak = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
     peak_burst = float(pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
-    kname = "k_tc_pair<EPI_UPDATE> (CTA pairs, 256x256 tiles)" if info["tile_n"] == 512 else \
-        f"k_tc<{info['tile_n']}, EPI_UPDATE, false>"
+    if info["tile_n"] == 512:
+        kname = "k_tc_pair<EPI_UPDATE> (CTA pairs, 256x256 tiles)"
+    elif info["tile_n"] > 1000:
+        kname = f"k_tc_csk<{info['tile_n'] - 1000}, EPI_UPDATE> (split-K over a thread-block cluster)"
+    else:
+        kname = f"k_tc<{info['tile_n']}, EPI_UPDATE, false>"
     line = {
         "metric": METRIC, "value": value, "unit": "restart-iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -169,7 +169,11 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *   SBO_OPT_USE_GRAPH:  1 (default) replay blocks of K iterations from a CUDA graph; 0 launch
  *                       every kernel directly
  *   SBO_OPT_TILE_N:     restarts per tensor-core tile: 0 auto, 64, 128 or 256 (one SM per
- *                       128-row tile), or 512: CTA pairs (two SMs per 256 x 256 tile)
+ *                       128-row tile), 512: CTA pairs (two SMs per 256 x 256 tile), or
+ *                       1064, 1128, 1256: width 64, 128, 256 with the K dimension of every tile
+ *                       split over a thread-block cluster of 2-8 SMs, reduced in distributed
+ *                       shared memory (problems with at most half as many tiles as SMs; others
+ *                       fall back to the plain width)
  *   SBO_OPT_AUTOTUNE:   1 (default): with SBO_OPT_TILE_N = 0, sbo_gda_start times the tcgen05
  *                       update kernel at every tile width on the run's own buffers and keeps
  *                       the fastest; decisions are cached per (device, n, B, SM count) in the

@@ -348,6 +348,10 @@ sbo_status run_tiny(sbo_problem* p, int64_t steps) {
 sbo_status read_err(sbo_problem* p);
 
 // Widest tile that still gives every SM a tile (else the widest), never wider than needed.
+// Tile codes: 64, 128, 256 restarts per single-CTA tile; 512 CTA pairs (256 x 256 tiles);
+// 1000 + w: width w with split-K over a thread-block cluster (small problems).
+int tile_width(int code) { return code == 512 ? 128 : code >= 1000 ? code - 1000 : code; }
+
 int heuristic_tile(const sbo_problem* p) {
   int tn = 256;
   while (tn > 64 && (int64_t)((p->n + 127) / 128) * ((p->B + tn - 1) / tn) < p->sms) tn /= 2;
@@ -382,7 +386,7 @@ std::string tune_key(const sbo_problem* p) {
   for (auto& ch : name)
     if (ch == ' ') ch = '_';
   std::ostringstream k;
-  k << "v2:" << name << ":sms" << p->sms << ":n" << p->n << ":B" << p->B << ":split" << p->opt_split_k;
+  k << "v3:" << name << ":sms" << p->sms << ":n" << p->n << ":B" << p->B << ":split" << p->opt_split_k;
   return k.str();
 }
 
@@ -439,15 +443,20 @@ sbo_status tune_tile(sbo_problem* p, int* out) {
   a.Xout = p->Xop[1];
   a.bits_out = nullptr;
   sbo_status st = SBO_OK;
-  for (int tn : {64, 128, 256, 512}) {
-    if (tn > 64 && tn / 2 >= p->B) continue;
+  for (int tn : {64, 128, 256, 512, 1128, 1256}) {
+    const int width = tile_width(tn);
+    if (width > 64 && width / 2 >= p->B) continue;
     if (tn == 512 && !tc_pair_supported(nullptr)) continue;
     TcPlan pl{};
     std::string why;
-    if (tc_make_plan(&pl, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, tn == 512 ? 128 : tn,
-                     &why) != cudaSuccess)
+    if (tc_make_plan(&pl, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B, width, &why) !=
+        cudaSuccess)
       continue;
     pl.pair = tn == 512;
+    if (tn >= 1000) {
+      pl.csk = tc_csk_factor(width, pl.num_tiles, (int)((p->n + 63) / 64), p->sms);
+      if (pl.csk < 2) continue;
+    }
     attach_workspace(p, &pl);
     cudaError_t e = launch_tc(pl, 0, nullptr, a, EPI_UPDATE, timeout_ns(p), p->stream);
     const int reps = 3;
@@ -683,8 +692,9 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       return SBO_OK;
     case SBO_OPT_USE_GRAPH: p->opt_graph = value != 0; return SBO_OK;
     case SBO_OPT_TILE_N:
-      if (value != 0 && value != 64 && value != 128 && value != 256 && value != 512)
-        return fail(SBO_EINVAL, "tile_n must be 0, 64, 128, 256 or 512 (CTA pairs)");
+      if (value != 0 && value != 64 && value != 128 && value != 256 && value != 512 && value != 1064 &&
+          value != 1128 && value != 1256)
+        return fail(SBO_EINVAL, "tile_n must be 0, 64, 128, 256, 512 (CTA pairs) or 1064, 1128, 1256 (cluster split-K)");
       p->opt_tile_n = (int)value;
       return SBO_OK;
     case SBO_OPT_AUTOTUNE: p->opt_autotune = value != 0; return SBO_OK;
@@ -808,11 +818,15 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
       tn = heuristic_tile(p);
     }
     if (tn == 512 && !tc_pair_supported(nullptr)) tn = 256;
-    p->tile_n = tn;
     e = tc_make_plan(&p->plan, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B,
-                     tn == 512 ? 128 : tn, &why);
+                     tile_width(tn), &why);
     if (e != cudaSuccess) { free_run(p); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
     p->plan.pair = tn == 512;
+    if (tn >= 1000) {
+      p->plan.csk = tc_csk_factor(tile_width(tn), p->plan.num_tiles, (int)((p->n + 63) / 64), p->sms);
+      if (p->plan.csk < 2) tn = tile_width(tn);   // too many tiles for clusters: plain tiles
+    }
+    p->tile_n = tn;
     attach_workspace(p, &p->plan);
   } else {
     p->tile_n = 0;

@@ -428,6 +428,7 @@ cudaError_t tc_make_plan(TcPlan* plan, const void* A, int64_t lda, int n, const 
   plan->counters = nullptr;
   plan->max_splits = 0;
   plan->pair = false;
+  plan->csk = 0;
   const cudaError_t attr_err = ensure_attrs();
   if (attr_err != cudaSuccess) {
     if (why) *why = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(attr_err);
@@ -475,6 +476,8 @@ cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_ov
   if (!plan.ready) return cudaErrorInvalidValue;
   if (plan.pair && !map_override && (mode == EPI_UPDATE || mode == EPI_EVAL))
     return launch_tc_pair(plan, which_x, a, mode, timeout_ns, s);
+  if (plan.csk >= 2 && !map_override && (mode == EPI_UPDATE || mode == EPI_EVAL))
+    return launch_tc_csk(plan, which_x, a, mode, timeout_ns, s);
   TcParams P;
   P.mapA = plan.mapA;
   P.mapX = map_override ? *map_override : plan.mapX[which_x];

@@ -84,6 +84,7 @@ struct TcPlan {
   int* counters;           // >= sms * 8 ints, zero before the first launch
   int max_splits;
   bool pair;               // CTA-pair kernel (k_tc2.cu): 256 x 256 tiles; tile_n is then 128
+  int csk;                 // >= 2: split-K over a cluster of csk CTAs per tile (k_tc3.cu)
   bool ready;
 };
 // One instance of a grouped launch (several dense problems in one persistent launch).  The
@@ -115,6 +116,11 @@ cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_ov
                       int mode, uint64_t timeout_ns, cudaStream_t s);
 // k_tc2.cu: CTA-pair variant (update and evaluation epilogues)
 bool tc_pair_supported(int* max_clusters);
+// k_tc3.cu: cluster split-K factor for num_tiles tiles of width tile_n (0: not applicable), and
+// its launch (EPI_UPDATE / EPI_EVAL)
+int tc_csk_factor(int tile_n, int num_tiles, int kblocks, int sms);
+cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,
+                          cudaStream_t s);
 cudaError_t launch_tc_pair(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,
                            cudaStream_t s);
 

@@ -154,6 +154,59 @@ def test_tcgen05_split_k_tail_tiles(n, B, tile):
     assert normwise(runs[0][20], runs[1][20]).max() <= TOL_MIXED
 
 
+@pytest.mark.parametrize("n,B,tile", [(1000, 256, 1256), (2000, 200, 1128), (700, 100, 1064)])
+def test_tcgen05_cluster_split_k(n, B, tile):
+    """Small problems with K split over a thread-block cluster and the partials summed through
+    distributed shared memory in split order (ragged rows and restarts): trajectories within the
+    mixed tolerance of the oracle, exact objectives, graph replay identical to direct launches,
+    and the same iterates as plain tiles of the same width up to the mixed tolerance."""
+    Q, c = W.dense_qubo(n, seed=n + 3)
+    p = W.dense_params(Q, restarts=B, iters=200, eval_every=10, seed=7)
+    prm = to_gda_params(p)
+    ox, oy, _ = oracle_trajectory(Q, c, p, 30)
+    with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
+        P.set_option(S.SBO_OPT_TILE_N, tile)
+        gx, gy = gpu_trajectory(P, prm, 30)
+        assert P.info()["tile_n"] == tile          # the cluster form was applicable and used
+        _check_traj(gx, gy, ox, oy, TOL_MIXED)
+        _check_evals_exact(Q, c, gx, P.trace(), p.eval_every)
+        P.start(prm)
+        P.run(30)
+        X, Y = P.state()
+        assert np.array_equal(X, gx[30]) and np.array_equal(Y, gy[30])
+    with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
+        P.set_option(S.SBO_OPT_TILE_N, tile - 1000)
+        P.start(prm)
+        P.run(30)
+        Xp, _ = P.state()
+    assert normwise(X, Xp).max() <= TOL_MIXED
+
+
+def test_dense_n5000_cluster_split_k_sampled_restarts():
+    """Dense QUBO n = 5,000, B = 256 with the cluster split-K kernel (width 256, 40 tiles):
+    three iterations, restarts 0, 128 and 255 against the oracle on those restarts alone, and
+    their exact objectives."""
+    n, B = 5000, 256
+    Q, c = W.dense_qubo(n, seed=0)
+    p = W.dense_params(Q, restarts=B, iters=1000, eval_every=3, seed=0)
+    with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
+        P.set_option(S.SBO_OPT_TILE_N, 1256)
+        P.start(to_gda_params(p))
+        P.run(3)
+        X, Y = P.state()
+        Fr, tr = P.restart_best()
+        assert P.info()["tile_n"] == 1256
+    sample = [0, 128, 255]
+    A, cp = O.canonicalize(Q, c)
+    X0, _ = O.init_state(n, B, p.seed, p.ybar)
+    ox, oy, _ = oracle_trajectory(None, None, p, 3, X0=X0[sample], A=A, cp=cp)
+    assert normwise(X[sample], ox[3]).max() <= TOL_MIXED
+    assert normwise(Y[sample], oy[3]).max() <= TOL_MIXED
+    for r in sample:
+        assert tr[r] == 3
+        assert Fr[r] == O.objective(Q, c, O.round_bits(X[r]))
+
+
 def test_tcgen05_contraction_is_exact_on_bf16_representable_inputs():
     """With x on a 1/256 grid (exact in BF16) the only error left is FP32 accumulation."""
     import torch
@@ -311,7 +364,7 @@ def test_full_size_dense_n20000_sampled_restarts():
         P.run(3)
         X, Y = P.state()
         Fr, tr = P.restart_best()
-        assert P.info()["tile_n"] in (64, 128, 256, 512)
+        assert P.info()["tile_n"] in (64, 128, 256, 512, 1064, 1128, 1256)
     sample = [0, 517, 1023]
     A, cp = O.canonicalize(Q, c)
     del Q

@@ -12,14 +12,16 @@ from paper_2509_21064_gb300.build import build as build_lib
 pytestmark = pytest.mark.gpu
 
 
-def test_bounded_waits_report_timeout_and_the_context_survives():
+@pytest.mark.parametrize("n,B,tile", [(8192, 1024, 128), (4096, 256, 1256)])
+def test_bounded_waits_report_timeout_and_the_context_survives(n, B, tile):
+    """tile 128: persistent single-CTA tiles; 1256: K split over thread-block clusters, whose
+    CTAs still reach both cluster barriers after giving up."""
     build_lib()
-    n, B = 8192, 1024
     Q, c = W.dense_qubo(n, seed=4)
     p = W.dense_params(Q, restarts=B, iters=100, eval_every=10, seed=2)
     prm = S.params(**p.asdict())
     with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
-        P.set_option(S.SBO_OPT_TILE_N, 128)
+        P.set_option(S.SBO_OPT_TILE_N, tile)
         P.set_option(S.SBO_OPT_TIMEOUT_US, 1)          # 1 us: far below one launch
         P.start(prm)
         P.run(3)
@@ -31,8 +33,9 @@ def test_bounded_waits_report_timeout_and_the_context_survives():
         P.start(prm)
         P.run(20)
         X, Y = P.state()
+        assert P.info()["tile_n"] == tile
     with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P2:
-        P2.set_option(S.SBO_OPT_TILE_N, 128)
+        P2.set_option(S.SBO_OPT_TILE_N, tile)
         P2.start(prm)
         P2.run(20)
         X2, Y2 = P2.state()
