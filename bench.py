@@ -596,7 +596,7 @@ def main():
     ap.add_argument("--mis-params", default="paper", choices=["paper", "scaled"],
                     help="MIS workload: the paper's table (ybar=5, alpha=beta=0.02) or the spectral scaling")
     ap.add_argument("--iters", type=int, default=3000, help="MIS workload: GDA iterations")
-    ap.add_argument("--tile", type=int, default=0, choices=[0, 64, 128, 256, 512],
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 64, 128, 256, 512, 1064, 1128, 1256],
                     help="tensor-core tile width (0: autotuned); profiling cases only")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the device loop only (no e2e, no CPU baseline): for profiling cases")

@@ -397,8 +397,15 @@ bool tune_cache_lookup(const std::string& key, int* tile) {
   std::string k;
   int t = 0;
   bool found = false;
-  while (f >> k >> t)
-    if (k == key && (t == 64 || t == 128 || t == 256 || t == 512)) { *tile = t; found = true; }
+  // a value is the tile code, plus 10000 x the cluster size for the cluster split-K codes
+  while (f >> k >> t) {
+    const int code = t % 10000;
+    if (k == key && (code == 64 || code == 128 || code == 256 || code == 512 ||
+                     ((code == 1064 || code == 1128 || code == 1256) && t / 10000 >= 2 && t / 10000 <= 8))) {
+      *tile = t;
+      found = true;
+    }
+  }
   return found;
 }
 
@@ -415,7 +422,9 @@ void tune_cache_store(const std::string& key, int tile) {
 // Autotuner of the tensor-core tile width: times the update kernel for every candidate width on
 // this run's own buffers (called before x^0 is written, so the trial launches only overwrite
 // state that initialisation rewrites) and keeps the fastest.  Decisions are kept for the life of
-// the process and in the persistent record above.
+// the process and in the persistent record above; a cluster split-K choice is returned (and
+// kept) as code + 10000 x its cluster size, so that a later process, where the occupancy query
+// behind the cluster size may answer differently (under a profiler), launches the same kernel.
 sbo_status tune_tile(sbo_problem* p, int* out) {
   static std::mutex mu;
   static std::map<std::string, int> cache;
@@ -468,7 +477,7 @@ sbo_status tune_tile(sbo_problem* p, int* out) {
     if (e != cudaSuccess) { st = cuda_fail(e, "autotuner launch"); break; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) { best_ms = ms; best = tn; }
+    if (ms < best_ms) { best_ms = ms; best = tn >= 1000 ? tn + 10000 * pl.csk : tn; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -817,13 +826,16 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
     } else if (tn == 0) {
       tn = heuristic_tile(p);
     }
+    const int tuned_csk = tn / 10000;   // cluster size decided by the autotuner (0: none)
+    tn %= 10000;
     if (tn == 512 && !tc_pair_supported(nullptr)) tn = 256;
     e = tc_make_plan(&p->plan, p->A, p->lda, (int)p->n, p->Xop[0], p->Xop[1], p->bits, p->ld, p->B,
                      tile_width(tn), &why);
     if (e != cudaSuccess) { free_run(p); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
     p->plan.pair = tn == 512;
     if (tn >= 1000) {
-      p->plan.csk = tc_csk_factor(tile_width(tn), p->plan.num_tiles, (int)((p->n + 63) / 64), p->sms);
+      p->plan.csk = tuned_csk >= 2 ? tuned_csk
+                                   : tc_csk_factor(tile_width(tn), p->plan.num_tiles, (int)((p->n + 63) / 64), p->sms);
       if (p->plan.csk < 2) tn = tile_width(tn);   // too many tiles for clusters: plain tiles
     }
     p->tile_n = tn;

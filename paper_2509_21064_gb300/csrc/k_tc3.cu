@@ -315,8 +315,22 @@ int tc_csk_factor(int tile_n, int num_tiles, int kblocks, int sms) {
 
 cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,
                           cudaStream_t s) {
-  if (!plan.ready || plan.csk < 2 || plan.pair) return cudaErrorInvalidValue;
+  if (!plan.ready || plan.csk < 2 || plan.csk > 8 || plan.pair) return cudaErrorInvalidValue;
   if (mode != EPI_UPDATE && mode != EPI_EVAL) return cudaErrorInvalidValue;
+  // shared-memory attributes (also set by the occupancy query, which a cached decision skips)
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    cudaError_t r = cudaSuccess;
+    r = r == cudaSuccess ? csk_set_attr<64, EPI_UPDATE>() : r;
+    r = r == cudaSuccess ? csk_set_attr<64, EPI_EVAL>() : r;
+    r = r == cudaSuccess ? csk_set_attr<128, EPI_UPDATE>() : r;
+    r = r == cudaSuccess ? csk_set_attr<128, EPI_EVAL>() : r;
+    r = r == cudaSuccess ? csk_set_attr<256, EPI_UPDATE>() : r;
+    r = r == cudaSuccess ? csk_set_attr<256, EPI_EVAL>() : r;
+    attr_err = r;
+  });
+  if (attr_err != cudaSuccess) return attr_err;
   CskParams P;
   memset(&P, 0, sizeof(P));
   P.mapA = plan.mapA;
