@@ -30,6 +30,13 @@ gda_step            Eq. 5 and Algorithm 1                            hand-worked
                                                                      telescoping invariants;
                                                                      Prop. 3.3 bound; convex
                                                                      special case (KKT)
+lagrangian_single   single-constraint Lagrangian of the PDBO-s        central finite differences;
+                    variant (section 4, Discussion and ablation):    L = F on binary points
+                    f(x) + mu sum_i g(x_i), one dual per restart
+gda_step_single     Algorithm 1 on that Lagrangian                   beta = 0 reduces it to
+                                                                     gda_step exactly; on a
+                                                                     symmetric instance it is
+                                                                     gda_step with beta / n
 round_bits / run    best-of-B retention (section 4.2), evaluation    brute force over 2^n;
                     every K iterations and at T                      tie rules on tiny inputs
 brute_force         Lemma 2.3 (min over the vertices)                exhaustive by definition
@@ -138,6 +145,23 @@ def lagrangian(A, cp, X, Y):
     return Lval, GX, GY
 
 
+def lagrangian_single(A, cp, X, MU):
+    """Single-constraint variant (PDBO-s, section 4 Discussion): the constraint sum_i g(x_i) = 0
+    with one dual mu per restart, ``L_s(x, mu) = f(x) + mu * sum_i g(x_i)``.
+
+    Returns ``(L[B], dL/dX [B, n], dL/dmu [B])`` with ``dL/dx = A x + c' + mu g'(x)`` and
+    ``dL/dmu = sum_i g(x_i)``.
+    """
+    X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+    MU = np.asarray(MU, dtype=np.float64).reshape(-1)
+    AX = np.asarray((A @ X.T).T)
+    G = g(X)
+    Lval = 0.5 * np.einsum("ri,ri->r", X, AX) + X @ cp + MU * np.sum(G, axis=1)
+    GX = AX + cp[None, :] + MU[:, None] * g_prime(X)
+    GMU = np.sum(G, axis=1)
+    return Lval, GX, GMU
+
+
 # ----------------------------------------------------------------------------------------
 # x^0 ~ Uniform([0,1]^n): SplitMix64 as a counter-based generator
 # ----------------------------------------------------------------------------------------
@@ -208,6 +232,24 @@ def gda_step(A, cp, X, Y, alpha, beta, delta, grad_tol=None):
     return Xn, Yn, D
 
 
+def gda_step_single(A, cp, X, MU, alpha, beta, delta, grad_tol=None):
+    """Algorithm 1 applied to the single-constraint Lagrangian (PDBO-s): the same primal step and
+    delta-perturbation with the restart's one dual mu in place of y_i, and the dual ascent
+    mu <- mu + beta * sum_i g(x_i) on the old x (simultaneous updates).
+    Returns (X^{t+1}, MU^{t+1}, D^t)."""
+    if grad_tol is None:
+        grad_tol = 2.0 * delta
+    X = np.asarray(X, dtype=np.float64)
+    MU = np.asarray(MU, dtype=np.float64).reshape(-1)
+    _, D, GMU = lagrangian_single(A, cp, X, MU)
+    stagnating = (np.abs(X - 0.5) <= delta) & (np.abs(D) <= grad_tol) & (MU[:, None] <= 0.0)
+    perturbed = np.where(X <= 0.5, 0.5 - delta, 0.5 + delta)
+    projected = np.minimum(1.0, np.maximum(0.0, X - alpha * D))
+    Xn = np.where(stagnating, perturbed, projected)
+    MUn = MU + beta * GMU
+    return Xn, MUn, D
+
+
 def round_bits(X):
     """Binary candidate of each restart: b_i = [x_i > 1/2] (ties go to 0, the x <= 1/2 side)."""
     return (np.asarray(X) > 0.5).astype(np.uint8)
@@ -222,18 +264,23 @@ def eval_points(T, K):
 
 
 def run(Q, c, restarts, iters, alpha, beta, ybar, delta=0.01, grad_tol=None, eval_every=10,
-        seed=0, X0=None, Y0=None, dump_iters=0, A=None, cp=None, **_ignored):
+        seed=0, X0=None, Y0=None, dump_iters=0, A=None, cp=None, dual="coordinate", **_ignored):
     """Batched PDBO: B restarts of Algorithm 1, best candidate retained (section 4.2).
 
     Candidates b = round_bits(x^t) are evaluated exactly at every t in eval_points(T, K).
     Per restart the best F is kept with its earliest t (strict improvement only); the global
     best is the lexicographic minimum of (F, t, r).  ``dump_iters`` keeps (x, y, d) for the
-    first iterations (parity dumps).
+    first iterations (parity dumps).  ``dual="single"`` runs the PDBO-s variant
+    (``gda_step_single``): Y is then one dual per restart, shape (B,).
     """
     Q = np.asarray(Q)
     n = Q.shape[0]
     if A is None or cp is None:
         A, cp = canonicalize(Q, c)
+    if dual not in ("coordinate", "single"):
+        raise ValueError("dual must be 'coordinate' or 'single'")
+    if dual == "single":
+        Y0 = np.full(restarts, float(ybar)) if Y0 is None else np.asarray(Y0, dtype=np.float64).reshape(-1)
     if X0 is None:
         X0, Y0d = init_state(n, restarts, seed, ybar)
         if Y0 is None:
@@ -242,6 +289,7 @@ def run(Q, c, restarts, iters, alpha, beta, ybar, delta=0.01, grad_tol=None, eva
         Y0 = np.full((restarts, n), float(ybar))
     X = np.array(X0, dtype=np.float64)
     Y = np.array(Y0, dtype=np.float64)
+    step = gda_step_single if dual == "single" else gda_step
     pts = set(eval_points(iters, eval_every))
     best_F = np.full(restarts, np.iinfo(np.int64).max, dtype=np.int64)
     best_t = np.full(restarts, -1, dtype=np.int64)
@@ -249,7 +297,7 @@ def run(Q, c, restarts, iters, alpha, beta, ybar, delta=0.01, grad_tol=None, eva
     evals = []
     dumps = {"x": [X.copy()], "y": [Y.copy()], "d": []}
     for t in range(iters):
-        Xn, Yn, D = gda_step(A, cp, X, Y, alpha, beta, delta, grad_tol)
+        Xn, Yn, D = step(A, cp, X, Y, alpha, beta, delta, grad_tol)
         if t < dump_iters:
             dumps["d"].append(D)
             dumps["x"].append(Xn.copy())
