@@ -188,9 +188,16 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       SBO_ETIMEOUT
  *   SBO_OPT_PDL:        1 (default): the sparse kernel's iterations are launched as programmatic
  *                       dependents of the previous kernel (the launch of iteration t+1 overlaps
- *                       iteration t; results identical); 0: plain stream order */
+ *                       iteration t; results identical); 0: plain stream order
+ *   SBO_OPT_DUAL:       0 (default): one dual y_i per coordinate (PDBO, Algorithm 1); 1: one dual
+ *                       mu per restart on the single constraint sum_i g(x_i) = 0 (the PDBO-s
+ *                       variant of section 4's discussion and ablation): the same primal step and
+ *                       perturbation rule with mu in place of y_i, and mu <- mu + beta sum_i g(x_i)
+ *                       on the old x.  Set before sbo_gda_start; y0 then gives mu0_r = y0[r*n];
+ *                       sbo_state reports mu_r in every coordinate of restart r.  Not available in
+ *                       grouped runs or the tiny kernel (FP32 problems with n <= 64 use SIMT) */
 enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4, SBO_OPT_SPLIT_K = 5,
-       SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7 };
+       SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7, SBO_OPT_DUAL = 8 };
 sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
 
 /* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL),

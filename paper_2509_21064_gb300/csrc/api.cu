@@ -97,6 +97,7 @@ struct sbo_problem {
   uint32_t* err = nullptr;
   // options
   int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0, opt_split_k = 16, opt_autotune = 1, opt_pdl = 1;
+  int opt_dual = 0;           // 0: one dual per coordinate (PDBO); 1: one per restart (PDBO-s)
   int64_t opt_timeout_us = 4000000;
   // run
   bool started = false;
@@ -116,6 +117,11 @@ struct sbo_problem {
   unsigned long long* F2 = nullptr;
   uint8_t* bestBits = nullptr;
   unsigned int* commit_ctr = nullptr;   // arrival counter of the evaluation commit (zero between launches)
+  // single-constraint form: one dual per restart and the update's rows of partial sums of g
+  bool single = false;
+  float* mu = nullptr;
+  float* gpart = nullptr;
+  int64_t gpart_rows = 0, gpart_ld = 0;
   int64_t trace_cap = 0;
   int64_t n_evals_host = 0;
   TcPlan plan{};
@@ -149,6 +155,9 @@ void free_run(sbo_problem* p) {
   dfree(p->F2, p->stream);
   dfree(p->bestBits, p->stream);
   dfree(p->commit_ctr, p->stream);
+  dfree(p->mu, p->stream);
+  dfree(p->gpart, p->stream);
+  p->single = false;
   dfree(p->tc_ws, p->stream);
   dfree(p->tc_ctr, p->stream);
   p->started = false;
@@ -196,6 +205,11 @@ EpiArgs base_args(const sbo_problem* p) {
   a.Y = p->Y;
   a.F2 = p->F2;
   a.err = p->err;
+  if (p->single) {
+    a.mu = p->mu;
+    a.gpart = p->gpart;
+    a.gpart_ld = p->gpart_ld;
+  }
   return a;
 }
 
@@ -220,6 +234,10 @@ cudaError_t enqueue_step(sbo_problem* p, bool write_bits, cudaStream_t s) {
   a.bits_out = write_bits ? p->bits : nullptr;
   cudaError_t e = contract(p, a, EPI_UPDATE, p->cur, s);
   p->cur ^= 1;
+  if (e == cudaSuccess && p->single) {
+    e = launch_dual_single(p->mu, p->gpart, (int)p->gpart_rows, p->gpart_ld, p->B, (float)p->prm.beta, s);
+    ++p->launches;
+  }
   return e;
 }
 
@@ -708,6 +726,10 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       return SBO_OK;
     case SBO_OPT_AUTOTUNE: p->opt_autotune = value != 0; return SBO_OK;
     case SBO_OPT_PDL: p->opt_pdl = value != 0; return SBO_OK;
+    case SBO_OPT_DUAL:
+      if (value != 0 && value != 1) return fail(SBO_EINVAL, "dual form must be 0 (per coordinate) or 1 (per restart)");
+      p->opt_dual = (int)value;
+      return SBO_OK;
     case SBO_OPT_SPLIT_K:
       if (value < 0 || value > 64) return fail(SBO_EINVAL, "split-K factor must be in [0, 64]");
       p->opt_split_k = (int)value;
@@ -740,10 +762,12 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
     if ((ker == KER_SIMT || ker == KER_TINY) && p->prec != SBO_FP32)
       return fail(SBO_EINVAL, "the SIMT and tiny kernels need an FP32 problem");
     if (ker == KER_TINY && p->n > 64) return fail(SBO_EINVAL, "the tiny kernel needs n <= 64");
+    if (ker == KER_TINY && p->opt_dual == 1)
+      return fail(SBO_EINVAL, "the tiny kernel runs the per-coordinate dual only; use the SIMT kernel");
   } else if (p->prec == SBO_BF16) {
     ker = KER_TC;
   } else {
-    ker = p->n <= 64 ? KER_TINY : KER_SIMT;
+    ker = p->n <= 64 && p->opt_dual == 0 ? KER_TINY : KER_SIMT;
   }
   if (ker == KER_TC && !tc_supported()) return fail(SBO_ECUDA, "tcgen05 path needs a compute capability 10.3 device");
   free_run(p);
@@ -781,6 +805,16 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   al((void**)&p->evalF, sizeof(long long) * p->B);
   al((void**)&p->F2, sizeof(unsigned long long) * p->B);
   al((void**)&p->commit_ctr, sizeof(unsigned int));
+  p->single = p->opt_dual == 1;
+  if (p->single) {
+    // rows of partial sums the update kernel writes: 4 per 128 variables (tcgen05 kernels; CTA
+    // pairs round up to 256), 1 per 64 variables (SIMT), 1 per block along the rows (CSR)
+    p->gpart_rows = ker == KER_TC ? (p->n + 255) / 256 * 8 : ker == KER_SIMT ? (p->n + 63) / 64
+                                                                             : csr_partial_rows(p->B);
+    p->gpart_ld = round_up(p->B, 8);
+    al((void**)&p->mu, sizeof(float) * p->gpart_ld);
+    al((void**)&p->gpart, sizeof(float) * p->gpart_rows * p->gpart_ld);
+  }
   al((void**)&p->bestBits, elems);
   al((void**)&p->trace, sizeof(long long) * p->trace_cap);
   al((void**)&p->n_evals, sizeof(long long));
@@ -858,6 +892,17 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
       dfree(x0d, s); dfree(y0d, s); free_run(p); return cuda_fail(e, "upload of x0 / y0");
     }
   }
+  if (p->single) {
+    // after the autotuner, whose trial launches may write rows the chosen kernel does not
+    std::vector<float> mu0((size_t)p->gpart_ld, 0.0f);
+    for (int r = 0; r < p->B; ++r) mu0[r] = y0 ? y0[(size_t)r * p->n] : (float)prm->ybar;
+    if ((e = cudaMemsetAsync(p->gpart, 0, sizeof(float) * p->gpart_rows * p->gpart_ld, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(p->mu, mu0.data(), sizeof(float) * p->gpart_ld, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      dfree(x0d, s); dfree(y0d, s); free_run(p); return cuda_fail(e, "single-constraint dual set-up");
+    }
+  }
   e = launch_init_state((int)p->n, p->B, p->ld, p->layout, prm->seed, (float)prm->ybar, x0d, y0d, p->Xm,
                         ker == KER_TINY ? (void*)p->Xm : p->Xop[0], ker == KER_TINY ? OP_F32 : p->op_type, p->Y,
                         p->err, s);
@@ -893,7 +938,7 @@ sbo_status sbo_gda_run(sbo_problem* p, int64_t iters) {
       }
       cudaError_t e = cudaGraphLaunch(p->gexec[par], p->stream);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-      p->launches += K + 2;
+      p->launches += K * (p->single ? 2 : 1) + 2;
       if (K & 1) p->cur ^= 1;
       p->t += K;
       p->t_last_eval = p->t;
@@ -1041,7 +1086,13 @@ sbo_status sbo_state(sbo_problem* p, float* X, float* Y) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(X, tmp, sizeof(float) * p->B * p->n, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
-  if (Y && e == cudaSuccess) {
+  if (Y && e == cudaSuccess && p->single) {
+    // one dual per restart: every coordinate of restart r reports mu_r
+    std::vector<float> mu((size_t)p->B);
+    e = cudaMemcpyAsync(mu.data(), p->mu, sizeof(float) * p->B, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int64_t r = 0; r < p->B && e == cudaSuccess; ++r) std::fill(Y + r * p->n, Y + (r + 1) * p->n, mu[r]);
+  } else if (Y && e == cudaSuccess) {
     e = launch_gather_state(p->Y, (int)p->n, p->B, p->ld, p->layout, tmp, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(Y, tmp, sizeof(float) * p->B * p->n, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1259,6 +1310,7 @@ sbo_status group_start_tile(sbo_group* g, const sbo_gda_params* prms, int tile_n
   // start every member on the group's tile width, then build the instance table
   for (size_t k = 0; k < cnt; ++k) {
     sbo_problem* p = g->members[k];
+    if (p->opt_dual != 0) return fail(SBO_EINVAL, "grouped runs use the per-coordinate dual");
     p->opt_kernel = KER_TC;
     p->opt_tile_n = tile_n;
     p->opt_split_k = 0;

@@ -38,7 +38,32 @@ struct EpiArgs {
   float* GY;               // EPI_LAGR: dL/dy, may be null
   const float* gout;       // EPI_LAGR: per-restart scale of GX, GY (upstream gradient), may be null
   uint32_t* err;           // device error word
+  // Single-constraint variant (PDBO-s): one dual per restart instead of y.  When mu is non-null
+  // the update reads mu[r] in place of y, leaves Y alone and writes partial sums of g(x^t) over
+  // its rows into gpart[row of partials][r] (row stride gpart_ld); a separate kernel then sums
+  // the rows in order and takes the dual step.
+  const float* mu;
+  float* gpart;
+  int64_t gpart_ld;
 };
+
+// Sum of v[j] over the 32 lanes of a warp for each j = 0..31 at once (31 shuffles): lane l
+// returns the sum of v[l].  Step k halves the values a lane holds: the lane keeps the half
+// selected by bit (4-k) of its lane id and adds its partner's copy of that half.
+__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int half = 16 >> k;
+    const bool upper = (lane & half) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const float keep = upper ? v[j + half] : v[j];
+      const float send = upper ? v[j] : v[j + half];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+  return v[0];
+}
 
 __device__ __forceinline__ float op_load(const void* p, int64_t idx, int type) {
   if (type == OP_F32) return static_cast<const float*>(p)[idx];

@@ -61,10 +61,13 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
   const int64_t ld = a.ld;
   const void* Xin = a.Xin;
   long long f2[NV][4];
+  float4 gs[NV];   // single-constraint form: sum of g(x^t) over this warp's rows, per restart
 #pragma unroll
-  for (int v = 0; v < NV; ++v)
+  for (int v = 0; v < NV; ++v) {
+    gs[v] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 4; ++k) f2[v][k] = 0;
+  }
 
   // The structure of the warp's first row (constant for the whole run) is read before waiting on
   // the previous kernel, so its dependent loads (row pointer, then indices and weights) overlap
@@ -109,7 +112,8 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
         const int64_t idx = i * ld + r0;
         if (MODE == EPI_UPDATE) {
           xo[v] = a.Xm ? *reinterpret_cast<const float4*>(a.Xm + idx) : load4<OP_F32>(Xin, idx);
-          yo[v] = *reinterpret_cast<const float4*>(a.Y + idx);
+          yo[v] = a.mu ? *reinterpret_cast<const float4*>(a.mu + r0)    // the restarts' duals
+                       : *reinterpret_cast<const float4*>(a.Y + idx);
         } else {
           xo[v] = load4<OPT>(Xin, idx);   // EPI_EVAL: the row's own bits
         }
@@ -161,16 +165,32 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
           set_comp(xn4, k, live ? xn : 0.0f);
           set_comp(yn4, k, live ? yn : 0.0f);
           set_comp(b4, k, (live && xn > 0.5f) ? 1.0f : 0.0f);
+          set_comp(gs[v], k, comp(gs[v], k) + (live ? x * x - x : 0.0f));
         }
         if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = xn4;
         store4<OPT>(a.Xout, idx, xn4);
-        *reinterpret_cast<float4*>(a.Y + idx) = yn4;
+        if (!a.mu) *reinterpret_cast<float4*>(a.Y + idx) = yn4;
         if (a.bits_out) store4<OPT>(a.bits_out, idx, b4);
       } else if (MODE == EPI_EVAL) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           if (r0 + k < B && comp(xo[v], k) != 0.0f) f2[v][k] += (long long)comp(acc[v], k) + cp2;
       }
+    }
+  }
+  if (MODE == EPI_UPDATE && a.mu) {
+    // single-constraint form: the block's warps cover the same restarts; their sums of g go to
+    // shared memory and are added in warp order into this block's row of partial sums
+    __shared__ float redf[8][128 * NV];
+    const int w = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) *reinterpret_cast<float4*>(&redf[w][128 * v + 4 * lane]) = gs[v];
+    __syncthreads();
+    const int64_t rb = (int64_t)blockIdx.y * 128 * NV;
+    for (int t = threadIdx.x; t < 128 * NV; t += blockDim.x) {
+      float sum = 0.0f;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += redf[q][t];
+      if (rb + t < B) a.gpart[(int64_t)blockIdx.x * a.gpart_ld + rb + t] = sum;
     }
   }
   if (MODE == EPI_EVAL) {
@@ -191,6 +211,13 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
   }
 }
 
+int csr_partial_rows(int B) {
+  int NV = 1;
+  while (NV < 2 && 128 * NV < B) NV *= 2;
+  const int chunks = (B + 128 * NV - 1) / (128 * NV);
+  return 152 * 8 / (chunks > 0 ? chunks : 1) + 1;
+}
+
 template <int MODE, int OPT>
 static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const void* val, int vt,
                                 const EpiArgs& a, bool pdl, cudaStream_t s) {
@@ -201,8 +228,9 @@ static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const
   const int64_t chunks = (a.B + 128 * NV - 1) / (128 * NV);
   const int warps_per_block = 8;
   int64_t want = (a.n + warps_per_block - 1) / warps_per_block;
-  if (MODE == EPI_EVAL) {
-    const int64_t cap = (int64_t)152 * 8 / (chunks > 0 ? chunks : 1) + 1;  // bounds the closing atomics
+  if (MODE == EPI_EVAL || a.mu) {
+    // bounds the closing atomics (evaluation) or the rows of partial sums (single-constraint form)
+    const int64_t cap = csr_partial_rows(a.B);
     if (want > cap) want = cap;
   }
   if (want > 65535) want = 65535;

@@ -8,7 +8,9 @@
 //   EPI_EVAL    X holds 0/1 candidates b: accumulates 2F(b) = sum_i b_i (G_i + 2 c'_i) per
 //               restart in int64 (G is an exact integer because row sums of |A| < 2^24)
 //   EPI_LAGR    value and gradients of the Lagrangian (section 3.1)
-// State arrays are restart-major: element (r, i) at [r * ld + i].
+// State arrays are restart-major: element (r, i) at [r * ld + i].  In the single-constraint form
+// (a.mu set) the update reads mu[r] for y and writes, per 64-variable tile (blockIdx.x), the sum
+// of g(x^t) of each restart into row blockIdx.x of the partial sums.
 #include "sbo_internal.h"
 
 namespace sbo {
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(256) k_simt(const float* __restrict__ A, int64
   for (int p = 0; p < 4; ++p) {
     const int64_t r = r0 + ty + 16 * p;
     long long f2 = 0;
-    float lsum = 0.0f;
+    float lsum = 0.0f, gsum = 0.0f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int64_t i = i0 + tx + 16 * q;
@@ -104,13 +106,14 @@ __global__ void __launch_bounds__(256) k_simt(const float* __restrict__ A, int64
       const float g = acc[p][q];
       if (MODE == EPI_UPDATE) {
         const float x = a.Xm ? a.Xm[idx] : static_cast<const float*>(a.Xin)[idx];
-        const float y = a.Y[idx];
+        const float y = a.mu ? a.mu[r] : a.Y[idx];   // single-constraint form: the restart's dual
         const float d = g + a.cp[i] + y * (2.0f * x - 1.0f);
         float yn;
         const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
         if (a.Xm) a.Xm[idx] = xn;
         static_cast<float*>(a.Xout)[idx] = xn;
-        a.Y[idx] = yn;
+        if (a.mu) gsum += x * x - x;
+        else a.Y[idx] = yn;
         if (a.bits_out) static_cast<float*>(a.bits_out)[idx] = xn > 0.5f ? 1.0f : 0.0f;
       } else if (MODE == EPI_EVAL) {
         const float b = X[idx];
@@ -129,6 +132,12 @@ __global__ void __launch_bounds__(256) k_simt(const float* __restrict__ A, int64
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, o);
       if (tx == 0 && r < B && f2 != 0) atomicAdd(&a.F2[r], (unsigned long long)f2);
+    }
+    if (MODE == EPI_UPDATE && a.mu) {
+      // this tile's 64 variables: the 16 lanes of a half warp hold one restart
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+      if (tx == 0 && r < B) a.gpart[(int64_t)blockIdx.x * a.gpart_ld + r] = gsum;
     }
     if (MODE == EPI_LAGR && a.L) {
 #pragma unroll

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
             waited = true;
           }
           tmem_ld32(tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc * BN + c0), g);
-          epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v);
+          epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v, m_tile * 4 + wq);
         }
       } else {
         ok = mbar_wait_warp(smem_u32(&tfull_bar[acc]), acc_phase, deadline, vabort, lane);
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc(const __grid_constant__ Tc
 #pragma unroll
               for (int j = 0; j < 32; ++j) g[j] += __ldcg(ps + (size_t)(c0 + j) * TC_BM + row);
             }
-            epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v);
+            epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v, m_tile * 4 + wq);
           }
         }
       }

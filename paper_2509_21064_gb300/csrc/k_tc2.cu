@@ -309,7 +309,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) k_tc_p
             waited = true;
           }
           tmem_ld32(tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)(acc * P_BN + c0), g);
-          epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v);
+          epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v, (m_tile * 2 + (int)rank) * 4 + wq);
         }
       } else {
         ok = mbar_wait_cl_warp(smem_u32(&tfull_bar[acc]), acc_phase, deadline, vabort, lane);
@@ -364,7 +364,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_THREADS, 1) k_tc_p
 #pragma unroll
               for (int j = 0; j < 32; ++j) g[j] += __ldcg(ps + (size_t)(c0 + j) * TC_BM + row);
             }
-            epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v);
+            epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v, (m_tile * 2 + (int)rank) * 4 + wq);
           }
         }
       }

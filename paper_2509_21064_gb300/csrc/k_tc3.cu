@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
 #pragma unroll
         for (int j = 0; j < 32; ++j) g[j] += csk_ld_remote(base + (uint32_t)(j * TC_BM * 4));
       }
-      epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v);
+      epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v, m_tile * 4 + wq);
     }
   }
 

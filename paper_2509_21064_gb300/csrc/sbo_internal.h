@@ -54,9 +54,11 @@ struct TinyArgs {
   long long* evalF;        // scratch [B], F of the current evaluation
 };
 cudaError_t launch_tiny(const TinyArgs& a, cudaStream_t s);
-// k_csr.cu  (variable-major state); pdl: launch as a programmatic dependent of the previous kernel
+// k_csr.cu  (variable-major state); pdl: launch as a programmatic dependent of the previous kernel.
+// csr_partial_rows: blocks along the rows (= rows of single-constraint partial sums) at most.
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
                        const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s);
+int csr_partial_rows(int B);
 // k_best.cu
 struct CommitArgs {
   const void* bits;              // candidate bits of this evaluation (operand type, state layout)
@@ -71,6 +73,8 @@ struct CommitArgs {
 cudaError_t launch_eval_commit(const CommitArgs& a, int64_t add, cudaStream_t s);
 cudaError_t launch_eval_commit_group(const CommitArgs* d_tab, int members, int64_t max_inner, int64_t max_outer,
                                      int64_t add, cudaStream_t s);
+// single-constraint form: mu[r] += beta * sum over the P rows of partial sums gpart[k][r]
+cudaError_t launch_dual_single(float* mu, const float* gpart, int P, int64_t ldg, int B, float beta, cudaStream_t s);
 cudaError_t launch_best_select(const long long* bestF, const long long* bestT, int B,
                                long long* out3, cudaStream_t s);
 // k_tc.cu  (tcgen05 BF16 contraction with fused epilogue, restart-major state)

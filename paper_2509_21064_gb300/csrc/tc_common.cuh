@@ -113,7 +113,7 @@ __device__ __forceinline__ void epi_load(const EpiArgs& a, int64_t i, bool row_o
       const bool ok = row_ok && r < a.B;
       const int64_t idx = r * a.ld + i;
       u[j] = ok ? a.Xm[idx] : 0.0f;
-      v[j] = ok ? a.Y[idx] : 0.0f;
+      v[j] = ok ? (a.mu ? a.mu[r] : a.Y[idx]) : 0.0f;   // single-constraint form: the restart's dual
     }
   } else if (MODE == EPI_EVAL) {
 #pragma unroll
@@ -134,12 +134,35 @@ __device__ __forceinline__ void epi_load(const EpiArgs& a, int64_t i, bool row_o
   }
 }
 
-// One chunk of the epilogue given the accumulator values g (= (A x_r)_i for 32 restarts r).
+// One chunk of the epilogue given the accumulator values g (= (A x_r)_i for 32 restarts r).  In
+// the single-constraint form (a.mu set) the warp's 32 rows also add up g(x^t) per restart into
+// row `prow` of the partial sums.
 template <int MODE>
 __device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_ok, float cpi, long long cp2,
                                           int64_t rbase, int lane, const float (&g)[32], const float (&u)[32],
-                                          const float (&v)[32]) {
-  if (MODE == EPI_UPDATE) {
+                                          const float (&v)[32], int prow = 0) {
+  if (MODE == EPI_UPDATE && a.mu) {
+    float gv[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int64_t r = rbase + j;
+      gv[j] = 0.0f;
+      if (row_ok && r < a.B) {
+        const int64_t idx = r * a.ld + i;
+        const float x = u[j], y = v[j];
+        const float d = g[j] + cpi + y * (2.0f * x - 1.0f);
+        float yn;
+        const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+        a.Xm[idx] = xn;
+        static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);
+        if (a.bits_out)
+          static_cast<__nv_bfloat16*>(a.bits_out)[idx] = __float2bfloat16_rn(xn > 0.5f ? 1.0f : 0.0f);
+        gv[j] = x * x - x;
+      }
+    }
+    const float sum = warp_transpose_sum32(gv, lane);
+    if (rbase + lane < a.B) a.gpart[(int64_t)prow * a.gpart_ld + rbase + lane] = sum;
+  } else if (MODE == EPI_UPDATE) {
     if (row_ok) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
