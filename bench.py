@@ -573,6 +573,111 @@ def run_mis(args):
     return 0
 
 
+# Max-Cut stand-ins shaped like the paper's sensitivity and ablation instances (Gset is not
+# available): G81 is a 100 x 200 toroidal grid with +-1 weights, G72 and G77 100 x 100 and 100 x 140
+# grids; G70 a sparse random graph on 10,000 vertices with 9,999 unit-weight edges.
+SWEEP_GRAPHS = {
+    "torus-100x200 (G81 shape)": lambda: (20000, W.maxcut_torus(100, 200, seed=0)),
+    "random n=10000, ~10^4 unit edges (G70 shape)": lambda: (10000, W.maxcut_er(10000, 2.0, seed=0, weights="unit")),
+}
+ABLATION_GRAPHS = {
+    "torus-100x100 (G72 shape)": lambda: (10000, W.maxcut_torus(100, 100, seed=1)),
+    "torus-100x140 (G77 shape)": lambda: (14000, W.maxcut_torus(100, 140, seed=2)),
+    "torus-100x200 (G81 shape)": lambda: (20000, W.maxcut_torus(100, 200, seed=0)),
+}
+# The paper's tables on the real Gset graphs (RTX 3090): context for the trends only.
+PAPER_SENSITIVITY = {
+    "ybar": {"values": [0, 1, 2, 4, 6, 8, 10], "G70": [8756, 9145, 9398, 9535, 9537, 9536, 9536],
+             "G81": [11338, 12886, 13836, 13840, 13852, 13846, 13846]},
+    "alpha": {"values": [0.0025, 0.005, 0.01, 0.025, 0.05, 0.1, 0.25], "G70": [9365, 9451, 9530, 9537, 9536, 9535, 9539],
+              "G81": [13828, 13842, 13848, 13852, 13842, 13854, 13840]},
+    "beta": {"values": [0.001, 0.0025, 0.005, 0.01, 0.025, 0.05, 0.1, 0.25],
+             "G70": [9538, 9536, 9542, 9534, 9537, 9509, 9495, 9415],
+             "G81": [13880, 13868, 13862, 13858, 13852, 13840, 13724, 13480]},
+    "B": {"values": [1, 10, 100, 1000], "G70": [9525, 9527, 9537, 9540], "G81": [13828, 13842, 13852, 13858]},
+    "ablation": {"PDBO-s": {"G72": 6880, "G77": 9782, "G81": 13786}, "PDBO": {"G72": 6906, "G77": 9812, "G81": 13852}},
+}
+
+
+def run_sweep(args):
+    """Sensitivity of the Max-Cut result to ybar, alpha, beta and B, and the PDBO / PDBO-s
+    ablation, on synthetic graphs shaped like the paper's instances (paper parameters ybar = 6,
+    alpha = beta = 0.025, B = 100 unless swept; T = args.iters; FP32).  One JSON line per run."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    import torch
+    from paper_2509_21064_gb300 import sbo as S
+    from paper_2509_21064_gb300.build import build
+    build()
+    S.lib()
+    T, K = args.iters, 10
+    stream = torch.cuda.Stream()
+
+    def one(n, csr, i, j, w, ybar=6.0, alpha=0.025, beta=0.025, B=100, dual=0, iters=None):
+        rowptr, col, val, c = csr
+        T_run = iters or T
+        p = W.GdaParams(restarts=B, iters=T_run, alpha=alpha, beta=beta, ybar=ybar, eval_every=K, seed=0)
+        P = S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32, stream=stream)
+        P.set_option(S.SBO_OPT_DUAL, dual)
+        P.start(S.params(**p.asdict()))
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.run(T_run)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        P.sync()
+        x, F, t_best, _ = P.best()
+        P.close()
+        cut = int(np.sum(w * (x[i] != x[j])))
+        assert cut == -int(F)
+        secs = e0.elapsed_time(e1) * 1e-3
+        return {"cut": cut, "iters": T_run, "best_iteration": int(t_best), "seconds": round(secs, 4),
+                "seconds_to_best": round(secs * t_best / T_run, 4)}
+
+    def graph(make):
+        n, (i, j, w) = make()
+        csr = W.maxcut_qubo(n, i, j, w)
+        Wm = sp.coo_matrix((w.astype(np.float64), (i, j)), shape=(n, n))
+        Wm = (Wm + Wm.T).tocsr()
+        lam_min = float(spla.eigsh(Wm, k=1, which="SA", return_eigenvectors=False)[0])
+        return n, csr, i, j, w, lam_min
+
+    out = {"ybar": {}, "alpha": {}, "beta": {}, "B": {}, "ablation": {}}
+    for name, make in SWEEP_GRAPHS.items():
+        n, csr, i, j, w, lam_min = graph(make)
+        for key, values, kw in (("ybar", PAPER_SENSITIVITY["ybar"]["values"], "ybar"),
+                                ("alpha", PAPER_SENSITIVITY["alpha"]["values"], "alpha"),
+                                ("beta", PAPER_SENSITIVITY["beta"]["values"], "beta"),
+                                ("B", PAPER_SENSITIVITY["B"]["values"], "B")):
+            rows = []
+            for v in values:
+                # beta sweep: T grows as 1/beta below the table's 0.025 (the iteration count of
+                # Theorem 3.7 scales with 1/beta), so small steps get the time they need
+                extra = {"iters": int(round(T * max(1.0, 0.025 / v)))} if key == "beta" else {}
+                r = one(n, csr, i, j, w, **{kw: v}, **extra)
+                if key == "ybar":
+                    r["convex_start"] = bool(v + lam_min >= 0.0)
+                r[kw] = v
+                rows.append(r)
+                print(json.dumps({"workload": "sweep", "graph": name, "swept": key, **r}), flush=True)
+            out[key][name] = {"lambda_min_W": round(lam_min, 4), "runs": rows}
+    for name, make in ABLATION_GRAPHS.items():
+        n, csr, i, j, w, _ = graph(make)
+        res = {}
+        # PDBO-s with the table's beta takes dual steps of up to n beta / 4; with beta / n its dual
+        # step is that of the normalised constraint (1/n) sum_i g(x_i) = 0
+        for label, dual, beta in (("PDBO-s (beta/n)", 1, 0.025 / n), ("PDBO-s (beta)", 1, 0.025), ("PDBO", 0, 0.025)):
+            res[label] = one(n, csr, i, j, w, dual=dual, beta=beta)
+            print(json.dumps({"workload": "ablation", "graph": name, "method": label, **res[label]}), flush=True)
+        out["ablation"][name] = res
+    print(json.dumps({"workload": "Max-Cut sensitivity and PDBO-s ablation (synthetic Gset-shaped graphs)",
+                      "iters": T, "eval_every": K, "precision": "fp32", "results": out,
+                      "paper_on_gset_rtx3090": PAPER_SENSITIVITY}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,7 +690,7 @@ def main():
     ap.add_argument("--no-plain-form", action="store_true")
     ap.add_argument("--n", type=int, default=N_VARS, help="variables (profiling cases only)")
     ap.add_argument("--restarts", type=int, default=RESTARTS, help="restarts (profiling cases only)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "hetero", "mis"] + sorted(SPARSE),
+    ap.add_argument("--workload", default="dense", choices=["dense", "hetero", "mis", "sweep"] + sorted(SPARSE),
                     help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
                     help="weight/operand precision of a sparse workload")
@@ -595,7 +700,7 @@ def main():
     ap.add_argument("--degree", type=int, default=3, help="MIS workload: graph degree")
     ap.add_argument("--mis-params", default="paper", choices=["paper", "scaled"],
                     help="MIS workload: the paper's table (ybar=5, alpha=beta=0.02) or the spectral scaling")
-    ap.add_argument("--iters", type=int, default=3000, help="MIS workload: GDA iterations")
+    ap.add_argument("--iters", type=int, default=3000, help="MIS and sweep workloads: GDA iterations")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 64, 128, 256, 512, 1064, 1128, 1256],
                     help="tensor-core tile width (0: autotuned); profiling cases only")
     ap.add_argument("--kernel-only", action="store_true",
@@ -607,6 +712,8 @@ def main():
         return run_reference(args)
     if args.workload == "hetero":
         return run_hetero(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.workload == "mis":
         if args.n == N_VARS:
             args.n = 10000

@@ -109,22 +109,32 @@ __global__ void __launch_bounds__(256) k_eval_commit(CommitArgs one, const Commi
 
 // Dual step of the single-constraint form (one dual per restart): mu_r += beta * sum_k
 // gpart[k][r], the rows of partial sums of g(x^t) written by the update kernel.  A block covers 32
-// restarts (lane = restart); warp w adds rows w, w + 8, ...; the eight warp sums are then added in
-// warp order, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(256) k_dual_single(float* mu, const float* __restrict__ gpart, int P, int64_t ldg,
-                                                     int B, float beta) {
-  __shared__ float part[8][32];
+// restarts (lane = restart); warp w adds rows w, w + 32, ... (eight loads in flight, added in row
+// order); the 32 warp sums are then added in warp order, so the result does not depend on
+// scheduling.
+__global__ void __launch_bounds__(1024) k_dual_single(float* mu, const float* __restrict__ gpart, int P, int64_t ldg,
+                                                      int B, float beta) {
+  __shared__ float part[32][33];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int r = blockIdx.x * 32 + lane;
   float sum = 0.0f;
-  if (r < B)
-    for (int k = w; k < P; k += 8) sum += gpart[(int64_t)k * ldg + r];
+  if (r < B) {
+    int k = w;
+    for (; k + 7 * 32 < P; k += 8 * 32) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = gpart[(int64_t)(k + 32 * q) * ldg + r];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sum += v[q];
+    }
+    for (; k < P; k += 32) sum += gpart[(int64_t)k * ldg + r];
+  }
   part[w][lane] = sum;
   __syncthreads();
   if (w == 0 && r < B) {
     float tot = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) tot += part[q][lane];
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) tot += part[q][lane];
     mu[r] += beta * tot;
   }
 }
@@ -201,7 +211,7 @@ cudaError_t launch_eval_commit_group(const CommitArgs* d_tab, int members, int64
 }
 
 cudaError_t launch_dual_single(float* mu, const float* gpart, int P, int64_t ldg, int B, float beta, cudaStream_t s) {
-  k_dual_single<<<(B + 31) / 32, 256, 0, s>>>(mu, gpart, P, ldg, B, beta);
+  k_dual_single<<<(B + 31) / 32, 1024, 0, s>>>(mu, gpart, P, ldg, B, beta);
   return cudaGetLastError();
 }
 
