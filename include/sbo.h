@@ -91,6 +91,20 @@ sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const i
                           const int32_t* val, const int32_t* c, int32_t precision,
                           void* stream, sbo_problem** out);
 
+/* sbo_create_maxkcut: Max-k-Cut on a weighted graph (the paper's appendix on Max-k-Cut): edges
+ * (ei[e], ej[e]) with integer weight w[e], each listed once (int32 ends in [0, n), no self-loops;
+ * duplicates are summed), k parts with 2 <= k <= 8.  Every vertex carries k logits Z_:,i and the
+ * point X_:,i = softmax(Z_:,i) of the simplex; sbo_gda runs the simultaneous gradient
+ * descent-ascent of section 3.2 on L(X, y) = Tr(X W X^T) + sum_i y_i (|X_:,i|^2 - 1) with
+ * Z^0_{r,i,j} = the x^0 generator at index i k + j and y^0 = ybar (x0, y0 must be NULL).
+ * Candidates are argmax parts (ties to the smallest index), scored F = -(weight of the cut);
+ * sbo_best and sbo_eval use one byte per vertex holding its part, and sbo_state reports X as
+ * [restart][vertex][part] (B n k floats) and y as [restart][vertex].  FP32 throughout; weights
+ * and row sums of |w| must stay below 2^24.  Not available: grouped runs, sbo_lagrangian,
+ * SBO_OPT_DUAL = 1. */
+sbo_status sbo_create_maxkcut(int64_t n, int64_t m, const int32_t* ei, const int32_t* ej, const int32_t* w, int32_t k,
+                              void* stream, sbo_problem** out);
+
 /* ---- the batched GDA run ----------------------------------------------------------------
  * sbo_gda_start: (re)initialises the run: allocates the state for B = prm->restarts,
  * x^0 from x0 (host, B*n float32 row-major [r][i], values in [0,1]) or, when x0 is NULL,
@@ -200,8 +214,9 @@ enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TI
        SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7, SBO_OPT_DUAL = 8 };
 sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
 
-/* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL),
- * the tile width and the iteration counter t; any pointer may be NULL. */
+/* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL; 4 the
+ * sparse QUBO kernel, 5 the Max-k-Cut kernel), the tile width and the iteration counter t; any
+ * pointer may be NULL. */
 sbo_status sbo_info(const sbo_problem* p, int64_t* n, int32_t* restarts, int32_t* kernel,
                     int32_t* tile_n, int64_t* t);
 

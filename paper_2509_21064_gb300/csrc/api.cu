@@ -91,6 +91,7 @@ struct sbo_problem {
   void* val = nullptr;
   int val_type = 0;
   int64_t nnz = 0;
+  int kparts = 0;              // Max-k-Cut: parts per vertex (FMT_MAXK)
   // linear term
   float* cp = nullptr;
   int64_t* cp64 = nullptr;
@@ -222,6 +223,7 @@ cudaError_t contract(sbo_problem* p, const EpiArgs& a, int mode, int which_x, cu
     case KER_SIMT: return launch_simt(static_cast<const float*>(p->A), p->lda, a, mode, s);
     case KER_TC: return launch_tc(p->plan, which_x, nullptr, a, mode, timeout_ns(p), s);
     case KER_CSR: return launch_csr(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, mode, p->opt_pdl != 0, s);
+    case KER_MAXK: return launch_maxk(p->rowptr, p->col, static_cast<const float*>(p->val), a, p->kparts, mode, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -709,6 +711,75 @@ sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const i
   return SBO_OK;
 }
 
+sbo_status sbo_create_maxkcut(int64_t n, int64_t m, const int32_t* ei, const int32_t* ej, const int32_t* w, int32_t k,
+                              void* stream, sbo_problem** out) {
+  g_last_error.clear();
+  if (!out) return fail(SBO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n >= (1ll << 31)) return fail(SBO_EINVAL, "n must be in [1, 2^31)");
+  if (m < 0 || (m > 0 && (!ei || !ej || !w))) return fail(SBO_EINVAL, "m must be >= 0 and the edge arrays non-NULL");
+  if (k < 2 || k > 8) return fail(SBO_EINVAL, "k must be in [2, 8]");
+  // W symmetric: both directions of every edge, duplicates summed, zero sums dropped
+  struct Trip { int32_t i, j; int64_t v; };
+  std::vector<Trip> tr;
+  tr.reserve((size_t)2 * m);
+  for (int64_t e = 0; e < m; ++e) {
+    const int32_t a = ei[e], b = ej[e];
+    if (a < 0 || a >= n || b < 0 || b >= n) return fail(SBO_EINVAL, "edge end out of range");
+    if (a == b) return fail(SBO_EINVAL, "self-loops are not allowed");
+    tr.push_back({a, b, (int64_t)w[e]});
+    tr.push_back({b, a, (int64_t)w[e]});
+  }
+  std::sort(tr.begin(), tr.end(), [](const Trip& x, const Trip& y) { return x.i != y.i ? x.i < y.i : x.j < y.j; });
+  std::vector<int32_t> rp(n + 1, 0), cc;
+  std::vector<float> vv;
+  std::vector<int64_t> rowabs(n, 0);
+  for (size_t q = 0; q < tr.size();) {
+    size_t r = q;
+    int64_t sum = 0;
+    while (r < tr.size() && tr[r].i == tr[q].i && tr[r].j == tr[q].j) sum += tr[r++].v;
+    if (sum != 0) {
+      const int64_t a = sum < 0 ? -sum : sum;
+      if (a > (1ll << 24)) return fail(SBO_ERANGE, "an edge weight is not exact in FP32");
+      rowabs[tr[q].i] += a;
+      cc.push_back(tr[q].j);
+      vv.push_back((float)sum);
+      rp[tr[q].i + 1]++;
+    }
+    q = r;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (rowabs[i] >= (1ll << 24)) return fail(SBO_ERANGE, "a row sum of |W_ij| reaches 2^24 (objective not exact)");
+  if (cc.size() >= (size_t)INT32_MAX) return fail(SBO_EINVAL, "too many edges");
+  for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+  sbo_problem* p = new (std::nothrow) sbo_problem();
+  if (!p) return fail(SBO_ENOMEM, "host allocation failed");
+  sbo_status st = init_common(p, stream);
+  auto bail = [&](sbo_status s2) { free_all(p); delete p; return s2; };
+  if (st != SBO_OK) return bail(st);
+  p->n = n;
+  p->fmt = FMT_MAXK;
+  p->prec = SBO_FP32;
+  p->kparts = k;
+  p->nnz = (int64_t)cc.size();
+  p->val_type = 0;
+  cudaError_t e;
+  cudaStream_t cs = p->stream;
+  if ((e = dalloc(&p->rowptr, n + 1, cs)) != cudaSuccess || (e = dalloc(&p->col, cc.size(), cs)) != cudaSuccess ||
+      (e = cudaMallocAsync(&p->val, std::max<size_t>(1, vv.size() * 4), cs)) != cudaSuccess ||
+      (e = dalloc(&p->cp, n, cs)) != cudaSuccess || (e = dalloc(&p->cp64, n, cs)) != cudaSuccess)
+    return bail(e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation failed") : cuda_fail(e, "cudaMalloc"));
+  if ((e = cudaStreamSynchronize(cs)) != cudaSuccess ||
+      (e = cudaMemcpy(p->rowptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (!cc.empty() && (e = cudaMemcpy(p->col, cc.data(), sizeof(int32_t) * cc.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (!vv.empty() && (e = cudaMemcpy(p->val, vv.data(), sizeof(float) * vv.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (e = cudaMemset(p->cp, 0, sizeof(float) * n)) != cudaSuccess ||
+      (e = cudaMemset(p->cp64, 0, sizeof(int64_t) * n)) != cudaSuccess)
+    return bail(cuda_fail(e, "upload graph"));
+  *out = p;
+  return SBO_OK;
+}
+
 sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
   g_last_error.clear();
   if (!p) return fail(SBO_EINVAL, "problem is NULL");
@@ -753,7 +824,12 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   if (st != SBO_OK) return st;
   // kernel selection
   int ker;
-  if (p->fmt == FMT_CSR) {
+  if (p->fmt == FMT_MAXK) {
+    if (p->opt_kernel != KER_AUTO) return fail(SBO_EINVAL, "Max-k-Cut problems use their own kernel only");
+    if (p->opt_dual != 0) return fail(SBO_EINVAL, "Max-k-Cut runs the per-vertex dual");
+    if (x0 || y0) return fail(SBO_EINVAL, "Max-k-Cut starts from its own random logits (x0, y0 must be NULL)");
+    ker = KER_MAXK;
+  } else if (p->fmt == FMT_CSR) {
     if (p->opt_kernel != KER_AUTO) return fail(SBO_EINVAL, "CSR problems use the CSR kernel only");
     ker = KER_CSR;
   } else if (p->opt_kernel != KER_AUTO) {
@@ -774,7 +850,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   p->prm = *prm;
   p->kernel = ker;
   p->B = prm->restarts;
-  p->layout = ker == KER_CSR ? LAYOUT_NR : LAYOUT_RN;
+  p->layout = (ker == KER_CSR || ker == KER_MAXK) ? LAYOUT_NR : LAYOUT_RN;
   p->op_type = (p->prec == SBO_FP32) ? OP_F32 : OP_BF16;
   p->ld = p->layout == LAYOUT_RN ? round_up(p->n, 8) : round_up(p->B, 8);
   p->t = 0;
@@ -786,18 +862,19 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   const size_t elems = (size_t)rows * p->ld;
   const size_t op_elt = p->op_type == OP_F32 ? 4 : 2;
   cudaError_t e = cudaSuccess;
-  const bool need_master = ker == KER_TINY || p->op_type != OP_F32;
+  const bool need_master = ker == KER_TINY || ker == KER_MAXK || p->op_type != OP_F32;
+  const size_t xelems = elems * (ker == KER_MAXK ? (size_t)p->kparts : 1);   // Max-k-Cut: k logits
   // min-F trace: one entry per evaluation up to T, plus slack for runs continued beyond T
   const int64_t evals_T = prm->iters / prm->eval_every + 2;
   p->trace_cap = std::min<int64_t>(evals_T, 1 << 20) + 4096;
   auto al = [&](void** q, size_t bytes) {
     if (e == cudaSuccess) e = cudaMallocAsync(q, bytes ? bytes : 1, p->stream);
   };
-  if (need_master) al((void**)&p->Xm, elems * 4);
+  if (need_master) al((void**)&p->Xm, xelems * 4);
   al((void**)&p->Y, elems * 4);
   if (ker != KER_TINY) {
-    al(&p->Xop[0], elems * op_elt);
-    al(&p->Xop[1], elems * op_elt);
+    al(&p->Xop[0], xelems * op_elt);
+    al(&p->Xop[1], xelems * op_elt);
     al(&p->bits, elems * op_elt);
   }
   al((void**)&p->bestF, sizeof(long long) * p->B);
@@ -827,10 +904,11 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   }
   cudaStream_t s = p->stream;
   // zero every buffer so padding never holds stale values; sentinels for bests and trace
-  if (p->Xm) cudaMemsetAsync(p->Xm, 0, elems * 4, s);
+  if (p->Xm) cudaMemsetAsync(p->Xm, 0, xelems * 4, s);
   cudaMemsetAsync(p->Y, 0, elems * 4, s);
-  for (void* b : {p->Xop[0], p->Xop[1], p->bits})
-    if (b) cudaMemsetAsync(b, 0, elems * op_elt, s);
+  for (void* b : {p->Xop[0], p->Xop[1]})
+    if (b) cudaMemsetAsync(b, 0, xelems * op_elt, s);
+  if (p->bits) cudaMemsetAsync(p->bits, 0, elems * op_elt, s);
   launch_fill_i64(p->bestF, p->B, LLONG_MAX, s);
   launch_fill_i64(p->bestT, p->B, -1, s);
   launch_fill_i64(p->trace, p->trace_cap, LLONG_MAX, s);
@@ -903,9 +981,13 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
       dfree(x0d, s); dfree(y0d, s); free_run(p); return cuda_fail(e, "single-constraint dual set-up");
     }
   }
-  e = launch_init_state((int)p->n, p->B, p->ld, p->layout, prm->seed, (float)prm->ybar, x0d, y0d, p->Xm,
-                        ker == KER_TINY ? (void*)p->Xm : p->Xop[0], ker == KER_TINY ? OP_F32 : p->op_type, p->Y,
-                        p->err, s);
+  if (ker == KER_MAXK)
+    e = launch_maxk_init((int)p->n, p->B, p->ld, p->kparts, prm->seed, (float)prm->ybar, p->Xm, p->Y,
+                         static_cast<float*>(p->Xop[0]), s);
+  else
+    e = launch_init_state((int)p->n, p->B, p->ld, p->layout, prm->seed, (float)prm->ybar, x0d, y0d, p->Xm,
+                          ker == KER_TINY ? (void*)p->Xm : p->Xop[0], ker == KER_TINY ? OP_F32 : p->op_type, p->Y,
+                          p->err, s);
   ++p->launches;
   if (x0d || y0d) { cudaStreamSynchronize(s); dfree(x0d, s); dfree(y0d, s); }
   if (e != cudaSuccess) { free_run(p); return cuda_fail(e, "init launch"); }
@@ -972,10 +1054,11 @@ sbo_status sbo_eval(sbo_problem* p, int64_t count, const uint8_t* bits, int64_t*
   if (count < 0 || (count > 0 && (!bits || !F))) return fail(SBO_EINVAL, "bad count or NULL arrays");
   if (count == 0) return SBO_OK;
   if (count > (1 << 20)) return fail(SBO_EINVAL, "count too large");
+  const int vmax = p->fmt == FMT_MAXK ? p->kparts - 1 : 1;
   for (int64_t k = 0; k < count * p->n; ++k)
-    if (bits[k] > 1) return fail(SBO_EINVAL, "bits must be 0 or 1");
+    if (bits[k] > vmax) return fail(SBO_EINVAL, p->fmt == FMT_MAXK ? "parts must be < k" : "bits must be 0 or 1");
   cudaStream_t s = p->stream;
-  const int layout = p->fmt == FMT_CSR ? LAYOUT_NR : LAYOUT_RN;
+  const int layout = p->fmt == FMT_DENSE ? LAYOUT_RN : LAYOUT_NR;
   const int op = p->prec == SBO_FP32 ? OP_F32 : OP_BF16;
   const int64_t ld = layout == LAYOUT_RN ? round_up(p->n, 8) : round_up(count, 8);
   const int64_t rows = layout == LAYOUT_RN ? count : p->n;
@@ -1010,7 +1093,9 @@ sbo_status sbo_eval(sbo_problem* p, int64_t count, const uint8_t* bits, int64_t*
   a.err = p->err;
   if (e == cudaSuccess) {
     ++p->launches;
-    if (p->fmt == FMT_CSR) {
+    if (p->fmt == FMT_MAXK) {
+      e = launch_maxk(p->rowptr, p->col, static_cast<const float*>(p->val), a, p->kparts, EPI_EVAL, s);
+    } else if (p->fmt == FMT_CSR) {
       e = launch_csr(p->rowptr, p->col, p->val, p->val_type, a, op, EPI_EVAL, false, s);
     } else if (p->prec == SBO_FP32) {
       e = launch_simt(static_cast<const float*>(p->A), p->lda, a, EPI_EVAL, s);
@@ -1078,12 +1163,16 @@ sbo_status sbo_state(sbo_problem* p, float* X, float* Y) {
   if (!p->started) return fail(SBO_ENOTREADY, "sbo_gda_start has not been called");
   cudaStream_t s = p->stream;
   float* tmp = nullptr;
-  SBO_CUDA(dalloc(&tmp, (size_t)p->B * p->n, s));
+  const int kx = p->kernel == KER_MAXK ? p->kparts : 1;   // Max-k-Cut: X_:,i has k entries
+  SBO_CUDA(dalloc(&tmp, (size_t)p->B * p->n * kx, s));
   const float* xsrc = p->Xm ? p->Xm : static_cast<const float*>(p->Xop[p->cur]);
   cudaError_t e = cudaSuccess;
   if (X) {
-    e = launch_gather_state(xsrc, (int)p->n, p->B, p->ld, p->layout, tmp, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(X, tmp, sizeof(float) * p->B * p->n, cudaMemcpyDeviceToHost, s);
+    if (p->kernel == KER_MAXK)
+      e = launch_maxk_gather(static_cast<const float*>(p->Xop[p->cur]), (int)p->n, kx, p->B, p->ld, tmp, s);
+    else
+      e = launch_gather_state(xsrc, (int)p->n, p->B, p->ld, p->layout, tmp, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(X, tmp, sizeof(float) * p->B * p->n * kx, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
   if (Y && e == cudaSuccess && p->single) {

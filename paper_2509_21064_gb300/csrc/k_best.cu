@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(256) k_eval_commit(CommitArgs one, const Commi
       for (int64_t qv = (int64_t)blockIdx.x * tpr + lq; qv < V; qv += (int64_t)gridDim.x * tpr) {
         const int64_t idx = o * a.ld + 4 * qv;
         const float4 v = op_load4(a.bits, idx, a.op_type);
-        *reinterpret_cast<uchar4*>(a.bestBits + idx) = make_uchar4(v.x != 0.f, v.y != 0.f, v.z != 0.f, v.w != 0.f);
+        *reinterpret_cast<uchar4*>(a.bestBits + idx) =
+            make_uchar4((unsigned char)v.x, (unsigned char)v.y, (unsigned char)v.z, (unsigned char)v.w);
       }
     }
   } else {
@@ -62,10 +63,10 @@ __global__ void __launch_bounds__(256) k_eval_commit(CommitArgs one, const Commi
         const int64_t idx = o * a.ld + q;
         const float4 v = op_load4(a.bits, idx, a.op_type);
         uchar4 nb = *reinterpret_cast<const uchar4*>(a.bestBits + idx);   // padding restarts keep theirs
-        if (i0) nb.x = v.x != 0.f;
-        if (i1) nb.y = v.y != 0.f;
-        if (i2) nb.z = v.z != 0.f;
-        if (i3) nb.w = v.w != 0.f;
+        if (i0) nb.x = (unsigned char)v.x;   // 0/1 bits, or the part index of Max-k-Cut
+        if (i1) nb.y = (unsigned char)v.y;
+        if (i2) nb.z = (unsigned char)v.z;
+        if (i3) nb.w = (unsigned char)v.w;
         *reinterpret_cast<uchar4*>(a.bestBits + idx) = nb;
       }
     }

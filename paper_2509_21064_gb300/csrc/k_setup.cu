@@ -152,7 +152,7 @@ __global__ void k_bits_to_operand(const uint8_t* __restrict__ bits, int n, int c
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / n, i = e % n;
     const int64_t idx = layout == LAYOUT_RN ? r * ld_out + i : i * ld_out + r;
-    op_store(out, idx, bits[e] ? 1.0f : 0.0f, op_type);
+    op_store(out, idx, (float)bits[e], op_type);   // 0/1, or a Max-k-Cut part index
   }
 }
 

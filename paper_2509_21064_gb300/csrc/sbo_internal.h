@@ -11,8 +11,8 @@
 
 namespace sbo {
 
-enum Format : int { FMT_DENSE = 0, FMT_CSR = 1 };
-enum Kernel : int { KER_AUTO = 0, KER_SIMT = 1, KER_TC = 2, KER_TINY = 3, KER_CSR = 4 };
+enum Format : int { FMT_DENSE = 0, FMT_CSR = 1, FMT_MAXK = 2 };
+enum Kernel : int { KER_AUTO = 0, KER_SIMT = 1, KER_TC = 2, KER_TINY = 3, KER_CSR = 4, KER_MAXK = 5 };
 enum Layout : int { LAYOUT_RN = 0 /* [r][i] */, LAYOUT_NR = 1 /* [i][r] */ };
 
 // ---- launchers (each returns the launch's cudaError_t) -----------------------------------
@@ -59,6 +59,12 @@ cudaError_t launch_tiny(const TinyArgs& a, cudaStream_t s);
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
                        const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s);
 int csr_partial_rows(int B);
+// k_maxk.cu  (Max-k-Cut: Z, X as [(i k + j) ld + r], y and parts as [i ld + r]; Z in EpiArgs::Xm)
+cudaError_t launch_maxk(const int32_t* rowptr, const int32_t* col, const float* w, const EpiArgs& a, int kp, int mode,
+                        cudaStream_t s);
+cudaError_t launch_maxk_init(int n, int B, int64_t ld, int kp, uint64_t seed, float ybar, float* Z, float* Y, float* X,
+                             cudaStream_t s);
+cudaError_t launch_maxk_gather(const float* src, int n, int kp, int B, int64_t ld, float* dst, cudaStream_t s);
 // k_best.cu
 struct CommitArgs {
   const void* bits;              // candidate bits of this evaluation (operand type, state layout)

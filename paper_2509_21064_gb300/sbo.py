@@ -22,10 +22,10 @@ SBO_FP32, SBO_BF16, SBO_FP8_E4M3 = 0, 1, 2
 SBO_OPT_KERNEL, SBO_OPT_USE_GRAPH, SBO_OPT_TILE_N, SBO_OPT_TIMEOUT_US, SBO_OPT_SPLIT_K, SBO_OPT_AUTOTUNE, \
     SBO_OPT_PDL, SBO_OPT_DUAL = 1, 2, 3, 4, 5, 6, 7, 8
 DUAL_COORDINATE, DUAL_SINGLE = 0, 1
-KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR, KERNEL_MAXK = 0, 1, 2, 3, 4, 5
 
 # every symbol include/sbo.h declares
-EXPORTS = ["sbo_create_dense", "sbo_create_csr", "sbo_gda_start", "sbo_gda_start_xy", "sbo_gda_run", "sbo_gda", "sbo_sync",
+EXPORTS = ["sbo_create_dense", "sbo_create_csr", "sbo_create_maxkcut", "sbo_gda_start", "sbo_gda_start_xy", "sbo_gda_run", "sbo_gda", "sbo_sync",
            "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace", "sbo_lagrangian", "sbo_lagrangian_noalloc",
            "sbo_set_option", "sbo_info", "sbo_launch_count", "sbo_destroy", "sbo_last_error", "sbo_version",
            "sbo_group_create", "sbo_group_start", "sbo_group_run", "sbo_group_sync", "sbo_group_set_option",
@@ -68,6 +68,8 @@ def lib():
         "sbo_create_dense": (st, [ctypes.c_int64, _I32P, _I32P, ctypes.c_int32, _P, ctypes.POINTER(_P)]),
         "sbo_create_csr": (st, [ctypes.c_int64, ctypes.c_int64, _I64P, _I32P, _I32P, _I32P, ctypes.c_int32, _P,
                                 ctypes.POINTER(_P)]),
+        "sbo_create_maxkcut": (st, [ctypes.c_int64, ctypes.c_int64, _I32P, _I32P, _I32P, ctypes.c_int32, _P,
+                                    ctypes.POINTER(_P)]),
         "sbo_gda_start": (st, [_P, ctypes.POINTER(sbo_gda_params), _F32P]),
         "sbo_gda_start_xy": (st, [_P, ctypes.POINTER(sbo_gda_params), _F32P, _F32P]),
         "sbo_gda_run": (st, [_P, ctypes.c_int64]),
@@ -197,8 +199,22 @@ def sbo_restart_best(h, B):
     return F, t
 
 
-def sbo_state(h, B, n):
-    X = np.zeros((B, n), dtype=np.float32)
+def sbo_create_maxkcut(n, ei, ej, w, k, stream=None):
+    ei = np.ascontiguousarray(ei, dtype=np.int32)
+    ej = np.ascontiguousarray(ej, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    if not (ei.size == ej.size == w.size):
+        raise ValueError("ei, ej and w must have the same length")
+    h = _P()
+    _check(lib().sbo_create_maxkcut(int(n), int(ei.size), _ptr(ei, ctypes.c_int32), _ptr(ej, ctypes.c_int32),
+                                    _ptr(w, ctypes.c_int32), int(k), _stream(stream), ctypes.byref(h)),
+           "sbo_create_maxkcut")
+    return h
+
+
+def sbo_state(h, B, n, k=1):
+    """x (B x n, or B x n x k for Max-k-Cut) and y (B x n)."""
+    X = np.zeros((B, n) if k == 1 else (B, n, k), dtype=np.float32)
     Y = np.zeros((B, n), dtype=np.float32)
     _check(lib().sbo_state(h, _ptr(X, ctypes.c_float), _ptr(Y, ctypes.c_float)), "sbo_state")
     return X, Y
@@ -251,9 +267,10 @@ def sbo_version() -> str:
 class Problem:
     """Owns one problem handle; every method forwards to the entry point of the same name."""
 
-    def __init__(self, handle, n: int):
+    def __init__(self, handle, n: int, k: int = 1):
         self.h = handle
         self.n = int(n)
+        self.k = int(k)          # parts per vertex (Max-k-Cut), 1 otherwise
         self.restarts = 0
 
     @classmethod
@@ -263,6 +280,10 @@ class Problem:
     @classmethod
     def csr(cls, n, rowptr, col, val, c=None, precision=SBO_FP32, stream=None):
         return cls(sbo_create_csr(n, rowptr, col, val, c, precision, stream), n)
+
+    @classmethod
+    def maxkcut(cls, n, ei, ej, w, k, stream=None):
+        return cls(sbo_create_maxkcut(n, ei, ej, w, k, stream), n, k)
 
     def set_option(self, option, value):
         sbo_set_option(self.h, option, value)
@@ -294,7 +315,7 @@ class Problem:
         return sbo_restart_best(self.h, self.restarts)
 
     def state(self):
-        return sbo_state(self.h, self.restarts, self.n)
+        return sbo_state(self.h, self.restarts, self.n, self.k)
 
     def trace(self, cap=1 << 16):
         return sbo_trace(self.h, cap)

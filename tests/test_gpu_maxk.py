@@ -1,0 +1,108 @@
+"""Max-k-Cut (appendix on Max-k-Cut) through the C ABI against the FP64 oracle ``oracle.maxkcut``.
+
+There is no discrete branch inside the iteration (softmax keeps X on the simplex, no perturbation
+rule), so the FP32 trajectory stays within 1e-4 (normwise per restart) of the oracle's over the
+first 30 iterations.  Objectives are exact: the GPU's evaluation of given parts equals the
+oracle's cut, and the best record is the cut of its own parts."""
+import numpy as np
+import pytest
+
+import oracle.maxkcut as K
+import workloads as W
+from paper_2509_21064_gb300 import sbo as S
+from paper_2509_21064_gb300.build import build as build_lib
+from _helpers import gpu_trajectory, normwise, to_gda_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib()
+    S.lib()
+
+
+def _params(B, T, seed=0):
+    return W.GdaParams(restarts=B, iters=T, alpha=0.01, beta=0.01, ybar=6.0, eval_every=10, seed=seed)
+
+
+@pytest.mark.parametrize("k", [3, 5])
+def test_maxk_trajectory_matches_the_oracle(k):
+    """Random graph n = 3001 (ragged rows), +-1 weights, B = 200 (ragged against 128-restart
+    chunks); 30 iterations one launch at a time, then the same 30 by graph replay."""
+    n = 3001
+    i, j, w = W.maxcut_er(n, 6.0, seed=7)
+    p = _params(200, 100, seed=3)
+    prm = to_gda_params(p)
+    with S.Problem.maxkcut(n, i, j, w, k) as P:
+        gx, gy = gpu_trajectory(P, prm, 30)
+        assert P.info()["kernel"] == S.KERNEL_MAXK
+        Wm = K.weight_matrix(n, i, j, w)
+        Z, Y = K.init_state_k(n, k, p.restarts, p.seed, p.ybar)
+        for t in range(31):
+            if t in (0, 1, 10, 30):
+                X = K.softmax(Z)
+                assert normwise(gx[t].reshape(p.restarts, -1), X.reshape(p.restarts, -1)).max() <= 1e-4, t
+                assert normwise(gy[t], Y).max() <= 1e-4, t
+            Z, Y, _ = K.gda_step_k(Wm, Z, Y, p.alpha, p.beta)
+        assert np.allclose(gx[30].sum(axis=2), 1.0, atol=1e-5)
+        P.start(prm)
+        P.run(30)
+        X30, Y30 = P.state()
+        assert np.array_equal(X30, gx[30]) and np.array_equal(Y30, gy[30])
+
+
+def test_maxk_evaluation_is_exact():
+    n, k = 2500, 4
+    i, j, w = W.maxcut_er(n, 8.0, seed=2)
+    rng = np.random.default_rng(0)
+    parts = rng.integers(0, k, size=(37, n)).astype(np.uint8)
+    with S.Problem.maxkcut(n, i, j, w, k) as P:
+        F = S.sbo_eval(P.h, parts)
+    assert np.array_equal(F, -K.cut_value(i, j, w, parts))
+
+
+def test_maxk_best_is_the_cut_of_its_own_parts_and_finds_small_optima():
+    for seed, (n, m, k) in enumerate(((8, 14, 3), (9, 16, 4))):
+        rng = np.random.default_rng(20 + seed)
+        pairs = set()
+        while len(pairs) < m:
+            a, b = sorted(rng.choice(n, size=2, replace=False))
+            pairs.add((int(a), int(b)))
+        i, j = (np.array(v, dtype=np.int32) for v in zip(*sorted(pairs)))
+        w = np.ones(m, dtype=np.int32)
+        best, _ = K.brute_force_k(n, k, i, j, w)
+        with S.Problem.maxkcut(n, i, j, w, k) as P:
+            P.gda(to_gda_params(_params(64, 1500, seed=seed)))
+            parts, F, t, r = P.best()
+        assert F == -K.cut_value(i, j, w, parts)
+        assert F == -best
+
+
+def test_maxk_three_cut_of_a_torus():
+    """Max-3-Cut of a 60 x 60 +-1 torus, the paper's parameters (B = 100, ybar = 6, alpha = beta =
+    0.01), T = 3000: the parts are valid, the best is exact, and the run beats a random 3-partition
+    by a wide margin (expected cut of a random partition: 2/3 of the positive weight minus 2/3 of
+    the negative, about 0)."""
+    i, j, w = W.maxcut_torus(60, 60, seed=4)
+    n = 3600
+    with S.Problem.maxkcut(n, i, j, w, 3) as P:
+        P.gda(to_gda_params(_params(100, 3000)))
+        parts, F, t, r = P.best()
+        X, Y = P.state()
+    assert parts.max() < 3
+    assert F == -K.cut_value(i, j, w, parts)
+    assert -F > 0.6 * int(np.sum(w > 0))
+    assert np.mean(X.max(axis=2) > 0.99) > 0.8       # the iterates approach the simplex vertices
+
+
+def test_maxk_rejects_what_it_does_not_offer():
+    i, j, w = W.maxcut_torus(4, 4, seed=0)
+    with pytest.raises(S.SboError):
+        S.Problem.maxkcut(16, i, j, w, 9)
+    with pytest.raises(S.SboError):
+        S.Problem.maxkcut(16, np.array([0, 3]), np.array([0, 2]), np.array([1, 1]), 3)   # self-loop
+    with S.Problem.maxkcut(16, i, j, w, 3) as P:
+        P.set_option(S.SBO_OPT_DUAL, S.DUAL_SINGLE)
+        with pytest.raises(S.SboError):
+            P.start(to_gda_params(_params(8, 10)))
