@@ -678,6 +678,57 @@ def run_sweep(args):
     return 0
 
 
+# Max-3-Cut stand-ins for the paper's table (Gset shapes; the paper's cut values are context only)
+MAXK_GRAPHS = {
+    "G67 shape: torus 100x100, +-1": lambda: (10000, W.maxcut_torus(100, 100, seed=3)),
+    "G70 shape: random n=10000, ~10^4 unit edges": lambda: (10000, W.maxcut_er(10000, 2.0, seed=0, weights="unit")),
+    "G72 shape: torus 100x100, +-1": lambda: (10000, W.maxcut_torus(100, 100, seed=1)),
+    "G77 shape: torus 100x140, +-1": lambda: (14000, W.maxcut_torus(100, 140, seed=2)),
+    "G81 shape: torus 100x200, +-1": lambda: (20000, W.maxcut_torus(100, 200, seed=0)),
+}
+PAPER_MAX3CUT = {"G67": (8015, 6.0), "G70": (9999, 3.3), "G72": (8111, 4.7), "G77": (11467, 5.0), "G81": (16191, 7.9)}
+
+
+def run_maxkcut(args):
+    """Max-k-Cut (k = args.parts) with the paper's parameters (B = 100, ybar = 6, beta = 0.01 and
+    alpha = args.maxk_alpha, the table's 0.01 by default), T = args.iters, on Gset-shaped synthetic
+    graphs: best cut, device time to it, and the kernel's restart-iterations/s."""
+    import torch
+    from paper_2509_21064_gb300 import sbo as S
+    from paper_2509_21064_gb300.build import build
+    build()
+    S.lib()
+    T, K, B, k = args.iters, 10, 100, args.parts
+    stream = torch.cuda.Stream()
+    rows = []
+    for name, make in MAXK_GRAPHS.items():
+        n, (i, j, w) = make()
+        p = W.GdaParams(restarts=B, iters=T, alpha=args.maxk_alpha, beta=0.01, ybar=6.0, eval_every=K, seed=0)
+        P = S.Problem.maxkcut(n, i, j, w, k, stream=stream)
+        P.start(S.params(**p.asdict()))
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.run(T)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        P.sync()
+        parts, F, t_best, _ = P.best()
+        P.close()
+        cut = int(np.sum(w.astype(np.int64) * (parts[i] != parts[j])))
+        assert cut == -int(F)
+        secs = e0.elapsed_time(e1) * 1e-3
+        row = {"workload": f"Max-{k}-Cut", "graph": name, "n": n, "edges": int(len(i)), "restarts": B, "iters": T,
+               "alpha": args.maxk_alpha,
+               "cut": cut, "best_iteration": int(t_best), "seconds": round(secs, 4),
+               "seconds_to_best": round(secs * t_best / T, 4), "restart_iterations_per_s": B * T / secs,
+               "paper_gset_cut_and_seconds_rtx3090": PAPER_MAX3CUT.get(name[:3]) if k == 3 else None}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -690,7 +741,7 @@ def main():
     ap.add_argument("--no-plain-form", action="store_true")
     ap.add_argument("--n", type=int, default=N_VARS, help="variables (profiling cases only)")
     ap.add_argument("--restarts", type=int, default=RESTARTS, help="restarts (profiling cases only)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "hetero", "mis", "sweep"] + sorted(SPARSE),
+    ap.add_argument("--workload", default="dense", choices=["dense", "hetero", "mis", "sweep", "maxkcut"] + sorted(SPARSE),
                     help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
                     help="weight/operand precision of a sparse workload")
@@ -700,7 +751,9 @@ def main():
     ap.add_argument("--degree", type=int, default=3, help="MIS workload: graph degree")
     ap.add_argument("--mis-params", default="paper", choices=["paper", "scaled"],
                     help="MIS workload: the paper's table (ybar=5, alpha=beta=0.02) or the spectral scaling")
-    ap.add_argument("--iters", type=int, default=3000, help="MIS and sweep workloads: GDA iterations")
+    ap.add_argument("--iters", type=int, default=3000, help="MIS, sweep and maxkcut workloads: GDA iterations")
+    ap.add_argument("--parts", type=int, default=3, help="maxkcut workload: number of parts k")
+    ap.add_argument("--maxk-alpha", type=float, default=0.01, help="maxkcut workload: primal step (paper: 0.01)")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 64, 128, 256, 512, 1064, 1128, 1256],
                     help="tensor-core tile width (0: autotuned); profiling cases only")
     ap.add_argument("--kernel-only", action="store_true",
@@ -714,6 +767,8 @@ def main():
         return run_hetero(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "maxkcut":
+        return run_maxkcut(args)
     if args.workload == "mis":
         if args.n == N_VARS:
             args.n = 10000
