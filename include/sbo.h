@@ -155,11 +155,25 @@ sbo_status sbo_trace(sbo_problem* p, int64_t* minF, int64_t cap, int64_t* count)
  * may be NULL = all ones) scales row r of GX and GY (the adjoint of a per-restart upstream
  * gradient).  L_dev (B), GX_dev, GY_dev (B*n) are device float32 outputs; any may be NULL.  A x is recomputed on every
  * call (nothing is cached between calls), with the contraction of the problem's precision.
- * stream: cudaStream_t or NULL; the call is asynchronous on it.  Scratch of B*n*2 bytes is
- * kept by the handle for the BF16 operand. */
+ * stream: cudaStream_t or NULL; the call is asynchronous on it.  Scratch for the operand is kept
+ * by the handle: B*n*2 bytes (dense BF16), or n*round_up(B,8)*4 (CSR FP32) or *2 (CSR BF16 /
+ * E4M3) bytes in the sparse kernels' variable-major layout.  Dense and CSR QUBO problems; not
+ * Max-k-Cut. */
 sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const float* Y_dev,
                           const float* gout_dev, float* L_dev, float* GX_dev, float* GY_dev,
                           void* stream);
+
+/* sbo_dual_bound: a certified lower bound on min F (the paper's section on the dual certificate).
+ * With y = ybar * 1 and ybar large enough that L(., y) is convex on [0,1]^n (for Max-Cut:
+ * ybar >= -lambda_min(W); in general A + 2 ybar I positive semidefinite -- the caller's
+ * responsibility, the library does not check it), min over the box of L(., y) <= min F, and for
+ * any box point x, L(x) + min over the box of <grad L(x), z - x> <= min over the box of L.  This
+ * call runs `iters` projected gradient steps of size alpha on L(., ybar) (the GDA of section 3.2
+ * with beta = 0 and one restart: it replaces the problem's current run), then forms that bound in
+ * FP64 from an FP64 product A x: *lower_bound gets it, *value (may be NULL) L(x).  For Max-Cut the
+ * cut is at most -(*lower_bound).  QUBO problems only (dense or CSR). */
+sbo_status sbo_dual_bound(sbo_problem* p, double ybar, double alpha, int64_t iters, double* lower_bound,
+                          double* value);
 
 /* sbo_lagrangian_noalloc: the same computation and arguments as sbo_lagrangian, for callers
  * that cannot allocate device memory -- code running inside a CUDA stream capture (where

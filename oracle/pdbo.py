@@ -37,6 +37,10 @@ gda_step_single     Algorithm 1 on that Lagrangian                   beta = 0 re
                                                                      gda_step exactly; on a
                                                                      symmetric instance it is
                                                                      gda_step with beta / n
+certificate         dual bound of the section on the dual            equals L at the box
+                    certificate: L(x) + min over the box of          minimiser (scipy L-BFGS-B);
+                    <grad L(x), z - x>, valid when L(., ybar) is     below brute-force min F
+                    convex on the box
 round_bits / run    best-of-B retention (section 4.2), evaluation    brute force over 2^n;
                     every K iterations and at T                      tie rules on tiny inputs
 brute_force         Lemma 2.3 (min over the vertices)                exhaustive by definition
@@ -248,6 +252,16 @@ def gda_step_single(A, cp, X, MU, alpha, beta, delta, grad_tol=None):
     Xn = np.where(stagnating, perturbed, projected)
     MUn = MU + beta * GMU
     return Xn, MUn, D
+
+
+def certificate(A, cp, ybar, x):
+    """Dual certificate (section on the dual certificate): with y = ybar * 1 and L(., y) convex on
+    the box, every box point x gives min F >= min_box L(., y) >= L(x) + min_{z in box} <grad L(x),
+    z - x> = L(x) - sum_i (grad_i x_i - min(0, grad_i)).  Returns that bound."""
+    x = np.asarray(x, dtype=np.float64).reshape(1, -1)
+    L, GX, _ = lagrangian(A, cp, x, np.full_like(x, float(ybar)))
+    gr = GX[0]
+    return float(L[0] - np.sum(gr * x[0] - np.minimum(0.0, gr)))
 
 
 def round_bits(X):

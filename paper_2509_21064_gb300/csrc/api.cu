@@ -1209,7 +1209,7 @@ sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const f
   g_last_error.clear();
   if (!p) return fail(SBO_EINVAL, "problem is NULL");
   if (B < 1 || !X_dev || !Y_dev) return fail(SBO_EINVAL, "B must be >= 1 and X, Y non-NULL");
-  if (p->fmt != FMT_DENSE) return fail(SBO_EINVAL, "sbo_lagrangian supports dense problems");
+  if (p->fmt == FMT_MAXK) return fail(SBO_EINVAL, "sbo_lagrangian supports QUBO problems (dense or CSR)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   EpiArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -1227,7 +1227,25 @@ sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const f
   a.err = p->err;
   if (L_dev) SBO_CUDA(cudaMemsetAsync(L_dev, 0, sizeof(float) * B, s));
   cudaError_t e;
-  if (p->prec == SBO_FP32) {
+  if (p->fmt == FMT_CSR) {
+    // sparse form: x goes to the variable-major operand of the sparse kernel (FP32, or BF16 for
+    // BF16 / E4M3 weights), the epilogue reads the caller's FP32 x and y
+    const int op = p->prec == SBO_FP32 ? OP_F32 : OP_BF16;
+    const int64_t ldx = round_up(B, 8);
+    const size_t need = (size_t)p->n * ldx * (op == OP_F32 ? 4 : 2);
+    if (need > p->lag_cap) {
+      if (p->lag_op) { cudaStreamSynchronize(s); cudaFree(p->lag_op); p->lag_op = nullptr; p->lag_cap = 0; }
+      SBO_CUDA(cudaMalloc(&p->lag_op, need));   // used on the caller's stream: not stream-ordered
+      p->lag_cap = need;
+    }
+    SBO_CUDA(cudaMemsetAsync(p->lag_op, 0, need, s));
+    e = launch_to_operand_t(X_dev, (int)p->n, B, p->n, p->lag_op, ldx, op, s);
+    if (e != cudaSuccess) return cuda_fail(e, "operand conversion");
+    a.Xin = p->lag_op;
+    a.ld = ldx;
+    e = launch_csr(p->rowptr, p->col, p->val, p->val_type, a, op, EPI_LAGR, false, s);
+    p->launches += 2;
+  } else if (p->prec == SBO_FP32) {
     a.Xin = X_dev;
     e = launch_simt(static_cast<const float*>(p->A), p->lda, a, EPI_LAGR, s);
     ++p->launches;
@@ -1253,6 +1271,77 @@ sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const f
   }
   if (e != cudaSuccess) return cuda_fail(e, "Lagrangian launch");
   return SBO_OK;
+}
+
+sbo_status sbo_dual_bound(sbo_problem* p, double ybar, double alpha, int64_t iters, double* lower_bound,
+                          double* value) {
+  g_last_error.clear();
+  if (!p) return fail(SBO_EINVAL, "problem is NULL");
+  if (p->fmt == FMT_MAXK) return fail(SBO_EINVAL, "the dual certificate is offered for QUBO problems");
+  if (!lower_bound) return fail(SBO_EINVAL, "lower_bound is NULL");
+  if (!std::isfinite(ybar) || ybar <= 0 || !std::isfinite(alpha) || alpha <= 0 || iters < 0)
+    return fail(SBO_EINVAL, "ybar and alpha must be finite and > 0, iters >= 0");
+  // projected gradient descent on L(., ybar): GDA with beta = 0 (y stays ybar > 0, so the
+  // perturbation rule never fires), one restart
+  sbo_gda_params prm{};
+  prm.restarts = 1;
+  prm.iters = iters > 0 ? iters : 1;
+  prm.eval_every = (int32_t)std::min<int64_t>(prm.iters, INT32_MAX);
+  prm.alpha = alpha;
+  prm.beta = 0.0;
+  prm.ybar = ybar;
+  prm.delta = 0.0;
+  prm.grad_tol = 0.0;
+  prm.seed = 0;
+  const int saved_dual = p->opt_dual;
+  p->opt_dual = 0;
+  sbo_status st = sbo_gda_start(p, &prm, nullptr);
+  p->opt_dual = saved_dual;
+  if (st != SBO_OK) return st;
+  if (iters > 0 && (st = sbo_gda_run(p, iters)) != SBO_OK) return st;
+  if ((st = sbo_sync(p)) != SBO_OK) return st;
+  const int64_t n = p->n;
+  cudaStream_t s = p->stream;
+  std::vector<float> xf((size_t)n);
+  std::vector<double> xd((size_t)n), g((size_t)n);
+  std::vector<int64_t> cp((size_t)n);
+  float* tmp = nullptr;
+  double *xdev = nullptr, *gdev = nullptr;
+  cudaError_t e = cudaSuccess;
+  if ((e = dalloc(&tmp, (size_t)n, s)) != cudaSuccess || (e = dalloc(&xdev, (size_t)n, s)) != cudaSuccess ||
+      (e = dalloc(&gdev, (size_t)n, s)) != cudaSuccess) {
+    dfree(tmp, s); dfree(xdev, s); dfree(gdev, s);
+    return cuda_fail(e, "cudaMalloc (dual bound)");
+  }
+  const float* xsrc = p->Xm ? p->Xm : static_cast<const float*>(p->Xop[p->cur]);
+  e = launch_gather_state(xsrc, (int)n, 1, p->ld, p->layout, tmp, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(xf.data(), tmp, sizeof(float) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cp.data(), p->cp64, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (int64_t i = 0; i < n; ++i) xd[i] = (double)xf[i];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(xdev, xd.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    DenseView v{};
+    const bool dense = dense_view(p, &v);
+    e = launch_matvec_f64(dense ? &v : nullptr, p->rowptr, p->col, p->val, p->val_type, (int)n, xdev, gdev, s);
+    p->launches += 2;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g.data(), gdev, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(tmp, s); dfree(xdev, s); dfree(gdev, s);
+  if (e != cudaSuccess) return cuda_fail(e, "dual bound");
+  // L(x) and the linearisation bound min over the box of L(x) + <grad, z - x> (valid when L(., ybar)
+  // is convex on the box), in FP64
+  double L = 0.0, gap = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double x = xd[i], c = (double)cp[i];
+    L += 0.5 * x * g[i] + c * x + ybar * (x * x - x);
+    const double grad = g[i] + c + ybar * (2.0 * x - 1.0);
+    gap += grad * x - std::min(0.0, grad);
+  }
+  *lower_bound = L - gap;
+  if (value) *value = L;
+  return read_err(p);
 }
 
 sbo_status sbo_info(const sbo_problem* p, int64_t* n, int32_t* restarts, int32_t* kernel, int32_t* tile_n, int64_t* t) {

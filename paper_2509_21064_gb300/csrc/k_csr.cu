@@ -114,8 +114,16 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
           xo[v] = a.Xm ? *reinterpret_cast<const float4*>(a.Xm + idx) : load4<OP_F32>(Xin, idx);
           yo[v] = a.mu ? *reinterpret_cast<const float4*>(a.mu + r0)    // the restarts' duals
                        : *reinterpret_cast<const float4*>(a.Y + idx);
-        } else {
+        } else if (MODE == EPI_EVAL) {
           xo[v] = load4<OPT>(Xin, idx);   // EPI_EVAL: the row's own bits
+        } else {
+          // EPI_LAGR: the caller's restart-major FP32 x and y, [r][n]
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const bool ok = r0 + k < B;
+            set_comp(xo[v], k, ok ? a.Xl[(r0 + k) * (int64_t)n + i] : 0.0f);
+            set_comp(yo[v], k, ok ? a.Yl[(r0 + k) * (int64_t)n + i] : 0.0f);
+          }
         }
       }
     }
@@ -175,12 +183,27 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           if (r0 + k < B && comp(xo[v], k) != 0.0f) f2[v][k] += (long long)comp(acc[v], k) + cp2;
+      } else {
+        // Lagrangian of section 3.1: dL/dx = A x + c' + y (2x - 1), dL/dy = g(x), and the row's
+        // share 1/2 x (A x) + c' x + y g(x) of L, summed per restart below
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t r = r0 + k;
+          if (r >= B) continue;
+          const float x = comp(xo[v], k), y = comp(yo[v], k), g = comp(acc[v], k);
+          const float gx = x * x - x;
+          const float sc = a.gout ? a.gout[r] : 1.0f;
+          if (a.GX) a.GX[r * n + i] = sc * (g + cpi + y * (2.0f * x - 1.0f));
+          if (a.GY) a.GY[r * n + i] = sc * gx;
+          set_comp(gs[v], k, comp(gs[v], k) + 0.5f * x * g + cpi * x + y * gx);
+        }
       }
     }
   }
-  if (MODE == EPI_UPDATE && a.mu) {
+  if ((MODE == EPI_UPDATE && a.mu) || (MODE == EPI_LAGR && a.L)) {
     // single-constraint form: the block's warps cover the same restarts; their sums of g go to
-    // shared memory and are added in warp order into this block's row of partial sums
+    // shared memory and are added in warp order into this block's row of partial sums.
+    // Lagrangian: the same per-block sums of the rows' shares of L, added to L[r] atomically
     __shared__ float redf[8][128 * NV];
     const int w = threadIdx.x >> 5;
 #pragma unroll
@@ -190,7 +213,9 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
     for (int t = threadIdx.x; t < 128 * NV; t += blockDim.x) {
       float sum = 0.0f;
       for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += redf[q][t];
-      if (rb + t < B) a.gpart[(int64_t)blockIdx.x * a.gpart_ld + rb + t] = sum;
+      if (rb + t >= B) continue;
+      if (MODE == EPI_LAGR) atomicAdd(&a.L[rb + t], sum);
+      else a.gpart[(int64_t)blockIdx.x * a.gpart_ld + rb + t] = sum;
     }
   }
   if (MODE == EPI_EVAL) {
@@ -228,7 +253,7 @@ static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const
   const int64_t chunks = (a.B + 128 * NV - 1) / (128 * NV);
   const int warps_per_block = 8;
   int64_t want = (a.n + warps_per_block - 1) / warps_per_block;
-  if (MODE == EPI_EVAL || a.mu) {
+  if (MODE != EPI_UPDATE || a.mu) {
     // bounds the closing atomics (evaluation) or the rows of partial sums (single-constraint form)
     const int64_t cap = csr_partial_rows(a.B);
     if (want > cap) want = cap;
@@ -257,6 +282,10 @@ cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* va
   if (mode == EPI_EVAL) {
     return op_type == OP_F32 ? launch_csr_v<EPI_EVAL, OP_F32>(rowptr, col, val, val_type, a, pdl, s)
                              : launch_csr_v<EPI_EVAL, OP_BF16>(rowptr, col, val, val_type, a, pdl, s);
+  }
+  if (mode == EPI_LAGR) {
+    return op_type == OP_F32 ? launch_csr_v<EPI_LAGR, OP_F32>(rowptr, col, val, val_type, a, pdl, s)
+                             : launch_csr_v<EPI_LAGR, OP_BF16>(rowptr, col, val, val_type, a, pdl, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -144,6 +144,26 @@ cudaError_t launch_to_operand(const float* X, int n, int B, int64_t ld_in, void*
   return cudaGetLastError();
 }
 
+// The same conversion into the variable-major layout of the sparse kernels: out[i * ld_out + r].
+__global__ void k_to_operand_t(const float* __restrict__ X, int n, int B, int64_t ld_in, void* out,
+                               int64_t ld_out, int op_type) {
+  const int64_t total = (int64_t)n * B;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / n, i = e % n;
+    op_store(out, i * ld_out + r, X[r * ld_in + i], op_type);
+  }
+}
+
+cudaError_t launch_to_operand_t(const float* X, int n, int B, int64_t ld_in, void* out, int64_t ld_out,
+                                int op_type, cudaStream_t s) {
+  const int64_t total = (int64_t)n * B;
+  const int64_t blocks = (total + 255) / 256;
+  k_to_operand_t<<<(unsigned)(blocks < 152 * 64 ? blocks : 152 * 64), 256, 0, s>>>(X, n, B, ld_in, out, ld_out,
+                                                                                   op_type);
+  return cudaGetLastError();
+}
+
 // 0/1 bytes [count][n] -> operand (0.0 / 1.0) in `layout`.
 __global__ void k_bits_to_operand(const uint8_t* __restrict__ bits, int n, int count, void* out,
                                   int64_t ld_out, int layout, int op_type) {

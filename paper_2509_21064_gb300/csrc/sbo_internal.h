@@ -27,6 +27,8 @@ cudaError_t launch_init_state(int n, int B, int64_t ld, int layout, uint64_t see
                               uint32_t* err, cudaStream_t s);
 cudaError_t launch_to_operand(const float* X, int n, int B, int64_t ld_in, void* out, int64_t ld_out,
                               int op_type, cudaStream_t s);
+cudaError_t launch_to_operand_t(const float* X, int n, int B, int64_t ld_in, void* out, int64_t ld_out,
+                                int op_type, cudaStream_t s);
 cudaError_t launch_bits_to_operand(const uint8_t* bits, int n, int count, void* out, int64_t ld_out,
                                    int layout, int op_type, cudaStream_t s);
 cudaError_t launch_fill_i64(long long* p, int64_t count, long long v, cudaStream_t s);
@@ -148,6 +150,9 @@ struct DenseView {
   int sms;
   int64_t* launches;
 };
+// k_cert.cu: g = A x in FP64 for one point (dense: pass the problem's view; sparse: view NULL)
+cudaError_t launch_matvec_f64(const DenseView* dense, const int32_t* rowptr, const int32_t* col, const void* val,
+                              int val_type, int n, const double* x, double* g, cudaStream_t s);
 bool dense_view(sbo_problem* p, DenseView* v);
 void set_last_error(const std::string& msg);
 

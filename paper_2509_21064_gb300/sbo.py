@@ -26,7 +26,7 @@ KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR, KERNEL_MAXK = 0, 1
 
 # every symbol include/sbo.h declares
 EXPORTS = ["sbo_create_dense", "sbo_create_csr", "sbo_create_maxkcut", "sbo_gda_start", "sbo_gda_start_xy", "sbo_gda_run", "sbo_gda", "sbo_sync",
-           "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace", "sbo_lagrangian", "sbo_lagrangian_noalloc",
+           "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace", "sbo_lagrangian", "sbo_lagrangian_noalloc", "sbo_dual_bound",
            "sbo_set_option", "sbo_info", "sbo_launch_count", "sbo_destroy", "sbo_last_error", "sbo_version",
            "sbo_group_create", "sbo_group_start", "sbo_group_run", "sbo_group_sync", "sbo_group_set_option",
            "sbo_group_launch_count", "sbo_group_destroy"]
@@ -71,6 +71,8 @@ def lib():
         "sbo_create_maxkcut": (st, [ctypes.c_int64, ctypes.c_int64, _I32P, _I32P, _I32P, ctypes.c_int32, _P,
                                     ctypes.POINTER(_P)]),
         "sbo_gda_start": (st, [_P, ctypes.POINTER(sbo_gda_params), _F32P]),
+        "sbo_dual_bound": (st, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
         "sbo_gda_start_xy": (st, [_P, ctypes.POINTER(sbo_gda_params), _F32P, _F32P]),
         "sbo_gda_run": (st, [_P, ctypes.c_int64]),
         "sbo_gda": (st, [_P, ctypes.POINTER(sbo_gda_params)]),
@@ -212,6 +214,14 @@ def sbo_create_maxkcut(n, ei, ej, w, k, stream=None):
     return h
 
 
+def sbo_dual_bound(h, ybar, alpha, iters):
+    """(certified lower bound on min F, L at the final point); see include/sbo.h."""
+    lb, val = ctypes.c_double(), ctypes.c_double()
+    _check(lib().sbo_dual_bound(h, float(ybar), float(alpha), int(iters), ctypes.byref(lb), ctypes.byref(val)),
+           "sbo_dual_bound")
+    return lb.value, val.value
+
+
 def sbo_state(h, B, n, k=1):
     """x (B x n, or B x n x k for Max-k-Cut) and y (B x n)."""
     X = np.zeros((B, n) if k == 1 else (B, n, k), dtype=np.float32)
@@ -316,6 +326,10 @@ class Problem:
 
     def state(self):
         return sbo_state(self.h, self.restarts, self.n, self.k)
+
+    def dual_bound(self, ybar, alpha, iters):
+        self.restarts = 1
+        return sbo_dual_bound(self.h, ybar, alpha, iters)
 
     def trace(self, cap=1 << 16):
         return sbo_trace(self.h, cap)
