@@ -169,8 +169,9 @@ sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const f
  * responsibility, the library does not check it), min over the box of L(., y) <= min F, and for
  * any box point x, L(x) + min over the box of <grad L(x), z - x> <= min over the box of L.  This
  * call runs `iters` projected gradient steps of size alpha on L(., ybar) (the GDA of section 3.2
- * with beta = 0 and one restart: it replaces the problem's current run), then forms that bound in
- * FP64 from an FP64 product A x: *lower_bound gets it, *value (may be NULL) L(x).  For Max-Cut the
+ * with beta = 0 and one restart: it replaces the problem's current run), polishes the point with
+ * min(iters, 500) FP64 projected gradient steps, then forms that bound in FP64 from an FP64
+ * product A x: *lower_bound gets it, *value (may be NULL) L(x).  For Max-Cut the
  * cut is at most -(*lower_bound).  QUBO problems only (dense or CSR). */
 sbo_status sbo_dual_bound(sbo_problem* p, double ybar, double alpha, int64_t iters, double* lower_bound,
                           double* value);

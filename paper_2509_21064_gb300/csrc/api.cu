@@ -1320,12 +1320,20 @@ sbo_status sbo_dual_bound(sbo_problem* p, double ybar, double alpha, int64_t ite
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   for (int64_t i = 0; i < n; ++i) xd[i] = (double)xf[i];
   if (e == cudaSuccess) e = cudaMemcpyAsync(xdev, xd.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) {
-    DenseView v{};
-    const bool dense = dense_view(p, &v);
+  DenseView v{};
+  const bool dense = dense_view(p, &v);
+  // FP64 polish of the point (the fast path's operand may be BF16), then g = A x at the final point
+  const int64_t polish = std::min<int64_t>(iters, 500);
+  for (int64_t k = 0; k < polish && e == cudaSuccess; ++k) {
     e = launch_matvec_f64(dense ? &v : nullptr, p->rowptr, p->col, p->val, p->val_type, (int)n, xdev, gdev, s);
+    if (e == cudaSuccess) e = launch_pgd_step_f64(xdev, gdev, p->cp64, (int)n, ybar, alpha, s);
     p->launches += 2;
   }
+  if (e == cudaSuccess) {
+    e = launch_matvec_f64(dense ? &v : nullptr, p->rowptr, p->col, p->val, p->val_type, (int)n, xdev, gdev, s);
+    ++p->launches;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(xd.data(), xdev, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g.data(), gdev, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   dfree(tmp, s); dfree(xdev, s); dfree(gdev, s);

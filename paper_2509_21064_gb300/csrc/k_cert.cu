@@ -1,8 +1,9 @@
-// FP64 product g = A x for one point x, used by the dual certificate (the paper's section on the
-// dual certificate): with y = ybar large enough that L(., y) is convex on the box, any box point
-// x gives the lower bound L(x) + min over the box of <grad L(x), z - x> on min F.  The bound is
-// formed on the host in FP64 from g; A is exact in its storage type, so the only rounding left is
-// FP64's.  One warp per row: dense rows are read with the lanes striding over the columns, sparse
+// FP64 product g = A x for one point x and an FP64 projected gradient step, used by the dual
+// certificate (the paper's section on the dual certificate): with y = ybar large enough that
+// L(., y) is convex on the box, any box point x gives the lower bound L(x) + min over the box of
+// <grad L(x), z - x> on min F.  The point from the fast path (whose operand may be BF16) is
+// polished by FP64 steps, and the bound is formed on the host in FP64 from g; A is exact in its
+// storage type, so the only rounding left is FP64's.  One warp per row: dense rows are read with the lanes striding over the columns, sparse
 // rows with the lanes striding over the row's entries; a warp-shuffle sum closes each row.
 #include <algorithm>
 
@@ -59,7 +60,24 @@ __global__ void k_matvec_csr_f64(const int32_t* __restrict__ rowptr, const int32
   }
 }
 
+// One FP64 projected gradient step on L(., ybar) given g = A x: x <- clip(x - alpha grad, 0, 1).
+__global__ void k_pgd_step_f64(double* x, const double* __restrict__ g, const int64_t* __restrict__ cp, int n,
+                               double ybar, double alpha) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double xi = x[i];
+    const double grad = g[i] + (double)cp[i] + ybar * (2.0 * xi - 1.0);
+    x[i] = fmin(1.0, fmax(0.0, xi - alpha * grad));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pgd_step_f64(double* x, const double* g, const int64_t* cp, int n, double ybar, double alpha,
+                                cudaStream_t s) {
+  const unsigned blocks = (unsigned)std::min<int64_t>(((int64_t)n + 255) / 256, 152 * 8);
+  k_pgd_step_f64<<<blocks, 256, 0, s>>>(x, g, cp, n, ybar, alpha);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_matvec_f64(const DenseView* dense, const int32_t* rowptr, const int32_t* col, const void* val,
                               int val_type, int n, const double* x, double* g, cudaStream_t s) {

@@ -153,6 +153,8 @@ struct DenseView {
 // k_cert.cu: g = A x in FP64 for one point (dense: pass the problem's view; sparse: view NULL)
 cudaError_t launch_matvec_f64(const DenseView* dense, const int32_t* rowptr, const int32_t* col, const void* val,
                               int val_type, int n, const double* x, double* g, cudaStream_t s);
+cudaError_t launch_pgd_step_f64(double* x, const double* g, const int64_t* cp, int n, double ybar, double alpha,
+                                cudaStream_t s);
 bool dense_view(sbo_problem* p, DenseView* v);
 void set_last_error(const std::string& msg);
 
