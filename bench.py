@@ -729,6 +729,54 @@ def run_maxkcut(args):
     return 0
 
 
+PAPER_DUAL_BOUNDS = {"G67": (6872, 8843.7), "G70": (9537, 13891.5), "G72": (6906, 8906.1), "G77": (9812, 12767.7),
+                     "G81": (13852, 18172.2)}
+CERT_GRAPHS = {
+    "G67 shape: torus 100x100, +-1": lambda: (10000, W.maxcut_torus(100, 100, seed=3)),
+    "G70 shape: random n=10000, ~10^4 unit edges": lambda: (10000, W.maxcut_er(10000, 2.0, seed=0, weights="unit")),
+    "G72 shape: torus 100x100, +-1": lambda: (10000, W.maxcut_torus(100, 100, seed=1)),
+    "G77 shape: torus 100x140, +-1": lambda: (14000, W.maxcut_torus(100, 140, seed=2)),
+    "G81 shape: torus 100x200, +-1": lambda: (20000, W.maxcut_torus(100, 200, seed=0)),
+}
+
+
+def run_certificate(args):
+    """Primal and dual bounds for Max-Cut (the paper's dual-certificate table) on Gset-shaped graphs:
+    the best cut PDBO finds (paper parameters, B = 100, T = args.iters) and the certified upper bound
+    -sbo_dual_bound at ybar = -lambda_min(W) (the smallest convex start; lambda from scipy)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    import torch
+    from paper_2509_21064_gb300 import sbo as S
+    from paper_2509_21064_gb300.build import build
+    build()
+    S.lib()
+    stream = torch.cuda.Stream()
+    for name, make in CERT_GRAPHS.items():
+        n, (i, j, w) = make()
+        rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+        Wm = sp.coo_matrix((w.astype(np.float64), (i, j)), shape=(n, n))
+        Wm = (Wm + Wm.T).tocsr()
+        lam_min = float(spla.eigsh(Wm, k=1, which="SA", return_eigenvectors=False)[0])
+        lam_max = float(spla.eigsh(Wm, k=1, which="LA", return_eigenvectors=False)[0])
+        p = W.graph_params("maxcut", restarts=100, iters=args.iters, eval_every=10, seed=0)
+        P = S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32, stream=stream)
+        P.gda(S.params(**p.asdict()))
+        x, F, _, _ = P.best()
+        cut = int(np.sum(w.astype(np.int64) * (x[i] != x[j])))
+        ybar = -lam_min + 1e-6
+        alpha = 1.0 / (2.0 * lam_max + 2.0 * ybar)
+        t0 = time.time()
+        lb, val_ = P.dual_bound(ybar, alpha, args.cert_iters)
+        secs = time.time() - t0
+        P.close()
+        print(json.dumps({"workload": "Max-Cut primal and dual bounds", "graph": name, "n": n,
+                          "lambda_min_W": round(lam_min, 5), "primal_cut": cut, "dual_bound": round(-lb, 2),
+                          "gap_percent": round(100.0 * (-lb - cut) / cut, 2), "certificate_seconds": round(secs, 2),
+                          "paper_gset_primal_dual": PAPER_DUAL_BOUNDS.get(name[:3])}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -741,7 +789,7 @@ def main():
     ap.add_argument("--no-plain-form", action="store_true")
     ap.add_argument("--n", type=int, default=N_VARS, help="variables (profiling cases only)")
     ap.add_argument("--restarts", type=int, default=RESTARTS, help="restarts (profiling cases only)")
-    ap.add_argument("--workload", default="dense", choices=["dense", "hetero", "mis", "sweep", "maxkcut"] + sorted(SPARSE),
+    ap.add_argument("--workload", default="dense", choices=["dense", "hetero", "mis", "sweep", "maxkcut", "certificate"] + sorted(SPARSE),
                     help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
                     help="weight/operand precision of a sparse workload")
@@ -754,6 +802,7 @@ def main():
     ap.add_argument("--iters", type=int, default=3000, help="MIS, sweep and maxkcut workloads: GDA iterations")
     ap.add_argument("--parts", type=int, default=3, help="maxkcut workload: number of parts k")
     ap.add_argument("--maxk-alpha", type=float, default=0.01, help="maxkcut workload: primal step (paper: 0.01)")
+    ap.add_argument("--cert-iters", type=int, default=20000, help="certificate workload: projected gradient steps")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 64, 128, 256, 512, 1064, 1128, 1256],
                     help="tensor-core tile width (0: autotuned); profiling cases only")
     ap.add_argument("--kernel-only", action="store_true",
@@ -769,6 +818,8 @@ def main():
         return run_sweep(args)
     if args.workload == "maxkcut":
         return run_maxkcut(args)
+    if args.workload == "certificate":
+        return run_certificate(args)
     if args.workload == "mis":
         if args.n == N_VARS:
             args.n = 10000
