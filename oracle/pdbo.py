@@ -20,9 +20,11 @@ canonicalize        Prop. 2.4 (exponents dropped on binary points)   Def. 2.2 ex
 objective           Eq. 1 with the QUBO objective                    Max-Cut edge count; MIS
                                                                      count; golden file
 multilinear         Def. 2.2 / Prop. 2.4 closed form                 enumeration; Lemma 2.3
-lagrangian          Lagrangian of section 3.1, g(x) = x^2 - x        Prop. 3.1 (L = F on binary
-                                                                     points); central finite
-                                                                     differences; Example in 3.2
+lagrangian          Lagrangian of section 3.1, g(x) = x^2 - x or     Prop. 3.1 (L = F on binary
+                    the entropy x log x + (1-x) log(1-x)             points); central finite
+                                                                     differences; Example in 3.2;
+                                                                     entropy: its three
+                                                                     conditions of section 3.1
 splitmix64/uniform  x^0 ~ Uniform([0,1]^n) (App. C.1) drawn from the  published SplitMix64 output
                     SplitMix64 generator (Steele, Lea, Flood 2014)   for seed 0
 gda_step            Eq. 5 and Algorithm 1                            hand-worked golden steps;
@@ -134,18 +136,46 @@ def g_prime(x):
     return 2.0 * x - 1.0
 
 
-def lagrangian(A, cp, X, Y):
+ENTROPY_EPS = 1e-6
+
+
+def g_entropy(x):
+    """The entropy constraint function x log x + (1 - x) log(1 - x) named in section 3.1, extended
+    continuously by g(0) = g(1) = 0."""
+    x = np.asarray(x, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        a = np.where(x > 0.0, x * np.log(np.where(x > 0.0, x, 1.0)), 0.0)
+        b = np.where(x < 1.0, (1.0 - x) * np.log(np.where(x < 1.0, 1.0 - x, 1.0)), 0.0)
+    return a + b
+
+
+def g_entropy_prime(x):
+    """log(x / (1 - x)), unbounded at 0 and 1: taken at x clamped to [ENTROPY_EPS, 1 - ENTROPY_EPS]."""
+    xc = np.clip(np.asarray(x, dtype=np.float64), ENTROPY_EPS, 1.0 - ENTROPY_EPS)
+    return np.log(xc) - np.log1p(-xc)
+
+
+def _g_pair(kind):
+    if kind == "quadratic":
+        return g, g_prime
+    if kind == "entropy":
+        return g_entropy, g_entropy_prime
+    raise ValueError("g must be 'quadratic' or 'entropy'")
+
+
+def lagrangian(A, cp, X, Y, gkind="quadratic"):
     """Value and gradients of ``L(x, y) = f(x) + sum_i y_i g(x_i)`` for every restart.
 
     Returns ``(L[B], dL/dX [B, n], dL/dY [B, n])`` with
-    ``dL/dx = A x + c' + y * g'(x)`` and ``dL/dy = g(x)``.
+    ``dL/dx = A x + c' + y * g'(x)`` and ``dL/dy = g(x)``; ``gkind`` selects g (section 3.1).
     """
+    gf, gp = _g_pair(gkind)
     X = np.atleast_2d(np.asarray(X, dtype=np.float64))
     Y = np.atleast_2d(np.asarray(Y, dtype=np.float64))
     AX = np.asarray((A @ X.T).T)          # A dense or scipy sparse
-    Lval = 0.5 * np.einsum("ri,ri->r", X, AX) + X @ cp + np.sum(Y * g(X), axis=1)
-    GX = AX + cp[None, :] + Y * g_prime(X)
-    GY = g(X)
+    Lval = 0.5 * np.einsum("ri,ri->r", X, AX) + X @ cp + np.sum(Y * gf(X), axis=1)
+    GX = AX + cp[None, :] + Y * gp(X)
+    GY = gf(X)
     return Lval, GX, GY
 
 
@@ -211,7 +241,7 @@ def init_state(n, B, seed, ybar):
 # ----------------------------------------------------------------------------------------
 # one iteration of Algorithm 1 for every restart
 # ----------------------------------------------------------------------------------------
-def gda_step(A, cp, X, Y, alpha, beta, delta, grad_tol=None):
+def gda_step(A, cp, X, Y, alpha, beta, delta, grad_tol=None, gkind="quadratic"):
     """One simultaneous projected GDA iteration with the delta-perturbation (Algorithm 1).
 
     For each restart and coordinate i, with d_i = dL/dx_i (x^t, y^t):
@@ -220,14 +250,14 @@ def gda_step(A, cp, X, Y, alpha, beta, delta, grad_tol=None):
       else:
           x_i <- Pi_[0,1](x_i - alpha d_i)
       y_i <- y_i + beta g(x_i)       (g evaluated at the old x_i: the updates are simultaneous)
-    ``grad_tol`` defaults to 2*delta, the threshold Algorithm 1 prints.
+    ``grad_tol`` defaults to 2*delta, the threshold Algorithm 1 prints; ``gkind`` selects g.
     Returns (X^{t+1}, Y^{t+1}, D^t).
     """
     if grad_tol is None:
         grad_tol = 2.0 * delta
     X = np.asarray(X, dtype=np.float64)
     Y = np.asarray(Y, dtype=np.float64)
-    _, D, GY = lagrangian(A, cp, X, Y)
+    _, D, GY = lagrangian(A, cp, X, Y, gkind)
     stagnating = (np.abs(X - 0.5) <= delta) & (np.abs(D) <= grad_tol) & (Y <= 0.0)
     perturbed = np.where(X <= 0.5, 0.5 - delta, 0.5 + delta)
     projected = np.minimum(1.0, np.maximum(0.0, X - alpha * D))
@@ -278,7 +308,8 @@ def eval_points(T, K):
 
 
 def run(Q, c, restarts, iters, alpha, beta, ybar, delta=0.01, grad_tol=None, eval_every=10,
-        seed=0, X0=None, Y0=None, dump_iters=0, A=None, cp=None, dual="coordinate", **_ignored):
+        seed=0, X0=None, Y0=None, dump_iters=0, A=None, cp=None, dual="coordinate", gkind="quadratic",
+        **_ignored):
     """Batched PDBO: B restarts of Algorithm 1, best candidate retained (section 4.2).
 
     Candidates b = round_bits(x^t) are evaluated exactly at every t in eval_points(T, K).
@@ -303,7 +334,11 @@ def run(Q, c, restarts, iters, alpha, beta, ybar, delta=0.01, grad_tol=None, eva
         Y0 = np.full((restarts, n), float(ybar))
     X = np.array(X0, dtype=np.float64)
     Y = np.array(Y0, dtype=np.float64)
-    step = gda_step_single if dual == "single" else gda_step
+    if dual == "single":
+        step = gda_step_single
+    else:
+        def step(A_, cp_, X_, Y_, a_, b_, d_, gt_):
+            return gda_step(A_, cp_, X_, Y_, a_, b_, d_, gt_, gkind)
     pts = set(eval_points(iters, eval_every))
     best_F = np.full(restarts, np.iinfo(np.int64).max, dtype=np.int64)
     best_t = np.full(restarts, -1, dtype=np.int64)
