@@ -613,12 +613,13 @@ def run_sweep(args):
     T, K = args.iters, 10
     stream = torch.cuda.Stream()
 
-    def one(n, csr, i, j, w, ybar=6.0, alpha=0.025, beta=0.025, B=100, dual=0, iters=None):
+    def one(n, csr, i, j, w, ybar=6.0, alpha=0.025, beta=0.025, B=100, dual=0, iters=None, gkind=0):
         rowptr, col, val, c = csr
         T_run = iters or T
         p = W.GdaParams(restarts=B, iters=T_run, alpha=alpha, beta=beta, ybar=ybar, eval_every=K, seed=0)
         P = S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32, stream=stream)
         P.set_option(S.SBO_OPT_DUAL, dual)
+        P.set_option(S.SBO_OPT_G, gkind)
         P.start(S.params(**p.asdict()))
         with torch.cuda.stream(stream):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -668,8 +669,9 @@ def run_sweep(args):
         res = {}
         # PDBO-s with the table's beta takes dual steps of up to n beta / 4; with beta / n its dual
         # step is that of the normalised constraint (1/n) sum_i g(x_i) = 0
-        for label, dual, beta in (("PDBO-s (beta/n)", 1, 0.025 / n), ("PDBO-s (beta)", 1, 0.025), ("PDBO", 0, 0.025)):
-            res[label] = one(n, csr, i, j, w, dual=dual, beta=beta)
+        for label, dual, beta, gk in (("PDBO-s (beta/n)", 1, 0.025 / n, 0), ("PDBO-s (beta)", 1, 0.025, 0),
+                                      ("PDBO", 0, 0.025, 0), ("PDBO, entropy g", 0, 0.025, 1)):
+            res[label] = one(n, csr, i, j, w, dual=dual, beta=beta, gkind=gk)
             print(json.dumps({"workload": "ablation", "graph": name, "method": label, **res[label]}), flush=True)
         out["ablation"][name] = res
     print(json.dumps({"workload": "Max-Cut sensitivity and PDBO-s ablation (synthetic Gset-shaped graphs)",

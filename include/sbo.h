@@ -224,9 +224,15 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       perturbation rule with mu in place of y_i, and mu <- mu + beta sum_i g(x_i)
  *                       on the old x.  Set before sbo_gda_start; y0 then gives mu0_r = y0[r*n];
  *                       sbo_state reports mu_r in every coordinate of restart r.  Not available in
- *                       grouped runs or the tiny kernel (FP32 problems with n <= 64 use SIMT) */
+ *                       grouped runs or the tiny kernel (FP32 problems with n <= 64 use SIMT)
+ *   SBO_OPT_G:          constraint function g of the Lagrangian (section 3.1): 0 (default) the
+ *                       quadratic x^2 - x; 1 the entropy x log x + (1 - x) log(1 - x) (g(0) = g(1)
+ *                       = 0), whose derivative log(x / (1 - x)) is taken at x clamped to
+ *                       [1e-6, 1 - 1e-6].  Applies to the run (update and dual step) and to
+ *                       sbo_lagrangian; QUBO problems only; sbo_dual_bound always uses the quadratic
+ *                       g */
 enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4, SBO_OPT_SPLIT_K = 5,
-       SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7, SBO_OPT_DUAL = 8 };
+       SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7, SBO_OPT_DUAL = 8, SBO_OPT_G = 9 };
 sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
 
 /* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL; 4 the

@@ -99,6 +99,7 @@ struct sbo_problem {
   // options
   int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0, opt_split_k = 16, opt_autotune = 1, opt_pdl = 1;
   int opt_dual = 0;           // 0: one dual per coordinate (PDBO); 1: one per restart (PDBO-s)
+  int opt_g = G_QUAD;         // constraint function g (SBO_OPT_G)
   int64_t opt_timeout_us = 4000000;
   // run
   bool started = false;
@@ -206,6 +207,7 @@ EpiArgs base_args(const sbo_problem* p) {
   a.Y = p->Y;
   a.F2 = p->F2;
   a.err = p->err;
+  a.gkind = p->opt_g;
   if (p->single) {
     a.mu = p->mu;
     a.gpart = p->gpart;
@@ -336,6 +338,7 @@ sbo_status run_tiny(sbo_problem* p, int64_t steps) {
   a.X = p->Xm;
   a.Y = p->Y;
   a.alpha = (float)p->prm.alpha;
+  a.gkind = p->opt_g;
   a.beta = (float)p->prm.beta;
   a.delta = (float)p->prm.delta;
   a.grad_tol = (float)p->prm.grad_tol;
@@ -797,6 +800,10 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       return SBO_OK;
     case SBO_OPT_AUTOTUNE: p->opt_autotune = value != 0; return SBO_OK;
     case SBO_OPT_PDL: p->opt_pdl = value != 0; return SBO_OK;
+    case SBO_OPT_G:
+      if (value != G_QUAD && value != G_ENTROPY) return fail(SBO_EINVAL, "g must be 0 (quadratic) or 1 (entropy)");
+      p->opt_g = (int)value;
+      return SBO_OK;
     case SBO_OPT_DUAL:
       if (value != 0 && value != 1) return fail(SBO_EINVAL, "dual form must be 0 (per coordinate) or 1 (per restart)");
       p->opt_dual = (int)value;
@@ -828,6 +835,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
     if (p->opt_kernel != KER_AUTO) return fail(SBO_EINVAL, "Max-k-Cut problems use their own kernel only");
     if (p->opt_dual != 0) return fail(SBO_EINVAL, "Max-k-Cut runs the per-vertex dual");
     if (x0 || y0) return fail(SBO_EINVAL, "Max-k-Cut starts from its own random logits (x0, y0 must be NULL)");
+    if (p->opt_g != G_QUAD) return fail(SBO_EINVAL, "Max-k-Cut uses the quadratic constraint function");
     ker = KER_MAXK;
   } else if (p->fmt == FMT_CSR) {
     if (p->opt_kernel != KER_AUTO) return fail(SBO_EINVAL, "CSR problems use the CSR kernel only");
@@ -1225,6 +1233,7 @@ sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const f
   a.GY = GY_dev;
   a.gout = gout_dev;
   a.err = p->err;
+  a.gkind = p->opt_g;
   if (L_dev) SBO_CUDA(cudaMemsetAsync(L_dev, 0, sizeof(float) * B, s));
   cudaError_t e;
   if (p->fmt == FMT_CSR) {
@@ -1293,10 +1302,12 @@ sbo_status sbo_dual_bound(sbo_problem* p, double ybar, double alpha, int64_t ite
   prm.delta = 0.0;
   prm.grad_tol = 0.0;
   prm.seed = 0;
-  const int saved_dual = p->opt_dual;
+  const int saved_dual = p->opt_dual, saved_g = p->opt_g;
   p->opt_dual = 0;
+  p->opt_g = G_QUAD;   // the bound below is formed for the quadratic g
   sbo_status st = sbo_gda_start(p, &prm, nullptr);
   p->opt_dual = saved_dual;
+  p->opt_g = saved_g;
   if (st != SBO_OK) return st;
   if (iters > 0 && (st = sbo_gda_run(p, iters)) != SBO_OK) return st;
   if ((st = sbo_sync(p)) != SBO_OK) return st;
@@ -1387,6 +1398,7 @@ bool dense_view(sbo_problem* p, DenseView* v) {
   v->cp64 = p->cp64;
   v->err = p->err;
   v->timeout_ns = timeout_ns(p);
+  v->gkind = p->opt_g;
   v->sms = p->sms;
   v->launches = &p->launches;
   return true;

@@ -10,6 +10,13 @@ namespace sbo {
 // Device error word bits (written with atomicOr, read and cleared by sbo_sync).
 enum : uint32_t { ERR_TIMEOUT = 1u, ERR_BOUNDS = 2u };
 
+// Constraint function g of the Lagrangian (section 3.1): the quadratic x^2 - x (the default) or
+// the entropy x log x + (1 - x) log(1 - x) named among the paper's choices.
+enum GKind : int { G_QUAD = 0, G_ENTROPY = 1 };
+// The entropy's derivative log(x / (1 - x)) is unbounded at 0 and 1: it is taken at x clamped to
+// [G_ENT_EPS, 1 - G_ENT_EPS] (g itself is continuous there, with g(0) = g(1) = 0).
+constexpr float G_ENT_EPS = 1e-6f;
+
 // Epilogue modes shared by the contraction kernels.
 enum EpiMode : int { EPI_UPDATE = 0, EPI_EVAL = 1, EPI_LAGR = 2 };
 
@@ -45,7 +52,25 @@ struct EpiArgs {
   const float* mu;
   float* gpart;
   int64_t gpart_ld;
+  int gkind;               // constraint function g (GKind)
 };
+
+__device__ __forceinline__ float g_val(float x, int kind) {
+  if (kind == G_QUAD) return x * x - x;
+  const float a = x > 0.0f ? x * logf(x) : 0.0f;
+  const float b = x < 1.0f ? (1.0f - x) * log1pf(-x) : 0.0f;
+  return a + b;
+}
+// log(x / (1 - x)) at x clamped to [eps, 1 - eps], formed from u = min(x, 1 - x) clamped to
+// [eps, 1/2] (1 - x is exact in FP32 for x >= 1/2, so the clamp near 1 loses nothing to 1 - eps
+// being unrepresentable) and g'(x) = -g'(1 - x).
+__device__ __forceinline__ float g_der(float x, int kind) {
+  if (kind == G_QUAD) return 2.0f * x - 1.0f;
+  const bool upper = x > 0.5f;
+  const float u = fmaxf(upper ? 1.0f - x : x, G_ENT_EPS);
+  const float v = logf(u) - log1pf(-u);
+  return upper ? -v : v;
+}
 
 // Sum of v[j] over the 32 lanes of a warp for each j = 0..31 at once (31 shuffles): lane l
 // returns the sum of v[l].  Step k halves the values a lane holds: the lane keeps the half
@@ -74,8 +99,9 @@ __device__ __forceinline__ void op_store(void* p, int64_t idx, float v, int type
   else static_cast<__nv_bfloat16*>(p)[idx] = __float2bfloat16_rn(v);
 }
 
-// One coordinate of Algorithm 1.  d is dL/dx at (x, y); returns x^{t+1}, writes y^{t+1}.
-__device__ __forceinline__ float pdbo_update(float x, float y, float d, float alpha, float beta,
+// One coordinate of Algorithm 1.  d is dL/dx at (x, y) and gx = g(x); returns x^{t+1}, writes
+// y^{t+1} = y + beta g(x).
+__device__ __forceinline__ float pdbo_update(float x, float y, float d, float gx, float alpha, float beta,
                                              float delta, float grad_tol, float* y_next) {
   const bool stagnating = fabsf(x - 0.5f) <= delta && fabsf(d) <= grad_tol && y <= 0.0f;
   float xn;
@@ -84,7 +110,7 @@ __device__ __forceinline__ float pdbo_update(float x, float y, float d, float al
   } else {
     xn = fminf(fmaxf(x - alpha * d, 0.0f), 1.0f);
   }
-  *y_next = y + beta * (x * x - x);
+  *y_next = y + beta * gx;
   return xn;
 }
 

@@ -166,14 +166,15 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const float x = comp(xo[v], k), y = comp(yo[v], k);
-          const float d = comp(acc[v], k) + cpi + y * (2.0f * x - 1.0f);
+          const float gx = g_val(x, a.gkind);
+          const float d = comp(acc[v], k) + cpi + y * g_der(x, a.gkind);
           float yn;
-          const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+          const float xn = pdbo_update(x, y, d, gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
           const bool live = r0 + k < B;   // padding restarts keep their zeros
           set_comp(xn4, k, live ? xn : 0.0f);
           set_comp(yn4, k, live ? yn : 0.0f);
           set_comp(b4, k, (live && xn > 0.5f) ? 1.0f : 0.0f);
-          set_comp(gs[v], k, comp(gs[v], k) + (live ? x * x - x : 0.0f));
+          set_comp(gs[v], k, comp(gs[v], k) + (live ? gx : 0.0f));
         }
         if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = xn4;
         store4<OPT>(a.Xout, idx, xn4);
@@ -191,9 +192,9 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
           const int64_t r = r0 + k;
           if (r >= B) continue;
           const float x = comp(xo[v], k), y = comp(yo[v], k), g = comp(acc[v], k);
-          const float gx = x * x - x;
+          const float gx = g_val(x, a.gkind);
           const float sc = a.gout ? a.gout[r] : 1.0f;
-          if (a.GX) a.GX[r * n + i] = sc * (g + cpi + y * (2.0f * x - 1.0f));
+          if (a.GX) a.GX[r * n + i] = sc * (g + cpi + y * g_der(x, a.gkind));
           if (a.GY) a.GY[r * n + i] = sc * gx;
           set_comp(gs[v], k, comp(gs[v], k) + 0.5f * x * g + cpi * x + y * gx);
         }

@@ -107,12 +107,13 @@ __global__ void __launch_bounds__(256) k_simt(const float* __restrict__ A, int64
       if (MODE == EPI_UPDATE) {
         const float x = a.Xm ? a.Xm[idx] : static_cast<const float*>(a.Xin)[idx];
         const float y = a.mu ? a.mu[r] : a.Y[idx];   // single-constraint form: the restart's dual
-        const float d = g + a.cp[i] + y * (2.0f * x - 1.0f);
+        const float gx = g_val(x, a.gkind);
+        const float d = g + a.cp[i] + y * g_der(x, a.gkind);
         float yn;
-        const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+        const float xn = pdbo_update(x, y, d, gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
         if (a.Xm) a.Xm[idx] = xn;
         static_cast<float*>(a.Xout)[idx] = xn;
-        if (a.mu) gsum += x * x - x;
+        if (a.mu) gsum += gx;
         else a.Y[idx] = yn;
         if (a.bits_out) static_cast<float*>(a.bits_out)[idx] = xn > 0.5f ? 1.0f : 0.0f;
       } else if (MODE == EPI_EVAL) {
@@ -120,9 +121,9 @@ __global__ void __launch_bounds__(256) k_simt(const float* __restrict__ A, int64
         if (b != 0.0f) f2 += (long long)g + 2 * (long long)a.cp64[i];
       } else {
         const float x = a.Xl[idx], y = a.Yl[idx];
-        const float gx = x * x - x;
+        const float gx = g_val(x, a.gkind);
         const float sc = a.gout ? a.gout[r] : 1.0f;
-        if (a.GX) a.GX[idx] = sc * (g + a.cp[i] + y * (2.0f * x - 1.0f));
+        if (a.GX) a.GX[idx] = sc * (g + a.cp[i] + y * g_der(x, a.gkind));
         if (a.GY) a.GY[idx] = sc * gx;
         lsum += 0.5f * x * g + a.cp[i] * x + y * gx;
       }

@@ -46,8 +46,8 @@ __global__ void __launch_bounds__(1024) k_tiny(TinyArgs a) {
       const float* xr = xs + rr * n;
       const float* Ai = As + i * n;
       for (int k = 0; k < n; ++k) g = fmaf(Ai[k], xr[k], g);
-      const float d = g + cps[i] + y * (2.0f * x - 1.0f);
-      xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+      const float d = g + cps[i] + y * g_der(x, a.gkind);
+      xn = pdbo_update(x, y, d, g_val(x, a.gkind), a.alpha, a.beta, a.delta, a.grad_tol, &yn);
     }
     __syncthreads();
     if (active) xs[rr * n + i] = xn;

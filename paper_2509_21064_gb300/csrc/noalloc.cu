@@ -77,6 +77,7 @@ extern "C" sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const fl
   a.ld = v.n;
   a.cp = v.cp;
   a.cp64 = v.cp64;
+  a.gkind = v.gkind;
   a.Xl = X_dev;
   a.Yl = Y_dev;
   a.L = L_dev;

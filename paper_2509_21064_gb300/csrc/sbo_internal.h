@@ -39,6 +39,7 @@ cudaError_t launch_simt(const float* A, int64_t lda, const EpiArgs& a, int mode,
 // k_tiny.cu  (whole run in one launch for n <= 64)
 struct TinyArgs {
   int n, B;
+  int gkind;               // constraint function g (GKind)
   int64_t ld;
   const float* A;          // FP32 [n][lda]
   int64_t lda;
@@ -147,6 +148,7 @@ struct DenseView {
   const int64_t* cp64;
   uint32_t* err;
   uint64_t timeout_ns;
+  int gkind;
   int sms;
   int64_t* launches;
 };

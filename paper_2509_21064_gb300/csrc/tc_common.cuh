@@ -150,14 +150,15 @@ __device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_
       if (row_ok && r < a.B) {
         const int64_t idx = r * a.ld + i;
         const float x = u[j], y = v[j];
-        const float d = g[j] + cpi + y * (2.0f * x - 1.0f);
+        const float gx = g_val(x, a.gkind);
+        const float d = g[j] + cpi + y * g_der(x, a.gkind);
         float yn;
-        const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+        const float xn = pdbo_update(x, y, d, gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
         a.Xm[idx] = xn;
         static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);
         if (a.bits_out)
           static_cast<__nv_bfloat16*>(a.bits_out)[idx] = __float2bfloat16_rn(xn > 0.5f ? 1.0f : 0.0f);
-        gv[j] = x * x - x;
+        gv[j] = gx;
       }
     }
     const float sum = warp_transpose_sum32(gv, lane);
@@ -170,9 +171,9 @@ __device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_
         if (r < a.B) {
           const int64_t idx = r * a.ld + i;
           const float x = u[j], y = v[j];
-          const float d = g[j] + cpi + y * (2.0f * x - 1.0f);
+          const float d = g[j] + cpi + y * g_der(x, a.gkind);
           float yn;
-          const float xn = pdbo_update(x, y, d, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+          const float xn = pdbo_update(x, y, d, g_val(x, a.gkind), a.alpha, a.beta, a.delta, a.grad_tol, &yn);
           a.Xm[idx] = xn;
           a.Y[idx] = yn;
           static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);
@@ -198,9 +199,9 @@ __device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_
       if (row_ok && r < a.B) {
         const int64_t idx = r * a.ld + i;
         const float x = u[j], y = v[j];
-        const float gx = x * x - x;
+        const float gx = g_val(x, a.gkind);
         const float sc = a.gout ? a.gout[r] : 1.0f;
-        if (a.GX) a.GX[idx] = sc * (g[j] + cpi + y * (2.0f * x - 1.0f));
+        if (a.GX) a.GX[idx] = sc * (g[j] + cpi + y * g_der(x, a.gkind));
         if (a.GY) a.GY[idx] = sc * gx;
         lv = 0.5f * x * g[j] + cpi * x + y * gx;
       }

@@ -20,7 +20,8 @@ STATUS_NAMES = ["SBO_OK", "SBO_EINVAL", "SBO_ENOMEM", "SBO_ECUDA", "SBO_ETIMEOUT
                 "SBO_ERANGE", "SBO_EDEVICE"]
 SBO_FP32, SBO_BF16, SBO_FP8_E4M3 = 0, 1, 2
 SBO_OPT_KERNEL, SBO_OPT_USE_GRAPH, SBO_OPT_TILE_N, SBO_OPT_TIMEOUT_US, SBO_OPT_SPLIT_K, SBO_OPT_AUTOTUNE, \
-    SBO_OPT_PDL, SBO_OPT_DUAL = 1, 2, 3, 4, 5, 6, 7, 8
+    SBO_OPT_PDL, SBO_OPT_DUAL, SBO_OPT_G = 1, 2, 3, 4, 5, 6, 7, 8, 9
+G_QUADRATIC, G_ENTROPY = 0, 1
 DUAL_COORDINATE, DUAL_SINGLE = 0, 1
 KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR, KERNEL_MAXK = 0, 1, 2, 3, 4, 5
 

@@ -1,0 +1,148 @@
+"""The entropy constraint function (SBO_OPT_G = 1) on every kernel against the FP64 oracle, in the
+quadratic g's branch-free window (y stays positive over the first 50 iterations: it falls by at
+most beta ln 2 per step) and tolerances (see _check for the BF16 operand), and the Lagrangian
+entry point."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from paper_2509_21064_gb300 import sbo as S
+from paper_2509_21064_gb300.build import build as build_lib
+from _helpers import gpu_trajectory, normwise, to_gda_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib()
+    S.lib()
+
+
+def _bf16(x):
+    """Round to the nearest BF16 value (ties to even), as the tensor-core and BF16 sparse paths
+    round the contraction operand x."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _oracle_traj(A, cp, p, steps, operand_bf16=False):
+    """FP64 oracle trajectory with the entropy g; with operand_bf16 the contraction A x takes x
+    rounded to BF16 (the operand the BF16 paths compute with) and everything else stays FP64."""
+    X, _ = O.init_state(A.shape[0], p.restarts, p.seed, p.ybar)
+    Y = np.full_like(X, p.ybar)
+    xs, ys = [X], [Y]
+    for _ in range(steps):
+        if operand_bf16:
+            D = np.asarray((A @ _bf16(X).T).T) + cp[None, :] + Y * O.g_entropy_prime(X)
+            stag = (np.abs(X - 0.5) <= p.delta) & (np.abs(D) <= p.grad_tol) & (Y <= 0.0)
+            Xn = np.where(stag, np.where(X <= 0.5, 0.5 - p.delta, 0.5 + p.delta),
+                          np.clip(X - p.alpha * D, 0.0, 1.0))
+            Y = Y + p.beta * O.g_entropy(X)
+            X = Xn
+        else:
+            X, Y, _ = O.gda_step(A, cp, X, Y, p.alpha, p.beta, p.delta, p.grad_tol, "entropy")
+        xs.append(X)
+        ys.append(Y)
+    return np.array(xs), np.array(ys)
+
+
+def _check(gx, gy, A, cp, p, tol, prec):
+    """FP32 operands: every restart and iteration within tol of the FP64 oracle (1e-4: FP32
+    rounding, ~6e-8, times the amplification near the ends of the box described next, which stays
+    below 10^3 in these cases; the quadratic g needs only 1e-5).  BF16 operands:
+    near the ends of the box the entropy's derivative (slope 1/x) amplifies the operand's rounding
+    -- the FP64 oracle fed the same BF16 operand deviates from the plain one by up to ~6e-2 for a
+    few iterations -- so the GPU is held to 2e-3 of that BF16-operand oracle throughout, and to tol
+    of the plain oracle for 99 % of (iteration, restart) pairs."""
+    ox, oy = _oracle_traj(A, cp, p, len(gx) - 1)
+    ex, ey = normwise(gx, ox), normwise(gy, oy)
+    if prec == S.SBO_FP32:
+        assert ex.max() <= tol and ey.max() <= tol, (ex.max(), ey.max())
+        return
+    bx, by = _oracle_traj(A, cp, p, len(gx) - 1, operand_bf16=True)
+    assert normwise(gx, bx).max() <= 2e-3 and normwise(gy, by).max() <= 2e-3
+    assert np.quantile(ex, 0.99) <= tol and np.quantile(ey, 0.99) <= tol
+
+
+@pytest.mark.parametrize("n,B,prec,kernel,tile,tol", [
+    (40, 33, S.SBO_FP32, S.KERNEL_TINY, 0, 1e-4),
+    (300, 70, S.SBO_FP32, S.KERNEL_SIMT, 0, 1e-4),
+    (333, 129, S.SBO_BF16, S.KERNEL_TC, 128, 2e-2),
+    (600, 300, S.SBO_BF16, S.KERNEL_TC, 512, 2e-2),
+    (1000, 256, S.SBO_BF16, S.KERNEL_TC, 1256, 2e-2),
+])
+def test_entropy_dense_parity(n, B, prec, kernel, tile, tol):
+    Q, c = W.dense_qubo(n, seed=n + 5)
+    p = W.dense_params(Q, restarts=B, iters=200, eval_every=10, seed=4)
+    prm = to_gda_params(p)
+    with S.Problem.dense(Q, c, precision=prec) as P:
+        P.set_option(S.SBO_OPT_KERNEL, kernel)
+        if tile:
+            P.set_option(S.SBO_OPT_TILE_N, tile)
+        P.set_option(S.SBO_OPT_G, S.G_ENTROPY)
+        gx, gy = gpu_trajectory(P, prm, 50)
+        A, cp = O.canonicalize(Q, c)
+        _check(gx, gy, A, cp, p, tol, prec)
+        P.start(prm)
+        P.run(50)
+        X, Y = P.state()
+        assert np.array_equal(X, gx[50]) and np.array_equal(Y, gy[50])
+
+
+@pytest.mark.parametrize("prec,tol", [(S.SBO_FP32, 1e-4), (S.SBO_BF16, 2e-2)])
+def test_entropy_csr_parity(prec, tol):
+    n = 2000
+    i, j, w = W.maxcut_er(n, 6.0, seed=11)
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    p = W.graph_params("maxcut", restarts=200, iters=200, eval_every=10, seed=6)
+    with S.Problem.csr(n, rowptr, col, val, c, precision=prec) as P:
+        P.set_option(S.SBO_OPT_G, S.G_ENTROPY)
+        gx, gy = gpu_trajectory(P, to_gda_params(p), 50)
+        A, cp = O.canonicalize_csr(n, rowptr, col, val, c)
+        _check(gx, gy, A, cp, p, tol, prec)
+
+
+@pytest.mark.parametrize("fmt", ["dense32", "dense16", "csr"])
+def test_entropy_lagrangian(fmt):
+    """x on a 1/256 grid including 0 and 1 (where g = 0 and the clamped derivative applies)."""
+    import torch
+    rng = np.random.default_rng(4)
+    if fmt == "csr":
+        n = 1500
+        i, j, w = W.maxcut_er(n, 6.0, seed=3)
+        rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+        A, cp = O.canonicalize_csr(n, rowptr, col, val, c)
+        make = lambda: S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32)
+    else:
+        n = 700
+        Q, c = W.dense_qubo(n, seed=2)
+        A, cp = O.canonicalize(Q, c)
+        make = lambda: S.Problem.dense(Q, c, precision=S.SBO_FP32 if fmt == "dense32" else S.SBO_BF16)
+    B = 20
+    X = rng.integers(0, 257, size=(B, n)) / 256.0
+    Y = rng.normal(scale=10.0, size=(B, n)).astype(np.float32).astype(np.float64)
+    L_o, GX_o, GY_o = O.lagrangian(A, cp, X, Y, "entropy")
+    with make() as P:
+        P.set_option(S.SBO_OPT_G, S.G_ENTROPY)
+        Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+        Yt = torch.tensor(Y, dtype=torch.float32, device="cuda")
+        L = torch.empty(B, device="cuda")
+        GX = torch.empty_like(Xt)
+        GY = torch.empty_like(Xt)
+        S.sbo_lagrangian(P.h, B, Xt.data_ptr(), Yt.data_ptr(), None, L.data_ptr(), GX.data_ptr(), GY.data_ptr(),
+                         torch.cuda.current_stream())
+        torch.cuda.synchronize()
+    assert normwise(GX.cpu().numpy(), GX_o).max() <= 1e-5
+    assert normwise(GY.cpu().numpy(), GY_o).max() <= 1e-6
+    assert np.max(np.abs(L.cpu().numpy() - L_o)) / np.max(np.abs(L_o)) <= 1e-5
+
+
+def test_entropy_is_refused_by_max_k_cut():
+    i, j, w = W.maxcut_torus(6, 6, seed=0)
+    with S.Problem.maxkcut(36, i, j, w, 3) as P:
+        P.set_option(S.SBO_OPT_G, S.G_ENTROPY)
+        with pytest.raises(S.SboError):
+            P.start(S.params(restarts=4, iters=10, alpha=0.01, beta=0.01, ybar=6.0))
