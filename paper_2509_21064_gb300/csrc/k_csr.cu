@@ -49,7 +49,9 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float s) {
   if (k == 0) v.x = s; else if (k == 1) v.y = s; else if (k == 2) v.z = s; else v.w = s;
 }
 
-template <int MODE, int NV, int OPT>
+// GK: constraint function g; SINGLE: one dual per restart (both uniform per launch, so each
+// combination is its own instantiation and the per-element code carries no test of them).
+template <int MODE, int NV, int OPT, int GK, bool SINGLE>
 __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                              const void* __restrict__ val, int vt, EpiArgs a) {
   const int lane = threadIdx.x & 31;
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
         const int64_t idx = i * ld + r0;
         if (MODE == EPI_UPDATE) {
           xo[v] = a.Xm ? *reinterpret_cast<const float4*>(a.Xm + idx) : load4<OP_F32>(Xin, idx);
-          yo[v] = a.mu ? *reinterpret_cast<const float4*>(a.mu + r0)    // the restarts' duals
+          yo[v] = SINGLE ? *reinterpret_cast<const float4*>(a.mu + r0)    // the restarts' duals
                        : *reinterpret_cast<const float4*>(a.Y + idx);
         } else if (MODE == EPI_EVAL) {
           xo[v] = load4<OPT>(Xin, idx);   // EPI_EVAL: the row's own bits
@@ -166,19 +168,19 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const float x = comp(xo[v], k), y = comp(yo[v], k);
-          const float gx = g_val(x, a.gkind);
-          const float d = comp(acc[v], k) + cpi + y * g_der(x, a.gkind);
+          const float gx = g_val(x, GK);
+          const float d = comp(acc[v], k) + cpi + y * g_der(x, GK);
           float yn;
           const float xn = pdbo_update(x, y, d, gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
           const bool live = r0 + k < B;   // padding restarts keep their zeros
           set_comp(xn4, k, live ? xn : 0.0f);
           set_comp(yn4, k, live ? yn : 0.0f);
           set_comp(b4, k, (live && xn > 0.5f) ? 1.0f : 0.0f);
-          set_comp(gs[v], k, comp(gs[v], k) + (live ? gx : 0.0f));
+          if (SINGLE) set_comp(gs[v], k, comp(gs[v], k) + (live ? gx : 0.0f));
         }
         if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = xn4;
         store4<OPT>(a.Xout, idx, xn4);
-        if (!a.mu) *reinterpret_cast<float4*>(a.Y + idx) = yn4;
+        if (!SINGLE) *reinterpret_cast<float4*>(a.Y + idx) = yn4;
         if (a.bits_out) store4<OPT>(a.bits_out, idx, b4);
       } else if (MODE == EPI_EVAL) {
 #pragma unroll
@@ -192,16 +194,16 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
           const int64_t r = r0 + k;
           if (r >= B) continue;
           const float x = comp(xo[v], k), y = comp(yo[v], k), g = comp(acc[v], k);
-          const float gx = g_val(x, a.gkind);
+          const float gx = g_val(x, GK);
           const float sc = a.gout ? a.gout[r] : 1.0f;
-          if (a.GX) a.GX[r * n + i] = sc * (g + cpi + y * g_der(x, a.gkind));
+          if (a.GX) a.GX[r * n + i] = sc * (g + cpi + y * g_der(x, GK));
           if (a.GY) a.GY[r * n + i] = sc * gx;
           set_comp(gs[v], k, comp(gs[v], k) + 0.5f * x * g + cpi * x + y * gx);
         }
       }
     }
   }
-  if ((MODE == EPI_UPDATE && a.mu) || (MODE == EPI_LAGR && a.L)) {
+  if ((MODE == EPI_UPDATE && SINGLE) || (MODE == EPI_LAGR && a.L)) {
     // single-constraint form: the block's warps cover the same restarts; their sums of g go to
     // shared memory and are added in warp order into this block's row of partial sums.
     // Lagrangian: the same per-block sums of the rows' shares of L, added to L[r] atomically
@@ -269,8 +271,17 @@ static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const
   attr.val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = pdl ? 1 : 0;
-  if (NV == 1) return cudaLaunchKernelEx(&cfg, k_csr<MODE, 1, OPT>, rowptr, col, val, vt, a);
-  return cudaLaunchKernelEx(&cfg, k_csr<MODE, 2, OPT>, rowptr, col, val, vt, a);
+  const bool single = MODE == EPI_UPDATE && a.mu != nullptr;
+  const bool ent = MODE != EPI_EVAL && a.gkind == G_ENTROPY;
+#define SBO_CSR_LAUNCH(NVV)                                                                           \
+  if (single)                                                                                          \
+    return ent ? cudaLaunchKernelEx(&cfg, k_csr<MODE, NVV, OPT, G_ENTROPY, true>, rowptr, col, val, vt, a)    \
+               : cudaLaunchKernelEx(&cfg, k_csr<MODE, NVV, OPT, G_QUAD, true>, rowptr, col, val, vt, a);      \
+  return ent ? cudaLaunchKernelEx(&cfg, k_csr<MODE, NVV, OPT, G_ENTROPY, false>, rowptr, col, val, vt, a)      \
+             : cudaLaunchKernelEx(&cfg, k_csr<MODE, NVV, OPT, G_QUAD, false>, rowptr, col, val, vt, a);
+  if (NV == 1) { SBO_CSR_LAUNCH(1) }
+  SBO_CSR_LAUNCH(2)
+#undef SBO_CSR_LAUNCH
 }
 
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,

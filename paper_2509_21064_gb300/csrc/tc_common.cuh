@@ -134,14 +134,15 @@ __device__ __forceinline__ void epi_load(const EpiArgs& a, int64_t i, bool row_o
   }
 }
 
-// One chunk of the epilogue given the accumulator values g (= (A x_r)_i for 32 restarts r).  In
-// the single-constraint form (a.mu set) the warp's 32 rows also add up g(x^t) per restart into
-// row `prow` of the partial sums.
-template <int MODE>
-__device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_ok, float cpi, long long cp2,
-                                          int64_t rbase, int lane, const float (&g)[32], const float (&u)[32],
-                                          const float (&v)[32], int prow = 0) {
-  if (MODE == EPI_UPDATE && a.mu) {
+// One chunk of the PDBO update for a compile-time constraint function GK, with one dual per
+// coordinate (SINGLE false) or per restart (SINGLE true: the warp's 32 rows also add up g(x^t) per
+// restart into row `prow` of the partial sums).  The kind and the form are uniform per launch, so
+// epi_apply picks one specialisation per chunk instead of testing them per element.
+template <int GK, bool SINGLE>
+__device__ __forceinline__ void epi_update(const EpiArgs& a, int64_t i, bool row_ok, float cpi, int64_t rbase,
+                                           int lane, const float (&g)[32], const float (&u)[32], const float (&v)[32],
+                                           int prow) {
+  if (SINGLE) {
     float gv[32];
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -150,8 +151,8 @@ __device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_
       if (row_ok && r < a.B) {
         const int64_t idx = r * a.ld + i;
         const float x = u[j], y = v[j];
-        const float gx = g_val(x, a.gkind);
-        const float d = g[j] + cpi + y * g_der(x, a.gkind);
+        const float gx = g_val(x, GK);
+        const float d = g[j] + cpi + y * g_der(x, GK);
         float yn;
         const float xn = pdbo_update(x, y, d, gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
         a.Xm[idx] = xn;
@@ -163,24 +164,40 @@ __device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_
     }
     const float sum = warp_transpose_sum32(gv, lane);
     if (rbase + lane < a.B) a.gpart[(int64_t)prow * a.gpart_ld + rbase + lane] = sum;
-  } else if (MODE == EPI_UPDATE) {
-    if (row_ok) {
+  } else if (row_ok) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int64_t r = rbase + j;
-        if (r < a.B) {
-          const int64_t idx = r * a.ld + i;
-          const float x = u[j], y = v[j];
-          const float d = g[j] + cpi + y * g_der(x, a.gkind);
-          float yn;
-          const float xn = pdbo_update(x, y, d, g_val(x, a.gkind), a.alpha, a.beta, a.delta, a.grad_tol, &yn);
-          a.Xm[idx] = xn;
-          a.Y[idx] = yn;
-          static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);
-          if (a.bits_out)
-            static_cast<__nv_bfloat16*>(a.bits_out)[idx] = __float2bfloat16_rn(xn > 0.5f ? 1.0f : 0.0f);
-        }
+    for (int j = 0; j < 32; ++j) {
+      const int64_t r = rbase + j;
+      if (r < a.B) {
+        const int64_t idx = r * a.ld + i;
+        const float x = u[j], y = v[j];
+        const float d = g[j] + cpi + y * g_der(x, GK);
+        float yn;
+        const float xn = pdbo_update(x, y, d, g_val(x, GK), a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+        a.Xm[idx] = xn;
+        a.Y[idx] = yn;
+        static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);
+        if (a.bits_out)
+          static_cast<__nv_bfloat16*>(a.bits_out)[idx] = __float2bfloat16_rn(xn > 0.5f ? 1.0f : 0.0f);
       }
+    }
+  }
+}
+
+// One chunk of the epilogue given the accumulator values g (= (A x_r)_i for 32 restarts r).  In
+// the single-constraint form (a.mu set) the warp's 32 rows also add up g(x^t) per restart into
+// row `prow` of the partial sums.
+template <int MODE>
+__device__ __forceinline__ void epi_apply(const EpiArgs& a, int64_t i, bool row_ok, float cpi, long long cp2,
+                                          int64_t rbase, int lane, const float (&g)[32], const float (&u)[32],
+                                          const float (&v)[32], int prow = 0) {
+  if (MODE == EPI_UPDATE) {
+    if (a.gkind == G_ENTROPY) {
+      if (a.mu) epi_update<G_ENTROPY, true>(a, i, row_ok, cpi, rbase, lane, g, u, v, prow);
+      else epi_update<G_ENTROPY, false>(a, i, row_ok, cpi, rbase, lane, g, u, v, prow);
+    } else {
+      if (a.mu) epi_update<G_QUAD, true>(a, i, row_ok, cpi, rbase, lane, g, u, v, prow);
+      else epi_update<G_QUAD, false>(a, i, row_ok, cpi, rbase, lane, g, u, v, prow);
     }
   } else if (MODE == EPI_EVAL) {
 #pragma unroll
