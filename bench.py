@@ -45,7 +45,7 @@ METRIC = "GDA restart-iterations/s at n=20k dense QUBO"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # DRAM bytes (read + write) per launch of the update kernel from one ncu capture of this
 # workload (profiles/k_tc_pair_update_dense_n20000.md); keyed by (tile width, n, restarts)
-MEASURED_TRAFFIC = {(512, 20000, 1024): 1.169377e9 + 0.1809856e9}
+MEASURED_TRAFFIC = {(512, 20000, 1024): 1.169179e9 + 0.180734e9}
 
 
 def peaks():
