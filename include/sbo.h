@@ -82,6 +82,11 @@ typedef struct sbo_gda_params {
 sbo_status sbo_create_dense(int64_t n, const int32_t* Q, const int32_t* c, int32_t precision,
                             void* stream, sbo_problem** out);
 
+/* sbo_create_dense_i8: the same problem from an int8 Q (entries in [-128, 127]; c as above):
+ * a quarter of the bytes to copy to the device, the same canonical form and checks. */
+sbo_status sbo_create_dense_i8(int64_t n, const int8_t* Q, const int32_t* c, int32_t precision, void* stream,
+                               sbo_problem** out);
+
 /* sbo_create_csr: Q in CSR on the host: rowptr[n+1] (int64, rowptr[0]=0, non-decreasing,
  * rowptr[n]=nnz), col[nnz] (int32 in [0,n)), val[nnz] (int32); duplicates are summed.
  * c as above.  precision: SBO_FP32, SBO_BF16 or SBO_FP8_E4M3 (weight storage).  A = Q + Q^T

@@ -548,8 +548,9 @@ extern "C" {
 const char* sbo_last_error(void) { return g_last_error.c_str(); }
 const char* sbo_version(void) { return "sbo 0.1 (sm_103a)"; }
 
-sbo_status sbo_create_dense(int64_t n, const int32_t* Q, const int32_t* c, int32_t precision, void* stream,
-                            sbo_problem** out) {
+// Dense set-up shared by the int32 and int8 entry points (q_bytes: size of one entry of Q).
+static sbo_status create_dense_impl(int64_t n, const void* Q, int q_bytes, const int32_t* c, int32_t precision,
+                                    void* stream, sbo_problem** out) {
   g_last_error.clear();
   if (!out) return fail(SBO_EINVAL, "out is NULL");
   *out = nullptr;
@@ -566,28 +567,33 @@ sbo_status sbo_create_dense(int64_t n, const int32_t* Q, const int32_t* c, int32
   p->prec = precision;
   p->a_type = precision == SBO_FP32 ? OP_F32 : OP_BF16;
   p->lda = round_up(n, 8);
-  int32_t *Qd = nullptr, *cd = nullptr;
+  void* Qd = nullptr;
+  int32_t* cd = nullptr;
   unsigned long long* rowsum = nullptr;
   uint32_t* rerr = nullptr;
   cudaStream_t s = p->stream;
-  auto cleanup_tmp = [&]() { dfree(Qd, s); dfree(cd, s); dfree(rowsum, s); dfree(rerr, s); };
+  auto cleanup_tmp = [&]() {
+    if (Qd) cudaFreeAsync(Qd, s);
+    Qd = nullptr;
+    dfree(cd, s); dfree(rowsum, s); dfree(rerr, s);
+  };
   auto bail = [&](sbo_status s) { cleanup_tmp(); free_all(p); delete p; return s; };
   cudaError_t e;
   const size_t a_elt = p->a_type == OP_F32 ? 4 : 2;
   configure_pool_once();
   if ((e = cudaMallocAsync(&p->A, (size_t)n * p->lda * a_elt, s)) != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc A"));
   if ((e = dalloc(&p->cp, n, s)) != cudaSuccess || (e = dalloc(&p->cp64, n, s)) != cudaSuccess ||
-      (e = dalloc(&Qd, (size_t)n * n, s)) != cudaSuccess || (e = dalloc(&rowsum, n, s)) != cudaSuccess ||
+      (e = cudaMallocAsync(&Qd, (size_t)n * n * q_bytes, s)) != cudaSuccess || (e = dalloc(&rowsum, n, s)) != cudaSuccess ||
       (e = dalloc(&rerr, 1, s)) != cudaSuccess || (c && (e = dalloc(&cd, n, s)) != cudaSuccess))
     return bail(e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation failed") : cuda_fail(e, "cudaMalloc"));
-  if ((e = cudaMemcpyAsync(Qd, Q, sizeof(int32_t) * n * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(Qd, Q, (size_t)q_bytes * n * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return bail(cuda_fail(e, "copy Q"));
   if (c && (e = cudaMemcpyAsync(cd, c, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return bail(cuda_fail(e, "copy c"));
   cudaMemsetAsync(rowsum, 0, sizeof(unsigned long long) * n, s);
   cudaMemsetAsync(rerr, 0, sizeof(uint32_t), s);
   const int64_t limit = p->a_type == OP_F32 ? (1ll << 24) : 256;
-  if ((e = launch_canon_dense(Qd, cd, n, p->A, p->lda, p->a_type, p->cp, p->cp64, rowsum, rerr, limit, s)) !=
+  if ((e = launch_canon_dense(Qd, q_bytes, cd, n, p->A, p->lda, p->a_type, p->cp, p->cp64, rowsum, rerr, limit, s)) !=
       cudaSuccess)
     return bail(cuda_fail(e, "canonicalisation launch"));
   if ((e = launch_rowsum_check(rowsum, p->cp64, n, rerr, s)) != cudaSuccess) return bail(cuda_fail(e, "row-sum check"));
@@ -606,6 +612,16 @@ sbo_status sbo_create_dense(int64_t n, const int32_t* Q, const int32_t* c, int32
   if (flags & 4u) { free_all(p); delete p; return fail(SBO_ERANGE, "c_i + Q_ii outside the int32 range"); }
   *out = p;
   return SBO_OK;
+}
+
+sbo_status sbo_create_dense(int64_t n, const int32_t* Q, const int32_t* c, int32_t precision, void* stream,
+                            sbo_problem** out) {
+  return create_dense_impl(n, Q, 4, c, precision, stream, out);
+}
+
+sbo_status sbo_create_dense_i8(int64_t n, const int8_t* Q, const int32_t* c, int32_t precision, void* stream,
+                               sbo_problem** out) {
+  return create_dense_impl(n, Q, 1, c, precision, stream, out);
 }
 
 sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const int32_t* val,

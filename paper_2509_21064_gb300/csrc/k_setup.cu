@@ -11,7 +11,8 @@ namespace sbo {
 // block; entries whose magnitude exceeds a_limit (not exact in the storage type) raise a flag.
 constexpr int CANON_TJ = 16;
 
-__global__ void __launch_bounds__(256) k_canon_dense(const int32_t* __restrict__ Q, int64_t n, void* A,
+template <typename TQ>   // int32_t or int8_t entries of Q
+__global__ void __launch_bounds__(256) k_canon_dense(const TQ* __restrict__ Q, int64_t n, void* A,
                                                      int64_t lda, int a_type, unsigned long long* rowsum,
                                                      uint32_t* range_err, int64_t a_limit) {
   __shared__ int32_t tT[32][33];
@@ -55,7 +56,8 @@ __global__ void __launch_bounds__(256) k_canon_dense(const int32_t* __restrict__
 }
 
 // c'_i = c_i + Q_ii, exact in int64, and its FP32 value.
-__global__ void k_canon_linear(const int32_t* __restrict__ Q, const int32_t* __restrict__ c, int64_t n,
+template <typename TQ>
+__global__ void k_canon_linear(const TQ* __restrict__ Q, const int32_t* __restrict__ c, int64_t n,
                                float* cp, int64_t* cp64) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -73,16 +75,25 @@ __global__ void k_rowsum_check(const unsigned long long* rowsum, const int64_t* 
   if (c >= (1ll << 31) || c <= -(1ll << 31)) atomicOr(range_err, 4u);
 }
 
-cudaError_t launch_canon_dense(const int32_t* Qd, const int32_t* cd, int64_t n, void* A, int64_t lda,
+cudaError_t launch_canon_dense(const void* Qd, int q_bytes, const int32_t* cd, int64_t n, void* A, int64_t lda,
                                int a_type, float* cp, int64_t* cp64, unsigned long long* rowsum,
                                uint32_t* range_err, int64_t a_limit, cudaStream_t s) {
   const int64_t nb = (n + 31) / 32;
   const int64_t nbx = (lda + 32 * CANON_TJ - 1) / (32 * CANON_TJ);
   dim3 grid((unsigned)nbx, (unsigned)nb), block(32, 8);
-  k_canon_dense<<<grid, block, 0, s>>>(Qd, n, A, lda, a_type, rowsum, range_err, a_limit);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_canon_linear<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Qd, cd, n, cp, cp64);
+  if (q_bytes == 1) {
+    const int8_t* Q8 = static_cast<const int8_t*>(Qd);
+    k_canon_dense<int8_t><<<grid, block, 0, s>>>(Q8, n, A, lda, a_type, rowsum, range_err, a_limit);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_canon_linear<int8_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Q8, cd, n, cp, cp64);
+  } else {
+    const int32_t* Q32 = static_cast<const int32_t*>(Qd);
+    k_canon_dense<int32_t><<<grid, block, 0, s>>>(Q32, n, A, lda, a_type, rowsum, range_err, a_limit);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_canon_linear<int32_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Q32, cd, n, cp, cp64);
+  }
   return cudaGetLastError();
 }
 

@@ -17,7 +17,7 @@ enum Layout : int { LAYOUT_RN = 0 /* [r][i] */, LAYOUT_NR = 1 /* [i][r] */ };
 
 // ---- launchers (each returns the launch's cudaError_t) -----------------------------------
 // k_setup.cu
-cudaError_t launch_canon_dense(const int32_t* Qd, const int32_t* cd, int64_t n, void* A, int64_t lda,
+cudaError_t launch_canon_dense(const void* Qd, int q_bytes, const int32_t* cd, int64_t n, void* A, int64_t lda,
                                int a_type, float* cp, int64_t* cp64, unsigned long long* rowsum,
                                uint32_t* range_err, int64_t a_limit, cudaStream_t s);
 cudaError_t launch_rowsum_check(const unsigned long long* rowsum, const int64_t* cp64, int64_t n,

@@ -26,7 +26,7 @@ DUAL_COORDINATE, DUAL_SINGLE = 0, 1
 KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR, KERNEL_MAXK = 0, 1, 2, 3, 4, 5
 
 # every symbol include/sbo.h declares
-EXPORTS = ["sbo_create_dense", "sbo_create_csr", "sbo_create_maxkcut", "sbo_gda_start", "sbo_gda_start_xy", "sbo_gda_run", "sbo_gda", "sbo_sync",
+EXPORTS = ["sbo_create_dense", "sbo_create_dense_i8", "sbo_create_csr", "sbo_create_maxkcut", "sbo_gda_start", "sbo_gda_start_xy", "sbo_gda_run", "sbo_gda", "sbo_sync",
            "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace", "sbo_lagrangian", "sbo_lagrangian_noalloc", "sbo_dual_bound",
            "sbo_set_option", "sbo_info", "sbo_launch_count", "sbo_destroy", "sbo_last_error", "sbo_version",
            "sbo_group_create", "sbo_group_start", "sbo_group_run", "sbo_group_sync", "sbo_group_set_option",
@@ -69,6 +69,8 @@ def lib():
         "sbo_create_dense": (st, [ctypes.c_int64, _I32P, _I32P, ctypes.c_int32, _P, ctypes.POINTER(_P)]),
         "sbo_create_csr": (st, [ctypes.c_int64, ctypes.c_int64, _I64P, _I32P, _I32P, _I32P, ctypes.c_int32, _P,
                                 ctypes.POINTER(_P)]),
+        "sbo_create_dense_i8": (st, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int8), _I32P, ctypes.c_int32, _P,
+                                     ctypes.POINTER(_P)]),
         "sbo_create_maxkcut": (st, [ctypes.c_int64, ctypes.c_int64, _I32P, _I32P, _I32P, ctypes.c_int32, _P,
                                     ctypes.POINTER(_P)]),
         "sbo_gda_start": (st, [_P, ctypes.POINTER(sbo_gda_params), _F32P]),
@@ -132,12 +134,19 @@ def params(restarts, iters, alpha, beta, ybar, delta=0.01, grad_tol=None, eval_e
 
 # ---- entry points ------------------------------------------------------------------------------
 def sbo_create_dense(Q, c=None, precision=SBO_BF16, stream=None):
-    Q = np.ascontiguousarray(Q, dtype=np.int32)
+    """Q as int32; an int8 array goes to sbo_create_dense_i8 (a quarter of the bytes to copy)."""
+    Q = np.asarray(Q)
     n = Q.shape[0]
     if Q.ndim != 2 or Q.shape[1] != n:
         raise ValueError("Q must be square")
     cc = None if c is None else np.ascontiguousarray(c, dtype=np.int32)
     h = _P()
+    if Q.dtype == np.int8:
+        Q = np.ascontiguousarray(Q)
+        _check(lib().sbo_create_dense_i8(n, _ptr(Q, ctypes.c_int8), None if cc is None else _ptr(cc, ctypes.c_int32),
+                                         int(precision), _stream(stream), ctypes.byref(h)), "sbo_create_dense_i8")
+        return h
+    Q = np.ascontiguousarray(Q, dtype=np.int32)
     _check(lib().sbo_create_dense(n, _ptr(Q, ctypes.c_int32), None if cc is None else _ptr(cc, ctypes.c_int32),
                                   int(precision), _stream(stream), ctypes.byref(h)), "sbo_create_dense")
     return h

@@ -23,7 +23,7 @@ def declared_symbols():
     with open(os.path.join(ROOT, "include", "sbo.h")) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sbo_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(sbo_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_what_the_binding_exports():
