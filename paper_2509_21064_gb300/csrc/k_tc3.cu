@@ -30,7 +30,7 @@
 namespace sbo {
 namespace {
 
-constexpr int CSK_THREADS = 384;   // warp 0 TMA, warp 1 TMEM + MMA, warps 4-11 epilogue
+constexpr int CSK_THREADS = 384;   // warp 0 TMA, warp 1 TMEM + MMA, warps 4-11 partial tile; all in the reduction
 constexpr int CSK_SMEM_BUDGET = 196 * 1024;
 constexpr int CSK_MIN_KB = 4;      // k-blocks per CTA at least
 
@@ -212,9 +212,12 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
   csk_cluster_sync();   // every CTA's partial tile is in its shared memory
   tc_fence_after();
 
-  if (warp >= 4 && *vabort == 0) {
+  if (*vabort == 0) {
     // ------------------------------------------------------------------ reduction + epilogue
-    const int wg = (warp - 4) >> 2;
+    // All twelve warps take part (the producer and MMA warps are idle by now): three groups of
+    // four warps, each over the tile's 128 rows, share the CTA's chunks round-robin.  The rows
+    // come from shared memory, not TMEM, so any warp may take any rows.
+    const int wg = warp >> 2;
     const int wq = warp & 3;
     const int row = wq * 32 + lane;
     const int64_t i = (int64_t)m_tile * TC_BM + row;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
     const int q0 = (int)((int)s * NC / S), q1 = (int)(((int)s + 1) * NC / S);
     const uint32_t part_local = smem_u32(tiles);
     float u[32], v[32], g[32];
-    for (int q = q0 + wg; q < q1; q += 2) {
+    for (int q = q0 + wg; q < q1; q += CSK_THREADS / 128) {
       const int c0 = q * 32;
       const int64_t rbase = (int64_t)n_tile * BN + c0;
       epi_load<MODE>(a, i, row_ok, rbase, u, v);
