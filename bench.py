@@ -218,12 +218,13 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    Q, c = W.dense_qubo(N_VARS, seed=0)
-    p = W.dense_params(Q, restarts=RESTARTS, iters=2000, eval_every=K_EVAL, seed=0)
+    n_vars, restarts = args.n, args.restarts      # the benchmark's sizes unless given
+    Q, c = W.dense_qubo(n_vars, seed=0)
+    p = W.dense_params(Q, restarts=restarts, iters=2000, eval_every=K_EVAL, seed=0)
     import oracle as O
     A, cp = O.canonicalize(Q, c)
-    sub = 16
-    X, _ = O.init_state(N_VARS, sub, p.seed, p.ybar)
+    sub = min(16, restarts)
+    X, _ = O.init_state(n_vars, sub, p.seed, p.ybar)
     Y = np.full_like(X, p.ybar)
     for _ in range(args.warmup):
         X, Y, _ = O.gda_step(A, cp, X, Y, p.alpha, p.beta, p.delta, p.grad_tol)
@@ -239,8 +240,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"dense QUBO n={N_VARS}, B={RESTARTS}, BF16 contraction (oracle: FP64)",
-                       "oracle_sample": f"{sub} of {RESTARTS} restarts, one GDA iteration per step"},
+            "config": {"workload": f"dense QUBO n={n_vars}, B={restarts}, BF16 contraction (oracle: FP64)",
+                       "oracle_sample": f"{sub} of {restarts} restarts, one GDA iteration per step"},
             "cpu_baseline": {"value": value, "unit": "restart-iterations/s", "cores": cores, "kind": "oracle",
                              "sample": f"{sub} restarts x 1 iteration per step, numpy FP64 matmul"},
             "e2e": {"value": value, "unit": "restart-iterations/s", "h2d_bytes_per_step": 0,
