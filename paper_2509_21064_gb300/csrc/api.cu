@@ -249,7 +249,7 @@ CommitArgs commit_args(const sbo_problem* p) {
   CommitArgs c;
   std::memset(&c, 0, sizeof(c));
   c.bits = p->bits;
-  c.op_type = p->op_type;
+  c.op_type = p->kernel == KER_CSR ? OP_U8 : p->op_type;
   c.layout = p->layout;
   c.n = (int)p->n;
   c.B = p->B;
@@ -899,7 +899,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   if (ker != KER_TINY) {
     al(&p->Xop[0], xelems * op_elt);
     al(&p->Xop[1], xelems * op_elt);
-    al(&p->bits, elems * op_elt);
+    al(&p->bits, elems * (ker == KER_CSR ? 1 : op_elt));   // the sparse path keeps candidates as bytes
   }
   al((void**)&p->bestF, sizeof(long long) * p->B);
   al((void**)&p->bestT, sizeof(long long) * p->B);
@@ -932,7 +932,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   cudaMemsetAsync(p->Y, 0, elems * 4, s);
   for (void* b : {p->Xop[0], p->Xop[1]})
     if (b) cudaMemsetAsync(b, 0, xelems * op_elt, s);
-  if (p->bits) cudaMemsetAsync(p->bits, 0, elems * op_elt, s);
+  if (p->bits) cudaMemsetAsync(p->bits, 0, elems * (ker == KER_CSR ? 1 : op_elt), s);
   launch_fill_i64(p->bestF, p->B, LLONG_MAX, s);
   launch_fill_i64(p->bestT, p->B, -1, s);
   launch_fill_i64(p->trace, p->trace_cap, LLONG_MAX, s);
@@ -1083,7 +1083,7 @@ sbo_status sbo_eval(sbo_problem* p, int64_t count, const uint8_t* bits, int64_t*
     if (bits[k] > vmax) return fail(SBO_EINVAL, p->fmt == FMT_MAXK ? "parts must be < k" : "bits must be 0 or 1");
   cudaStream_t s = p->stream;
   const int layout = p->fmt == FMT_DENSE ? LAYOUT_RN : LAYOUT_NR;
-  const int op = p->prec == SBO_FP32 ? OP_F32 : OP_BF16;
+  const int op = p->fmt == FMT_CSR ? OP_U8 : p->prec == SBO_FP32 ? OP_F32 : OP_BF16;
   const int64_t ld = layout == LAYOUT_RN ? round_up(p->n, 8) : round_up(count, 8);
   const int64_t rows = layout == LAYOUT_RN ? count : p->n;
   uint8_t* bd = nullptr;
@@ -1092,12 +1092,12 @@ sbo_status sbo_eval(sbo_problem* p, int64_t count, const uint8_t* bits, int64_t*
   auto cleanup = [&]() { dfree(bd, s); if (opd) cudaFreeAsync(opd, s); opd = nullptr; dfree(f2, s); };
   cudaError_t e;
   if ((e = dalloc(&bd, (size_t)count * p->n, s)) != cudaSuccess ||
-      (e = cudaMallocAsync(&opd, (size_t)rows * ld * (op == OP_F32 ? 4 : 2), s)) != cudaSuccess ||
+      (e = cudaMallocAsync(&opd, (size_t)rows * ld * (op == OP_F32 ? 4 : op == OP_U8 ? 1 : 2), s)) != cudaSuccess ||
       (e = dalloc(&f2, count, s)) != cudaSuccess) {
     cleanup();
     return cuda_fail(e, "cudaMalloc (eval)");
   }
-  cudaMemsetAsync(opd, 0, (size_t)rows * ld * (op == OP_F32 ? 4 : 2), s);
+  cudaMemsetAsync(opd, 0, (size_t)rows * ld * (op == OP_F32 ? 4 : op == OP_U8 ? 1 : 2), s);
   cudaMemsetAsync(f2, 0, sizeof(unsigned long long) * count, s);
   if ((e = cudaMemcpyAsync(bd, bits, (size_t)count * p->n, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
     cleanup();

@@ -21,7 +21,9 @@ constexpr float G_ENT_EPS = 1e-6f;
 enum EpiMode : int { EPI_UPDATE = 0, EPI_EVAL = 1, EPI_LAGR = 2 };
 
 // Operand element types of the contraction.
-enum OpType : int { OP_F32 = 0, OP_BF16 = 1 };
+// OP_U8: 0/1 candidate bytes (the sparse path's candidates; never a contraction operand of the
+// tensor cores).
+enum OpType : int { OP_F32 = 0, OP_BF16 = 1, OP_U8 = 2 };
 
 // Arguments of the fused GDA / evaluation / Lagrangian epilogue.  Every state array is
 // addressed as [r * ld + i] (dense, restart-major) or [i * ld + r] (CSR, variable-major);
@@ -92,10 +94,12 @@ __device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane) 
 
 __device__ __forceinline__ float op_load(const void* p, int64_t idx, int type) {
   if (type == OP_F32) return static_cast<const float*>(p)[idx];
+  if (type == OP_U8) return (float)static_cast<const uint8_t*>(p)[idx];
   return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[idx]);
 }
 __device__ __forceinline__ void op_store(void* p, int64_t idx, float v, int type) {
   if (type == OP_F32) static_cast<float*>(p)[idx] = v;
+  else if (type == OP_U8) static_cast<uint8_t*>(p)[idx] = (uint8_t)v;
   else static_cast<__nv_bfloat16*>(p)[idx] = __float2bfloat16_rn(v);
 }
 

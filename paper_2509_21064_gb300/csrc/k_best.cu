@@ -14,6 +14,10 @@ namespace sbo {
 
 __device__ __forceinline__ float4 op_load4(const void* p, int64_t idx, int type) {
   if (type == OP_F32) return *reinterpret_cast<const float4*>(static_cast<const float*>(p) + idx);
+  if (type == OP_U8) {
+    const uchar4 b = *reinterpret_cast<const uchar4*>(static_cast<const uint8_t*>(p) + idx);
+    return make_float4((float)b.x, (float)b.y, (float)b.z, (float)b.w);
+  }
   const uint2 raw = *reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(p) + idx);
   const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
   const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);

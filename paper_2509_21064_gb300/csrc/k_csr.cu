@@ -23,9 +23,14 @@ __device__ __forceinline__ float load_val(const void* val, int64_t e, int vt) {
   return static_cast<float>(q);
 }
 
-// 4 consecutive operand values (FP32: one 16-byte load; BF16: one 8-byte load).
+// 4 consecutive operand values (FP32: one 16-byte load; BF16: one 8-byte load; candidate bytes:
+// one 4-byte load).
 template <int OPT>
 __device__ __forceinline__ float4 load4(const void* p, int64_t idx) {
+  if (OPT == OP_U8) {
+    const uchar4 b = __ldg(reinterpret_cast<const uchar4*>(static_cast<const uint8_t*>(p) + idx));
+    return make_float4((float)b.x, (float)b.y, (float)b.z, (float)b.w);
+  }
   if (OPT == OP_F32) return __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(p) + idx));
   const uint2 raw = __ldg(reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(p) + idx));
   const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
@@ -34,7 +39,10 @@ __device__ __forceinline__ float4 load4(const void* p, int64_t idx) {
 }
 template <int OPT>
 __device__ __forceinline__ void store4(void* p, int64_t idx, float4 v) {
-  if (OPT == OP_F32) {
+  if (OPT == OP_U8) {
+    *reinterpret_cast<uchar4*>(static_cast<uint8_t*>(p) + idx) =
+        make_uchar4((unsigned char)v.x, (unsigned char)v.y, (unsigned char)v.z, (unsigned char)v.w);
+  } else if (OPT == OP_F32) {
     *reinterpret_cast<float4*>(static_cast<float*>(p) + idx) = v;
   } else {
     __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
@@ -181,7 +189,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
         if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = xn4;
         store4<OPT>(a.Xout, idx, xn4);
         if (!SINGLE) *reinterpret_cast<float4*>(a.Y + idx) = yn4;
-        if (a.bits_out) store4<OPT>(a.bits_out, idx, b4);
+        if (a.bits_out) store4<OP_U8>(a.bits_out, idx, b4);   // candidates as bytes
       } else if (MODE == EPI_EVAL) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
@@ -292,8 +300,7 @@ cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* va
                              : launch_csr_v<EPI_UPDATE, OP_BF16>(rowptr, col, val, val_type, a, pdl, s);
   }
   if (mode == EPI_EVAL) {
-    return op_type == OP_F32 ? launch_csr_v<EPI_EVAL, OP_F32>(rowptr, col, val, val_type, a, pdl, s)
-                             : launch_csr_v<EPI_EVAL, OP_BF16>(rowptr, col, val, val_type, a, pdl, s);
+    return launch_csr_v<EPI_EVAL, OP_U8>(rowptr, col, val, val_type, a, pdl, s);   // candidate bytes
   }
   if (mode == EPI_LAGR) {
     return op_type == OP_F32 ? launch_csr_v<EPI_LAGR, OP_F32>(rowptr, col, val, val_type, a, pdl, s)
