@@ -911,7 +911,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
     // rows of partial sums the update kernel writes: 4 per 128 variables (tcgen05 kernels; CTA
     // pairs round up to 256), 1 per 64 variables (SIMT), 1 per block along the rows (CSR)
     p->gpart_rows = ker == KER_TC ? (p->n + 255) / 256 * 8 : ker == KER_SIMT ? (p->n + 63) / 64
-                                                                             : csr_partial_rows(p->B);
+                                                                             : csr_partial_rows(p->n, p->B);
     p->gpart_ld = round_up(p->B, 8);
     al((void**)&p->mu, sizeof(float) * p->gpart_ld);
     al((void**)&p->gpart, sizeof(float) * p->gpart_rows * p->gpart_ld);

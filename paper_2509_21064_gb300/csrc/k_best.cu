@@ -63,15 +63,32 @@ __global__ void __launch_bounds__(256) k_eval_commit(CommitArgs one, const Commi
       const int64_t q = 4 * qv;
       const bool i0 = improves(a, q), i1 = improves(a, q + 1), i2 = improves(a, q + 2), i3 = improves(a, q + 3);
       if (!(i0 || i1 || i2 || i3)) continue;
-      for (int64_t o = (int64_t)blockIdx.y * rpb + lr; o < outer; o += (int64_t)gridDim.y * rpb) {
-        const int64_t idx = o * a.ld + q;
-        const float4 v = op_load4(a.bits, idx, a.op_type);
-        uchar4 nb = *reinterpret_cast<const uchar4*>(a.bestBits + idx);   // padding restarts keep theirs
-        if (i0) nb.x = (unsigned char)v.x;   // 0/1 bits, or the part index of Max-k-Cut
-        if (i1) nb.y = (unsigned char)v.y;
-        if (i2) nb.z = (unsigned char)v.z;
-        if (i3) nb.w = (unsigned char)v.w;
-        *reinterpret_cast<uchar4*>(a.bestBits + idx) = nb;
+      // four lines per pass, their loads issued before any store; the old best bits are read only
+      // where some of the four restarts keep theirs (padding restarts keep theirs too)
+      const bool all4 = i0 && i1 && i2 && i3;
+      const int64_t step = (int64_t)gridDim.y * rpb;
+      for (int64_t o0 = (int64_t)blockIdx.y * rpb + lr; o0 < outer; o0 += 4 * step) {
+        float4 v[4];
+        uchar4 nb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t o = o0 + u * step;
+          if (o < outer) {
+            v[u] = op_load4(a.bits, o * a.ld + q, a.op_type);
+            if (!all4) nb[u] = *reinterpret_cast<const uchar4*>(a.bestBits + o * a.ld + q);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t o = o0 + u * step;
+          if (o >= outer) continue;
+          if (all4) nb[u] = make_uchar4(0, 0, 0, 0);
+          if (i0) nb[u].x = (unsigned char)v[u].x;   // 0/1 bits, or the part index of Max-k-Cut
+          if (i1) nb[u].y = (unsigned char)v[u].y;
+          if (i2) nb[u].z = (unsigned char)v[u].z;
+          if (i3) nb[u].w = (unsigned char)v[u].w;
+          *reinterpret_cast<uchar4*>(a.bestBits + o * a.ld + q) = nb[u];
+        }
       }
     }
   }

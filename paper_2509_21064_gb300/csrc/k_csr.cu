@@ -9,11 +9,18 @@
 // x and y are loaded before the gathers.  Warps stride over rows; in EPI_EVAL every lane keeps
 // per-restart int64 partial sums of 2F over its rows; a block sums its warps' partials in shared
 // memory and adds one value per restart to the global accumulator.
+#include <algorithm>
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "sbo_internal.h"
 
 namespace sbo {
 
 enum ValType : int { VAL_F32 = 0, VAL_BF16 = 1, VAL_E4M3 = 2 };
+
+constexpr int64_t CSR_WAVES = 1;   // resident waves of blocks per launch
 
 __device__ __forceinline__ float load_val(const void* val, int64_t e, int vt) {
   if (vt == VAL_F32) return __ldg(static_cast<const float*>(val) + e);
@@ -79,16 +86,27 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
     for (int k = 0; k < 4; ++k) f2[v][k] = 0;
   }
 
-  // The structure of the warp's first row (constant for the whole run) is read before waiting on
-  // the previous kernel, so its dependent loads (row pointer, then indices and weights) overlap
-  // that kernel's tail under programmatic dependent launch.
+  // The evaluation's grid is bounded (one closing atomic per restart per block), so its warps
+  // stride over several rows each; they are software-pipelined: while row i is processed, the
+  // column indices and weights of row i + nwarps (whose extent arrived during the previous row)
+  // and the extent of row i + 2 nwarps are in flight, so a row waits only on its gathers.  The
+  // update and the Lagrangian take one row per warp (a grid of ceil(n / 8) blocks per chunk of
+  // restarts), which measured faster than striding at the lower occupancy the pipeline's
+  // registers allow.  The structure is constant for the whole run, so the first rows' is read
+  // before waiting on the previous kernel and overlaps its tail under programmatic dependent
+  // launch.
+  constexpr bool PIPE = MODE == EPI_EVAL;
   int64_t i = warp0;
-  int e0 = 0, e1 = 0, col0 = 0;
+  int e0 = 0, e1 = 0, col0 = 0, f0 = 0, f1 = 0;
   float val0 = 0.0f, cpi = 0.0f;
   long long cp2 = 0;
   if (i < n) {
     e0 = __ldg(rowptr + i);
     e1 = __ldg(rowptr + i + 1);
+    if (PIPE && i + nwarps < n) {
+      f0 = __ldg(rowptr + i + nwarps);
+      f1 = __ldg(rowptr + i + nwarps + 1);
+    }
     const int k = e0 + lane;
     col0 = k < e1 ? __ldg(col + k) : 0;
     val0 = k < e1 ? load_val(val, k, vt) : 0.0f;
@@ -102,14 +120,28 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   for (; i < n; i += nwarps) {
-    if (i != warp0) {
+    if (!PIPE && i != warp0) {
       e0 = __ldg(rowptr + i);
       e1 = __ldg(rowptr + i + 1);
       const int k = e0 + lane;
       col0 = k < e1 ? __ldg(col + k) : 0;
       val0 = k < e1 ? load_val(val, k, vt) : 0.0f;
       cpi = a.cp[i];
-      if (MODE == EPI_EVAL) cp2 = 2 * (long long)a.cp64[i];
+    }
+    const int64_t i1 = i + nwarps, i2 = i1 + nwarps;
+    int ncol = 0, g0 = 0, g1 = 0;
+    float nval = 0.0f, ncpi = 0.0f;
+    long long ncp2 = 0;
+    if (PIPE && i1 < n) {
+      const int k = f0 + lane;
+      ncol = k < f1 ? __ldg(col + k) : 0;
+      nval = k < f1 ? load_val(val, k, vt) : 0.0f;
+      ncpi = a.cp[i1];
+      if (MODE == EPI_EVAL) ncp2 = 2 * (long long)a.cp64[i1];
+      if (i2 < n) {
+        g0 = __ldg(rowptr + i2);
+        g1 = __ldg(rowptr + i2 + 1);
+      }
     }
     // the row's own state first: independent of the gathers
     float4 xo[NV], yo[NV];
@@ -210,6 +242,16 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
         }
       }
     }
+    if (PIPE) {
+      e0 = f0;
+      e1 = f1;
+      col0 = ncol;
+      val0 = nval;
+      cpi = ncpi;
+      cp2 = ncp2;
+      f0 = g0;
+      f1 = g1;
+    }
   }
   if ((MODE == EPI_UPDATE && SINGLE) || (MODE == EPI_LAGR && a.L)) {
     // single-constraint form: the block's warps cover the same restarts; their sums of g go to
@@ -247,26 +289,70 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
   }
 }
 
-int csr_partial_rows(int B) {
-  int NV = 1;
-  while (NV < 2 && 128 * NV < B) NV *= 2;
+// Restarts per lane group: 256 per warp (NV = 2) when there are more than 128 restarts and the
+// grid still holds two full waves of resident warps (152 SMs x 32 warps at 64 registers per
+// thread), else 128 (NV = 1), which doubles the warps of a small graph.  Fewer registers and more
+// warps in flight matter because this kernel is bound by memory latency.
+static int csr_nv(int64_t n, int B) {
+  if (B <= 128) return 1;
+  const int64_t chunks2 = (B + 255) / 256;
+  return n * chunks2 >= 2 * 152 * 32 ? 2 : 1;
+}
+
+int csr_partial_rows(int64_t n, int B) {
+  const int NV = csr_nv(n, B);
   const int chunks = (B + 128 * NV - 1) / (128 * NV);
   return 152 * 8 / (chunks > 0 ? chunks : 1) + 1;
+}
+
+using CsrKernel = void (*)(const int32_t*, const int32_t*, const void*, int, EpiArgs);
+
+template <int MODE, int NV, int OPT>
+static CsrKernel csr_kernel(bool single, bool ent) {
+  if (single) return ent ? k_csr<MODE, NV, OPT, G_ENTROPY, true> : k_csr<MODE, NV, OPT, G_QUAD, true>;
+  return ent ? k_csr<MODE, NV, OPT, G_ENTROPY, false> : k_csr<MODE, NV, OPT, G_QUAD, false>;
+}
+
+// Blocks of 256 threads of kernel k resident on the current device at once (queried once per
+// kernel and device).
+static int64_t csr_resident_blocks(CsrKernel k) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, int64_t>> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152 * 4;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& e : cache)
+    if (e.first.first == (const void*)k && e.first.second == dev) return e.second;
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, 0) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 152 * 4;
+  }
+  const int64_t r = std::max<int64_t>(1, (int64_t)per_sm * sms);
+  cache.push_back({{(const void*)k, dev}, r});
+  return r;
 }
 
 template <int MODE, int OPT>
 static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const void* val, int vt,
                                 const EpiArgs& a, bool pdl, cudaStream_t s) {
-  // at most 256 restarts per warp: fewer registers, more warps in flight (this kernel is bound
-  // by memory latency)
-  int NV = 1;
-  while (NV < 2 && 128 * NV < a.B) NV *= 2;
+  const int NV = csr_nv(a.n, a.B);
+  const bool single = MODE == EPI_UPDATE && a.mu != nullptr;
+  const bool ent = MODE != EPI_EVAL && a.gkind == G_ENTROPY;
+  const CsrKernel kern = NV == 1 ? csr_kernel<MODE, 1, OPT>(single, ent) : csr_kernel<MODE, 2, OPT>(single, ent);
   const int64_t chunks = (a.B + 128 * NV - 1) / (128 * NV);
   const int warps_per_block = 8;
   int64_t want = (a.n + warps_per_block - 1) / warps_per_block;
+  if (MODE == EPI_EVAL) {
+    // one wave of resident blocks: each warp strides over rows with its next rows' structure in
+    // flight
+    const int64_t wave = std::max<int64_t>(1, CSR_WAVES * csr_resident_blocks(kern) / chunks);
+    if (want > wave) want = wave;
+  }
   if (MODE != EPI_UPDATE || a.mu) {
     // bounds the closing atomics (evaluation) or the rows of partial sums (single-constraint form)
-    const int64_t cap = csr_partial_rows(a.B);
+    const int64_t cap = csr_partial_rows(a.n, a.B);
     if (want > cap) want = cap;
   }
   if (want > 65535) want = 65535;
@@ -279,17 +365,7 @@ static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const
   attr.val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = pdl ? 1 : 0;
-  const bool single = MODE == EPI_UPDATE && a.mu != nullptr;
-  const bool ent = MODE != EPI_EVAL && a.gkind == G_ENTROPY;
-#define SBO_CSR_LAUNCH(NVV)                                                                           \
-  if (single)                                                                                          \
-    return ent ? cudaLaunchKernelEx(&cfg, k_csr<MODE, NVV, OPT, G_ENTROPY, true>, rowptr, col, val, vt, a)    \
-               : cudaLaunchKernelEx(&cfg, k_csr<MODE, NVV, OPT, G_QUAD, true>, rowptr, col, val, vt, a);      \
-  return ent ? cudaLaunchKernelEx(&cfg, k_csr<MODE, NVV, OPT, G_ENTROPY, false>, rowptr, col, val, vt, a)      \
-             : cudaLaunchKernelEx(&cfg, k_csr<MODE, NVV, OPT, G_QUAD, false>, rowptr, col, val, vt, a);
-  if (NV == 1) { SBO_CSR_LAUNCH(1) }
-  SBO_CSR_LAUNCH(2)
-#undef SBO_CSR_LAUNCH
+  return cudaLaunchKernelEx(&cfg, kern, rowptr, col, val, vt, a);
 }
 
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,

@@ -61,7 +61,7 @@ cudaError_t launch_tiny(const TinyArgs& a, cudaStream_t s);
 // csr_partial_rows: blocks along the rows (= rows of single-constraint partial sums) at most.
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
                        const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s);
-int csr_partial_rows(int B);
+int csr_partial_rows(int64_t n, int B);
 // k_maxk.cu  (Max-k-Cut: Z, X as [(i k + j) ld + r], y and parts as [i ld + r]; Z in EpiArgs::Xm)
 cudaError_t launch_maxk(const int32_t* rowptr, const int32_t* col, const float* w, const EpiArgs& a, int kp, int mode,
                         cudaStream_t s);
