@@ -4,54 +4,92 @@
 
 namespace sbo {
 
-// A_ij = Q_ij + Q_ji (i != j), A_ii = 0, written as FP32 or BF16 with leading dimension lda.
-// A block owns 32 rows and CANON_TJ consecutive 32x32 column tiles; each tile's transpose is
-// staged through shared memory so both reads coalesce.  Row sums of |A_ij| (exactness of A b in
-// FP32) accumulate in registers over the block's tiles and are added with one atomic per row per
-// block; entries whose magnitude exceeds a_limit (not exact in the storage type) raise a flag.
-constexpr int CANON_TJ = 16;
+// A_ij = Q_ij + Q_ji (i != j), A_ii = 0, written as FP32 or BF16 with leading dimension lda
+// (columns n .. lda-1 zero).  A block owns the pair of 64 x 64 tiles (I, J) and (J, I), I <= J,
+// of the upper triangle of tile pairs: it reads both tiles of Q once into shared memory and
+// writes both tiles of A (A(J, I) is A(I, J) transposed), so Q is read once in all and every
+// global access runs along rows.  Row sums of |A_ij| (exactness of A b in FP32) are formed per
+// tile row from shared memory and added with one atomic per row per tile; entries whose magnitude
+// exceeds a_limit (not exact in the storage type) raise a flag.
+constexpr int CANON_T = 64;
+
+__device__ __forceinline__ int64_t pairs_before(int64_t I, int64_t nt) { return I * nt - I * (I - 1) / 2; }
 
 template <typename TQ>   // int32_t or int8_t entries of Q
-__global__ void __launch_bounds__(256) k_canon_dense(const TQ* __restrict__ Q, int64_t n, void* A,
+__global__ void __launch_bounds__(256) k_canon_dense(const TQ* __restrict__ Q, int64_t n, int64_t nt, void* A,
                                                      int64_t lda, int a_type, unsigned long long* rowsum,
                                                      uint32_t* range_err, int64_t a_limit) {
-  __shared__ int32_t tT[32][33];
-  const int64_t i0 = (int64_t)blockIdx.y * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  unsigned long long rs[4] = {0ull, 0ull, 0ull, 0ull};
-  bool over = false;
-  for (int t = 0; t < CANON_TJ; ++t) {
-    const int64_t j0 = ((int64_t)blockIdx.x * CANON_TJ + t) * 32;
-    if (j0 >= lda) break;
-    // transposed tile: tT[a][b] = Q[j0 + a][i0 + b]
-    for (int a = ty; a < 32; a += 8) {
-      const int64_t r = j0 + a, cidx = i0 + tx;
-      tT[a][tx] = (r < n && cidx < n) ? Q[r * n + cidx] : 0;
-    }
-    __syncthreads();
+  __shared__ int32_t s1[CANON_T][CANON_T + 1];   // Q(I, J)
+  __shared__ int32_t s2[CANON_T][CANON_T + 1];   // Q(J, I)
+  // pair index -> (I, J): row I of the triangle holds the pairs (I, I .. nt-1)
+  const int64_t pidx = blockIdx.x;
+  const double b = 2.0 * (double)nt + 1.0;
+  int64_t I = (int64_t)((b - sqrt(b * b - 8.0 * (double)pidx)) * 0.5);
+  if (I < 0) I = 0;
+  if (I > nt - 1) I = nt - 1;
+  while (I > 0 && pairs_before(I, nt) > pidx) --I;
+  while (pairs_before(I + 1, nt) <= pidx) ++I;
+  const int64_t J = I + (pidx - pairs_before(I, nt));
+  const int64_t r0 = I * CANON_T, c0 = J * CANON_T;
+  const int tid = threadIdx.x;
+  // both tiles, rows of 64 entries: a warp reads two rows' 4-entry groups, thread t columns 4(t%16)..+3
+#pragma unroll 4
+  for (int e = tid; e < CANON_T * CANON_T / 4; e += 256) {
+    const int r = e >> 4, q = (e & 15) * 4;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int a = ty + 8 * k;
-      const int64_t i = i0 + a, j = j0 + tx;
-      int64_t v = 0;
-      if (i < n && j < n && i != j) v = (int64_t)Q[i * n + j] + (int64_t)tT[tx][a];
-      const int64_t av = v < 0 ? -v : v;
-      over |= av > a_limit;
-      if (i < n && j < lda) {
-        if (a_type == OP_F32) static_cast<float*>(A)[i * lda + j] = (float)v;
-        else static_cast<__nv_bfloat16*>(A)[i * lda + j] = __float2bfloat16_rn((float)v);
-      }
-      rs[k] += (unsigned long long)av;
+    for (int u = 0; u < 4; ++u) {
+      const int64_t gi = r0 + r, gj = c0 + q + u;
+      s1[r][q + u] = (gi < n && gj < n) ? (int32_t)Q[gi * n + gj] : 0;
+      const int64_t hi = c0 + r, hj = r0 + q + u;
+      s2[r][q + u] = (hi < n && hj < n) ? (int32_t)Q[hi * n + hj] : 0;
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  bool over = false;
+  // A(I, J)[r][q] = s1[r][q] + s2[q][r];  A(J, I)[r][q] = s2[r][q] + s1[q][r]
+#pragma unroll 2
+  for (int e = tid; e < CANON_T * CANON_T / 4; e += 256) {
+    const int r = e >> 4, q = (e & 15) * 4;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      if (side == 1 && I == J) break;
+      const int64_t gi = (side ? c0 : r0) + r, gj0 = (side ? r0 : c0) + q;
+      if (gi >= n || gj0 >= lda) continue;   // rows beyond n are not stored; lda - gj0 >= 4
+      int64_t v[4];   // int32 entries: the sum of two can leave int32
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u] = side ? (int64_t)s2[r][q + u] + s1[q + u][r] : (int64_t)s1[r][q + u] + s2[q + u][r];
+        if (gi == gj0 + u) v[u] = 0;
+        over |= (v[u] < 0 ? -v[u] : v[u]) > a_limit;
+      }
+      if (a_type == OP_F32) {
+        *reinterpret_cast<float4*>(static_cast<float*>(A) + gi * lda + gj0) =
+            make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+      } else {
+        __nv_bfloat162 lo = __floats2bfloat162_rn((float)v[0], (float)v[1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn((float)v[2], (float)v[3]);
+        uint2 raw;
+        raw.x = *reinterpret_cast<uint32_t*>(&lo);
+        raw.y = *reinterpret_cast<uint32_t*>(&hi);
+        *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(A) + gi * lda + gj0) = raw;
+      }
+    }
   }
   if (over) atomicOr(range_err, 1u);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    unsigned long long s2 = rs[k];
-    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    const int64_t i = i0 + ty + 8 * k;
-    if (tx == 0 && i < n && s2) atomicAdd(&rowsum[i], s2);
+  // row sums: threads 0..63 the rows of A(I, J), threads 64..127 the rows of A(J, I)
+  if (tid < 2 * CANON_T && !(tid >= CANON_T && I == J)) {
+    const bool side = tid >= CANON_T;
+    const int r = tid & (CANON_T - 1);
+    const int64_t gi = (side ? c0 : r0) + r;
+    if (gi < n) {
+      unsigned long long sum = 0ull;
+      for (int q = 0; q < CANON_T; ++q) {
+        const int64_t gj = (side ? r0 : c0) + q;
+        const int64_t v = (gj == gi) ? 0 : (side ? (int64_t)s2[r][q] + s1[q][r] : (int64_t)s1[r][q] + s2[q][r]);
+        sum += (unsigned long long)(v < 0 ? -v : v);
+      }
+      if (sum) atomicAdd(&rowsum[gi], sum);
+    }
   }
 }
 
@@ -78,18 +116,20 @@ __global__ void k_rowsum_check(const unsigned long long* rowsum, const int64_t* 
 cudaError_t launch_canon_dense(const void* Qd, int q_bytes, const int32_t* cd, int64_t n, void* A, int64_t lda,
                                int a_type, float* cp, int64_t* cp64, unsigned long long* rowsum,
                                uint32_t* range_err, int64_t a_limit, cudaStream_t s) {
-  const int64_t nb = (n + 31) / 32;
-  const int64_t nbx = (lda + 32 * CANON_TJ - 1) / (32 * CANON_TJ);
-  dim3 grid((unsigned)nbx, (unsigned)nb), block(32, 8);
+  if (lda % 4 != 0 || lda < n) return cudaErrorInvalidValue;   // 4-entry stores along rows
+  const int64_t nt = (lda + CANON_T - 1) / CANON_T;
+  const int64_t pairs = nt * (nt + 1) / 2;
+  if (pairs > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)pairs), block(256);
   if (q_bytes == 1) {
     const int8_t* Q8 = static_cast<const int8_t*>(Qd);
-    k_canon_dense<int8_t><<<grid, block, 0, s>>>(Q8, n, A, lda, a_type, rowsum, range_err, a_limit);
+    k_canon_dense<int8_t><<<grid, block, 0, s>>>(Q8, n, nt, A, lda, a_type, rowsum, range_err, a_limit);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_canon_linear<int8_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Q8, cd, n, cp, cp64);
   } else {
     const int32_t* Q32 = static_cast<const int32_t*>(Qd);
-    k_canon_dense<int32_t><<<grid, block, 0, s>>>(Q32, n, A, lda, a_type, rowsum, range_err, a_limit);
+    k_canon_dense<int32_t><<<grid, block, 0, s>>>(Q32, n, nt, A, lda, a_type, rowsum, range_err, a_limit);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_canon_linear<int32_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Q32, cd, n, cp, cp64);
