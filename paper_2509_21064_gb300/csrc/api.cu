@@ -548,6 +548,41 @@ extern "C" {
 const char* sbo_last_error(void) { return g_last_error.c_str(); }
 const char* sbo_version(void) { return "sbo 0.1 (sm_103a)"; }
 
+// A second stream for host-to-device copies that the problem's stream consumes piecewise: each
+// copy is ordered after the work already on the problem's stream (the destination's stream-ordered
+// allocation), and the problem's stream waits for it before its next launch.  The stream and
+// events are released when the lane goes out of scope (work in flight completes first).
+struct CopyLane {
+  cudaStream_t cs = nullptr;
+  std::vector<cudaEvent_t> evs;
+  cudaError_t open(cudaStream_t s) {
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { cs = nullptr; return e; }
+    return mark(s, cs);
+  }
+  // event on `from`, waited on by `to`
+  cudaError_t mark(cudaStream_t from, cudaStream_t to) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    evs.push_back(ev);
+    if ((e = cudaEventRecord(ev, from)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(to, ev, 0);
+  }
+  cudaError_t copy(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) return e;
+    return mark(cs, s);
+  }
+  void drain() {   // error paths: no copy may still write memory that is about to be freed
+    if (cs) cudaStreamSynchronize(cs);
+  }
+  ~CopyLane() {
+    for (cudaEvent_t ev : evs) cudaEventDestroy(ev);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
 // Dense set-up shared by the int32 and int8 entry points (q_bytes: size of one entry of Q).
 static sbo_status create_dense_impl(int64_t n, const void* Q, int q_bytes, const int32_t* c, int32_t precision,
                                     void* stream, sbo_problem** out) {
@@ -586,18 +621,41 @@ static sbo_status create_dense_impl(int64_t n, const void* Q, int q_bytes, const
       (e = cudaMallocAsync(&Qd, (size_t)n * n * q_bytes, s)) != cudaSuccess || (e = dalloc(&rowsum, n, s)) != cudaSuccess ||
       (e = dalloc(&rerr, 1, s)) != cudaSuccess || (c && (e = dalloc(&cd, n, s)) != cudaSuccess))
     return bail(e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation failed") : cuda_fail(e, "cudaMalloc"));
-  if ((e = cudaMemcpyAsync(Qd, Q, (size_t)q_bytes * n * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return bail(cuda_fail(e, "copy Q"));
   if (c && (e = cudaMemcpyAsync(cd, c, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return bail(cuda_fail(e, "copy c"));
   cudaMemsetAsync(rowsum, 0, sizeof(unsigned long long) * n, s);
   cudaMemsetAsync(rerr, 0, sizeof(uint32_t), s);
   const int64_t limit = p->a_type == OP_F32 ? (1ll << 24) : 256;
-  if ((e = launch_canon_dense(Qd, q_bytes, cd, n, p->A, p->lda, p->a_type, p->cp, p->cp64, rowsum, rerr, limit, s)) !=
-      cudaSuccess)
+  // Q crosses in up to 16 panels of whole 64-row tiles on a second stream; as each lands, the
+  // problem's stream canonicalises the tile pairs whose rows have all arrived (the panel's tile
+  // columns), so the copy and the canonicalisation overlap.
+  {
+    CopyLane lane;
+    if ((e = lane.open(s)) != cudaSuccess) return bail(cuda_fail(e, "copy stream"));
+    const int64_t nt = (p->lda + 63) / 64;
+    const int64_t per = (nt + 15) / 16;
+    for (int64_t j0 = 0; j0 < nt; j0 += per) {
+      const int64_t j1 = std::min(nt, j0 + per);
+      const int64_t r0 = 64 * j0, r1 = std::min<int64_t>(n, 64 * j1);
+      if (r1 > r0) {
+        const size_t off = (size_t)r0 * n * q_bytes, bytes = (size_t)(r1 - r0) * n * q_bytes;
+        if ((e = lane.copy(static_cast<char*>(Qd) + off, static_cast<const char*>(Q) + off, bytes, s)) != cudaSuccess) {
+          lane.drain();
+          return bail(cuda_fail(e, "copy Q"));
+        }
+      }
+      if ((e = launch_canon_dense(Qd, q_bytes, n, j0, j1, p->A, p->lda, p->a_type, rowsum, rerr, limit, s)) !=
+          cudaSuccess) {
+        lane.drain();
+        return bail(cuda_fail(e, "canonicalisation launch"));
+      }
+      ++p->launches;
+    }
+  }
+  if ((e = launch_canon_linear(Qd, q_bytes, cd, n, p->cp, p->cp64, s)) != cudaSuccess)
     return bail(cuda_fail(e, "canonicalisation launch"));
   if ((e = launch_rowsum_check(rowsum, p->cp64, n, rerr, s)) != cudaSuccess) return bail(cuda_fail(e, "row-sum check"));
-  p->launches += 3;
+  p->launches += 2;
   uint32_t flags = 0;
   if ((e = cudaMemcpyAsync(&flags, rerr, sizeof(flags), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)

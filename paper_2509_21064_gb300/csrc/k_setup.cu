@@ -6,30 +6,29 @@ namespace sbo {
 
 // A_ij = Q_ij + Q_ji (i != j), A_ii = 0, written as FP32 or BF16 with leading dimension lda
 // (columns n .. lda-1 zero).  A block owns the pair of 64 x 64 tiles (I, J) and (J, I), I <= J,
-// of the upper triangle of tile pairs: it reads both tiles of Q once into shared memory and
+// of the tile columns J in [j0, j1) (pairs numbered down each column: (0, J), (1, J) .. (J, J)),
+// which needs Q's rows of tiles up to j1 only: it reads both tiles of Q once into shared memory and
 // writes both tiles of A (A(J, I) is A(I, J) transposed), so Q is read once in all and every
 // global access runs along rows.  Row sums of |A_ij| (exactness of A b in FP32) are formed per
 // tile row from shared memory and added with one atomic per row per tile; entries whose magnitude
 // exceeds a_limit (not exact in the storage type) raise a flag.
 constexpr int CANON_T = 64;
 
-__device__ __forceinline__ int64_t pairs_before(int64_t I, int64_t nt) { return I * nt - I * (I - 1) / 2; }
+__device__ __forceinline__ int64_t tri(int64_t J) { return J * (J + 1) / 2; }   // pairs in columns < J
 
 template <typename TQ>   // int32_t or int8_t entries of Q
-__global__ void __launch_bounds__(256) k_canon_dense(const TQ* __restrict__ Q, int64_t n, int64_t nt, void* A,
+__global__ void __launch_bounds__(256) k_canon_dense(const TQ* __restrict__ Q, int64_t n, int64_t j0, void* A,
                                                      int64_t lda, int a_type, unsigned long long* rowsum,
                                                      uint32_t* range_err, int64_t a_limit) {
   __shared__ int32_t s1[CANON_T][CANON_T + 1];   // Q(I, J)
   __shared__ int32_t s2[CANON_T][CANON_T + 1];   // Q(J, I)
-  // pair index -> (I, J): row I of the triangle holds the pairs (I, I .. nt-1)
-  const int64_t pidx = blockIdx.x;
-  const double b = 2.0 * (double)nt + 1.0;
-  int64_t I = (int64_t)((b - sqrt(b * b - 8.0 * (double)pidx)) * 0.5);
-  if (I < 0) I = 0;
-  if (I > nt - 1) I = nt - 1;
-  while (I > 0 && pairs_before(I, nt) > pidx) --I;
-  while (pairs_before(I + 1, nt) <= pidx) ++I;
-  const int64_t J = I + (pidx - pairs_before(I, nt));
+  // pair index -> (I, J): q = tri(J) + I with 0 <= I <= J
+  const int64_t q = tri(j0) + (int64_t)blockIdx.x;
+  int64_t J = (int64_t)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  if (J < 0) J = 0;
+  while (J > 0 && tri(J) > q) --J;
+  while (tri(J + 1) <= q) ++J;
+  const int64_t I = q - tri(J);
   const int64_t r0 = I * CANON_T, c0 = J * CANON_T;
   const int tid = threadIdx.x;
   // both tiles, rows of 64 entries: a warp reads two rows' 4-entry groups, thread t columns 4(t%16)..+3
@@ -113,27 +112,30 @@ __global__ void k_rowsum_check(const unsigned long long* rowsum, const int64_t* 
   if (c >= (1ll << 31) || c <= -(1ll << 31)) atomicOr(range_err, 4u);
 }
 
-cudaError_t launch_canon_dense(const void* Qd, int q_bytes, const int32_t* cd, int64_t n, void* A, int64_t lda,
-                               int a_type, float* cp, int64_t* cp64, unsigned long long* rowsum,
-                               uint32_t* range_err, int64_t a_limit, cudaStream_t s) {
-  if (lda % 4 != 0 || lda < n) return cudaErrorInvalidValue;   // 4-entry stores along rows
-  const int64_t nt = (lda + CANON_T - 1) / CANON_T;
-  const int64_t pairs = nt * (nt + 1) / 2;
+cudaError_t launch_canon_dense(const void* Qd, int q_bytes, int64_t n, int64_t j0, int64_t j1, void* A, int64_t lda,
+                               int a_type, unsigned long long* rowsum, uint32_t* range_err, int64_t a_limit,
+                               cudaStream_t s) {
+  if (lda % 4 != 0 || lda < n || j0 < 0 || j1 < j0) return cudaErrorInvalidValue;   // 4-entry stores along rows
+  const int64_t pairs = j1 * (j1 + 1) / 2 - j0 * (j0 + 1) / 2;
+  if (pairs == 0) return cudaSuccess;
   if (pairs > 0x7fffffffLL) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)pairs), block(256);
-  if (q_bytes == 1) {
-    const int8_t* Q8 = static_cast<const int8_t*>(Qd);
-    k_canon_dense<int8_t><<<grid, block, 0, s>>>(Q8, n, nt, A, lda, a_type, rowsum, range_err, a_limit);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_canon_linear<int8_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Q8, cd, n, cp, cp64);
-  } else {
-    const int32_t* Q32 = static_cast<const int32_t*>(Qd);
-    k_canon_dense<int32_t><<<grid, block, 0, s>>>(Q32, n, nt, A, lda, a_type, rowsum, range_err, a_limit);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_canon_linear<int32_t><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(Q32, cd, n, cp, cp64);
-  }
+  if (q_bytes == 1)
+    k_canon_dense<int8_t><<<grid, block, 0, s>>>(static_cast<const int8_t*>(Qd), n, j0, A, lda, a_type, rowsum,
+                                                 range_err, a_limit);
+  else
+    k_canon_dense<int32_t><<<grid, block, 0, s>>>(static_cast<const int32_t*>(Qd), n, j0, A, lda, a_type, rowsum,
+                                                  range_err, a_limit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_canon_linear(const void* Qd, int q_bytes, const int32_t* cd, int64_t n, float* cp, int64_t* cp64,
+                                cudaStream_t s) {
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (q_bytes == 1)
+    k_canon_linear<int8_t><<<blocks, 256, 0, s>>>(static_cast<const int8_t*>(Qd), cd, n, cp, cp64);
+  else
+    k_canon_linear<int32_t><<<blocks, 256, 0, s>>>(static_cast<const int32_t*>(Qd), cd, n, cp, cp64);
   return cudaGetLastError();
 }
 

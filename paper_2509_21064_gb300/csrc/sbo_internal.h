@@ -17,9 +17,13 @@ enum Layout : int { LAYOUT_RN = 0 /* [r][i] */, LAYOUT_NR = 1 /* [i][r] */ };
 
 // ---- launchers (each returns the launch's cudaError_t) -----------------------------------
 // k_setup.cu
-cudaError_t launch_canon_dense(const void* Qd, int q_bytes, const int32_t* cd, int64_t n, void* A, int64_t lda,
-                               int a_type, float* cp, int64_t* cp64, unsigned long long* rowsum,
-                               uint32_t* range_err, int64_t a_limit, cudaStream_t s);
+// canonical A for the 64 x 64 tile pairs (I, J), I <= J, of tile columns [j0, j1) (rows of Q up
+// to tile j1 must be present); c' = c + diag Q once all of Q is present
+cudaError_t launch_canon_dense(const void* Qd, int q_bytes, int64_t n, int64_t j0, int64_t j1, void* A, int64_t lda,
+                               int a_type, unsigned long long* rowsum, uint32_t* range_err, int64_t a_limit,
+                               cudaStream_t s);
+cudaError_t launch_canon_linear(const void* Qd, int q_bytes, const int32_t* cd, int64_t n, float* cp, int64_t* cp64,
+                                cudaStream_t s);
 cudaError_t launch_rowsum_check(const unsigned long long* rowsum, const int64_t* cp64, int64_t n,
                                 uint32_t* range_err, cudaStream_t s);
 cudaError_t launch_init_state(int n, int B, int64_t ld, int layout, uint64_t seed, float ybar,
