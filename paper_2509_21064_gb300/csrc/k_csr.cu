@@ -272,20 +272,21 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
     }
   }
   if (MODE == EPI_EVAL) {
-    // the block's warps cover the same restarts: sum them in shared memory, then one atomic
-    // per restart per block
-    __shared__ unsigned long long red[128 * NV];
-    for (int t = threadIdx.x; t < 128 * NV; t += blockDim.x) red[t] = 0ull;
-    __syncthreads();
+    // the block's warps cover the same restarts: each warp's sums go to its row of shared
+    // memory, a thread per restart adds the rows, then one atomic per restart per block
+    __shared__ long long red[8][128 * NV];
+    const int w = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (f2[v][k] != 0) atomicAdd(&red[128 * v + 4 * lane + k], (unsigned long long)f2[v][k]);
+      for (int k = 0; k < 4; ++k) red[w][128 * v + 4 * lane + k] = f2[v][k];
     __syncthreads();
     const int64_t rb = (int64_t)blockIdx.y * 128 * NV;
-    for (int t = threadIdx.x; t < 128 * NV; t += blockDim.x)
-      if (rb + t < B && red[t] != 0ull) atomicAdd(&a.F2[rb + t], red[t]);
+    for (int t = threadIdx.x; t < 128 * NV; t += blockDim.x) {
+      long long sum = 0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += red[q][t];
+      if (rb + t < B && sum != 0) atomicAdd(&a.F2[rb + t], (unsigned long long)sum);
+    }
   }
 }
 

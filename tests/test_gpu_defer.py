@@ -1,0 +1,82 @@
+"""Deferred evaluation of sparse runs replayed from CUDA graphs: a replayed block leaves the
+candidates of its last iteration pending, and the next block evaluates them on a graph branch
+beside its first K - 1 steps; every call that reads results evaluates what is pending first.
+Against the same run without graphs (every evaluation right after its step): identical states,
+per-restart bests, min-F traces and global bests, for several splittings of the run into calls,
+with and without results read between the calls, K even and odd, T not a multiple of K."""
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2509_21064_gb300 import sbo as S
+from paper_2509_21064_gb300.build import build as build_lib
+from _helpers import to_gda_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib()
+    S.lib()
+
+
+def _run(n, csr, prec, prm, graph, chunks, peek):
+    rowptr, col, val, c = csr
+    seen = []
+    with S.Problem.csr(n, rowptr, col, val, c, precision=prec) as P:
+        P.set_option(S.SBO_OPT_USE_GRAPH, int(graph))
+        P.start(prm)
+        for k in chunks:
+            P.run(k)
+            if peek:   # results between calls: pending evaluations are flushed here
+                Fr, tr = P.restart_best()
+                seen.append((Fr.copy(), tr.copy(), P.trace().copy()))
+        P.sync()
+        X, Y = P.state()
+        Fr, tr = P.restart_best()
+        best = P.best()
+        trace = P.trace()
+    return X, Y, Fr, tr, best, trace, seen
+
+
+def _same(a, b):
+    for u, v in zip(a[:4], b[:4]):
+        assert np.array_equal(u, v)
+    assert a[4][1:] == b[4][1:] and np.array_equal(a[4][0], b[4][0])
+    assert np.array_equal(a[5], b[5])
+    assert len(a[6]) == len(b[6])
+    for (f1, t1, s1), (f2, t2, s2) in zip(a[6], b[6]):
+        assert np.array_equal(f1, f2) and np.array_equal(t1, t2) and np.array_equal(s1, s2)
+
+
+@pytest.mark.parametrize("K,T,chunks", [(7, 100, (100,)), (7, 100, (3, 11, 1, 28, 57)), (10, 120, (10,) * 12),
+                                         (2, 31, (5, 4, 22)), (10, 95, (40, 40, 15))])
+@pytest.mark.parametrize("peek", [False, True])
+@pytest.mark.parametrize("prec", [S.SBO_FP32, S.SBO_BF16])
+def test_deferred_evaluations_match_immediate_ones(K, T, chunks, peek, prec):
+    """Erdos-Renyi n = 3001, B = 200 (ragged rows and restart chunks)."""
+    n = 3001
+    i, j, w = W.maxcut_er(n, 6.0, seed=3)
+    csr = W.maxcut_qubo(n, i, j, w)
+    p = W.graph_params("maxcut", restarts=200, iters=T, eval_every=K, seed=5)
+    prm = to_gda_params(p)
+    a = _run(n, csr, prec, prm, 1, chunks, peek)
+    b = _run(n, csr, prec, prm, 0, chunks, peek)
+    _same(a, b)
+    x_star, F_star = a[4][0], a[4][1]
+    assert F_star == -int(np.sum(w * (x_star[i] != x_star[j])))
+    assert len(a[5]) == len(range(K, T + 1, K)) + (T % K != 0)   # one trace entry per evaluation
+
+
+def test_deferred_evaluations_on_the_torus_with_two_restart_groups_per_warp():
+    """100 x 100 torus, B = 512 (256 restarts per warp in the update and the evaluation), K = 10,
+    the run split into calls of one block each (as the benchmark drives it)."""
+    i, j, w = W.maxcut_torus(100, 100, seed=0)
+    n = 10000
+    csr = W.maxcut_qubo(n, i, j, w)
+    p = W.graph_params("maxcut", restarts=512, iters=80, eval_every=10, seed=2)
+    prm = to_gda_params(p)
+    a = _run(n, csr, S.SBO_FP32, prm, 1, (10,) * 8, False)
+    b = _run(n, csr, S.SBO_FP32, prm, 0, (10,) * 8, False)
+    _same(a, b)
