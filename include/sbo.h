@@ -115,7 +115,10 @@ sbo_status sbo_create_maxkcut(int64_t n, int64_t m, const int32_t* ei, const int
  * x^0 from x0 (host, B*n float32 row-major [r][i], values in [0,1]) or, when x0 is NULL,
  * from the SplitMix64 rule of prm->seed; y^0 = ybar; clears every best.  Asynchronous.
  * sbo_gda_run: enqueues `iters` more iterations (the iteration counter continues), with
- * evaluations at t = K, 2K, ... and t = prm->iters.  Asynchronous.
+ * evaluations at t = K, 2K, ... and t = prm->iters.  Asynchronous.  A sparse run replayed from
+ * CUDA graphs may leave the evaluation of its latest evaluation point pending (it then runs beside
+ * the next block's iterations); sbo_sync, sbo_best, sbo_restart_best and sbo_trace complete it
+ * first, so every result they report covers all evaluation points up to the current t.
  * sbo_gda: start (x0 = NULL) + run(prm->iters) + synchronise.  A handle may run again:
  * each start begins afresh. */
 sbo_status sbo_gda_start(sbo_problem* p, const sbo_gda_params* prm, const float* x0);
