@@ -133,11 +133,11 @@ struct sbo_problem {
   float* tc_ws = nullptr;      // split-K partial tiles of the tcgen05 contraction
   int* tc_ctr = nullptr;       // split-K arrival counters (zero between launches)
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  // Deferred evaluation (sparse runs with K >= 2): a replayed block leaves the candidates of its
-  // last iteration unevaluated (eval_pending; they are those of iteration t), and the next block
-  // evaluates them on a branch of its graph beside its first K - 1 steps, which neither read nor
-  // write what the evaluation touches.  Every call that reads results first evaluates what is
-  // pending (flush_pending).
+  // Deferred evaluation (sparse and Max-k-Cut runs with K >= 2): a replayed block leaves the
+  // candidates of its last iteration unevaluated (eval_pending; they are those of iteration t), and
+  // the next block evaluates them on a branch of its graph beside its first K - 1 steps, which
+  // neither read nor write what the evaluation touches.  Every call that reads results first
+  // evaluates what is pending (flush_pending).
   cudaGraphExec_t gexec_nv[2] = {nullptr, nullptr};   // K steps, no evaluation
   cudaGraphExec_t gexec_ov[2] = {nullptr, nullptr};   // pending evaluation beside K steps
   bool eval_pending = false;
@@ -313,14 +313,17 @@ int64_t next_eval_after(const sbo_problem* p, int64_t t) {
 }
 
 // Evaluations are deferred across blocks only where every step leaves the bits alone (K >= 2) and
-// the evaluation runs well beside the steps: sparse runs replayed from graphs whose x and y fit in
-// three quarters of L2, so that the steps, like the evaluation, wait on latency rather than on
-// DRAM.  Measured per iteration with K = 10 (FP32): Max-Cut ER n = 2,000, B = 256 5.76 -> 5.14 us
+// the evaluation runs well beside the steps: sparse and Max-k-Cut runs replayed from graphs whose
+// state fits in three quarters of L2, so that the steps, like the evaluation, wait on latency
+// rather than on DRAM.  Measured per iteration with K = 10 (FP32): Max-Cut ER n = 2,000, B = 256 5.76 -> 5.14 us
 // and the 100 x 100 torus, B = 512 16.99 -> 16.41 us deferred; the 4-regular graph n = 20,000,
 // B = 512, whose 164 MB of x and y stream from DRAM, 42.95 -> 43.48 us, so it is not deferred.
 bool defer_evals(const sbo_problem* p) {
-  const int64_t state = p->n * (int64_t)p->B * 16;   // x and y, FP32, read and written
-  return p->kernel == KER_CSR && p->prm.eval_every >= 2 && p->opt_graph && state * 4 <= p->l2_bytes * 3;
+  // bytes read and written per element: x and y (FP32); Max-k-Cut: Z and X (k floats each) and y
+  const int64_t per = p->kernel == KER_MAXK ? 16 * (int64_t)p->kparts + 8 : 16;
+  const int64_t state = p->n * (int64_t)p->B * per;
+  return (p->kernel == KER_CSR || p->kernel == KER_MAXK) && p->prm.eval_every >= 2 && p->opt_graph &&
+         state * 4 <= p->l2_bytes * 3;
 }
 
 // Evaluate the deferred candidates (those of iteration t) on the problem's stream.

@@ -80,3 +80,31 @@ def test_deferred_evaluations_on_the_torus_with_two_restart_groups_per_warp():
     a = _run(n, csr, S.SBO_FP32, prm, 1, (10,) * 8, False)
     b = _run(n, csr, S.SBO_FP32, prm, 0, (10,) * 8, False)
     _same(a, b)
+
+
+@pytest.mark.parametrize("peek", [False, True])
+def test_deferred_evaluations_of_max3cut(peek):
+    """Max-3-Cut of a 30 x 40 +-1 torus, B = 100, K = 7, T = 60, the run split at points that are
+    and are not evaluation points: parts, cuts, traces and states as with in-line evaluation."""
+    i, j, w = W.maxcut_torus(30, 40, seed=1)
+    n = 1200
+    p = W.GdaParams(restarts=100, iters=60, alpha=0.01, beta=0.01, ybar=6.0, eval_every=7, seed=4)
+    prm = to_gda_params(p)
+    out = []
+    for graph in (1, 0):
+        seen = []
+        with S.Problem.maxkcut(n, i, j, w, 3) as P:
+            P.set_option(S.SBO_OPT_USE_GRAPH, graph)
+            P.start(prm)
+            for k in (3, 11, 1, 28, 17):
+                P.run(k)
+                if peek:
+                    Fr, tr = P.restart_best()
+                    seen.append((Fr.copy(), tr.copy(), P.trace().copy()))
+            P.sync()
+            X, Y = P.state()
+            Fr, tr = P.restart_best()
+            out.append((X, Y, Fr, tr, P.best(), P.trace(), seen))
+    _same(out[0], out[1])
+    parts, F = out[0][4][0], out[0][4][1]
+    assert F == -int(np.sum(w * (parts[i] != parts[j])))
