@@ -1157,6 +1157,10 @@ sbo_status sbo_gda_run(sbo_problem* p, int64_t iters) {
   const int64_t K = p->prm.eval_every;
   const int64_t t_end = p->t + iters;
   while (p->t < t_end) {
+    if (p->eval_pending && !defer_evals(p)) {   // deferral switched off (graphs): evaluate in line
+      sbo_status st = flush_pending(p);
+      if (st != SBO_OK) return st;
+    }
     const int64_t nx = next_eval_after(p, p->t);
     const int64_t stop = std::min(nx, t_end);
     const int64_t steps = stop - p->t;

@@ -108,3 +108,28 @@ def test_deferred_evaluations_of_max3cut(peek):
     _same(out[0], out[1])
     parts, F = out[0][4][0], out[0][4][1]
     assert F == -int(np.sum(w * (parts[i] != parts[j])))
+
+
+def test_graphs_switched_off_and_on_between_calls():
+    """Replay switched off while an evaluation is pending, then on again: the pending evaluation
+    runs in line and nothing is lost or evaluated twice."""
+    n = 3001
+    i, j, w = W.maxcut_er(n, 6.0, seed=3)
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    p = W.graph_params("maxcut", restarts=200, iters=120, eval_every=10, seed=5)
+    prm = to_gda_params(p)
+    out = []
+    for toggle in (True, False):
+        with S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32) as P:
+            P.set_option(S.SBO_OPT_USE_GRAPH, 1 if toggle else 0)
+            P.start(prm)
+            for k, g in ((40, 0), (30, 1), (50, 1)):
+                P.run(k)
+                if toggle:
+                    P.set_option(S.SBO_OPT_USE_GRAPH, g)
+            P.sync()
+            X, Y = P.state()
+            Fr, tr = P.restart_best()
+            out.append((X, Y, Fr, tr, P.best(), P.trace(), []))
+    _same(out[0], out[1])
+    assert len(out[0][5]) == 12
