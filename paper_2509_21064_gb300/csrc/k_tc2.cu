@@ -41,7 +41,6 @@ constexpr int P_SMEM = P_STAGES * P_STAGE_BYTES + 1024 /* align */ + 1024 /* bar
 constexpr int P_TMEM_COLS = 2 * P_BN;
 constexpr uint32_t P_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(P_BN >> 3) << 17) |
                              ((uint32_t)(256 >> 4) << 24);
-constexpr int P_MIN_KB_PER_SPLIT = 8;
 
 struct PairParams {
   CUtensorMap mapA;   // box 64 x 128
