@@ -190,6 +190,23 @@ def time_to_target(S, torch, Q, c, seed, stream, dev, target, iters=2000):
     return out
 
 
+def quality_vs_plain_fp32(S, Q, c, seed, stream, iters=500):
+    """Best objective after the same T iterations (K = K_EVAL, same x^0, all restarts) of the
+    chosen form (BF16 tensor-core contraction) and of the plain FP32 form, and their relative gap
+    (positive: the chosen form's best is worse)."""
+    p = W.dense_params(Q, restarts=RESTARTS_DEFAULT, iters=iters, eval_every=K_EVAL, seed=seed)
+    best = {}
+    for name, prec in (("bf16", S.SBO_BF16), ("fp32", S.SBO_FP32)):
+        P = S.Problem.dense(Q, c, precision=prec, stream=stream)
+        if prec == S.SBO_FP32:
+            P.set_option(S.SBO_OPT_KERNEL, S.KERNEL_SIMT)
+        P.gda(S.params(**p.asdict()))
+        best[name] = int(P.best()[1])
+        P.close()
+    return {"iters": iters, "restarts": RESTARTS_DEFAULT, "best_F_chosen": best["bf16"], "best_F_plain_fp32": best["fp32"],
+            "rel_gap": (best["bf16"] - best["fp32"]) / abs(best["fp32"])}
+
+
 def plain_fp32_form(S, torch, Q, c, seed, stream, dev, iters=3):
     """The plain form on the same instance: FP32 A and x, CUDA-core (SIMT) contraction with the
     same fused update, one launch per iteration, no CUDA graph."""
@@ -376,6 +393,7 @@ def run_ours(args):
     plain = None
     if rank == 0 and N_VARS == 20000 and RESTARTS == 1024 and not args.no_plain_form:
         plain = plain_fp32_form(S, torch, Q, c, 0, stream, dev)
+        plain["quality_at_equal_iterations"] = quality_vs_plain_fp32(S, Q, c, 0, stream)
 
     pk, src = peaks()
     flops = 2.0 * N_VARS * N_VARS * RESTARTS
