@@ -14,6 +14,9 @@ Reported (one JSON line on rank 0):
               (CUDA events around each launch inside the timed region), against the measured
               sustained BF16 peak
   cpu_baseline the FP64 oracle on the host cores, on a bounded sample (restart subset)
+  time_to_target  device seconds until the best objective reaches the FP64 oracle's best
+  plain_fp32_form the plain FP32 CUDA-core form on the same instance: its throughput, and the best
+              objectives of both forms after the same T iterations
 ``--impl reference`` times the oracle alone (the reference arm of this comparison).
 Multi-GPU (torchrun): every rank runs its own B restarts (different seeds) of the same instance,
 no collective in the timed loop; value = all ranks' restart-iterations / max rank time.
