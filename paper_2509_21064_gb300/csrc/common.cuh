@@ -38,7 +38,7 @@ struct EpiArgs {
   float* Y;                // y, updated in place
   const void* Xin;         // contraction operand x^t (FP32 or BF16), read by every tile
   void* Xout;              // operand x^{t+1} (ping-pong partner of Xin)
-  void* bits_out;          // if non-null: b = [x^{t+1} > 1/2] in the operand type
+  void* bits_out;          // if non-null: b = [x^{t+1} > 1/2] in the operand type (bytes for the sparse kernel)
   unsigned long long* F2;  // EPI_EVAL: 2F(b) accumulators per restart (two's complement)
   const float* Xl;         // EPI_LAGR: x (FP32)
   const float* Yl;         // EPI_LAGR: y (FP32)
