@@ -3,12 +3,13 @@
 // State is variable-major: element (i, r) at [i * ld + r] (ld a multiple of 8), so the B
 // restarts of one variable are contiguous.  One warp owns one row i of A and a chunk of 128*NV
 // restarts; lane l holds the 4 consecutive restarts rbase + 128 v + 4 l .. +3 (v < NV), so each
-// gather X[j][...] of a neighbour j is one 512-byte (FP32) or 256-byte (BF16) run per v.  The
-// row's column indices and weights are loaded 32 at a time, one per lane, and broadcast with
-// shuffles, so the gathers of consecutive neighbours do not wait on each other; the row's own
-// x and y are loaded before the gathers.  Warps stride over rows; in EPI_EVAL every lane keeps
-// per-restart int64 partial sums of 2F over its rows; a block sums its warps' partials in shared
-// memory and adds one value per restart to the global accumulator.
+// gather X[j][...] of a neighbour j is one 512-byte (FP32) or 256-byte (BF16) run per v (128
+// bytes of candidates in EPI_EVAL, which reads one byte per (vertex, restart)).  The row's column
+// indices and weights are loaded 32 at a time, one per lane, and broadcast with shuffles, so the
+// gathers of consecutive neighbours do not wait on each other; the row's own x and y are loaded
+// before the gathers.  Warps stride over rows; in EPI_EVAL every lane keeps per-restart int64
+// partial sums of 2F over its rows; a block sums its warps' partials in shared memory, in warp
+// order, and adds one value per restart to the global accumulator.
 #include <algorithm>
 #include <mutex>
 #include <utility>
