@@ -8,6 +8,7 @@ library.  Usage: ``python -m paper_2509_21064_gb300.build [--force] [--verbose]`
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -47,10 +48,24 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every CUDA source for sm_103a and link libsbo.so; returns the library path."""
+    """Compile every CUDA source for sm_103a and link libsbo.so; returns the library path.
+
+    Processes that build at once (ranks of one job) take turns on a lock file; a process that
+    waited finds the library current and returns."""
     if not force and up_to_date():
         return LIB
     os.makedirs(LIBDIR, exist_ok=True)
+    with open(os.path.join(LIBDIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date():
+                return LIB
+            return _build_locked(verbose, extra)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, extra) -> str:
     objdir = os.path.join(LIBDIR, "obj")
     os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
