@@ -201,6 +201,9 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
 
 /* ---- execution options -------------------------------------------------------------------
  * sbo_set_option: selects execution details; values take effect at the next sbo_gda_start.
+ * SBO_OPT_USE_GRAPH also applies to the next sbo_gda_run of the current run, and SBO_OPT_PDL and
+ * SBO_OPT_TIMEOUT_US to its directly launched kernels (replayed graphs keep the values they were
+ * captured with until the next start); results depend on none of the three.
  *   SBO_OPT_KERNEL:     0 auto, 1 SIMT FP32 (plain form), 2 tcgen05 (BF16 dense),
  *                       3 tiny-n single-CTA loop (n <= 64, FP32)
  *   SBO_OPT_USE_GRAPH:  1 (default) replay blocks of K iterations from a CUDA graph; 0 launch
