@@ -79,7 +79,7 @@ def canonicalize(Q, c=None):
 
 
 def canonicalize_csr(n, rowptr, col, val, c=None):
-    """The same multilinear form as ``canonicalize`` for a CSR Q, as a scipy sparse A
+    """Prop. 2.4 for a CSR Q: the same multilinear form as ``canonicalize``, as a scipy sparse A
     (A = Q + Q^T off the diagonal, c' = c + diag Q).  scipy is only the storage and the matmul."""
     import scipy.sparse as sp
     Qs = sp.csr_matrix((np.asarray(val, dtype=np.float64), np.asarray(col), np.asarray(rowptr)), shape=(n, n))
@@ -101,7 +101,7 @@ def objective(Q, c, b):
 
 
 def objective_batch(Q, c, Bits):
-    """Exact F for every row of ``Bits`` (B x n, values 0/1) in int64."""
+    """Exact F (Eq. 1, QUBO) for every row of ``Bits`` (B x n, values 0/1) in int64."""
     Q = np.asarray(Q, dtype=np.int64)
     Bm = np.asarray(Bits, dtype=np.int64)
     c = np.zeros(Q.shape[0], np.int64) if c is None else np.asarray(c, dtype=np.int64)
@@ -109,7 +109,7 @@ def objective_batch(Q, c, Bits):
 
 
 def objective_csr(n, rowptr, col, val, c, b):
-    """Exact F(b) for a CSR Q: sum over stored (i, j, q) of q b_i b_j, plus c^T b."""
+    """Exact F(b) (Eq. 1, QUBO) for a CSR Q: sum over stored (i, j, q) of q b_i b_j, plus c^T b."""
     b = np.asarray(b, dtype=np.int64)
     rows = np.repeat(np.arange(n), np.diff(np.asarray(rowptr)))
     col = np.asarray(col, dtype=np.int64)
@@ -119,7 +119,7 @@ def objective_csr(n, rowptr, col, val, c, b):
 
 
 def multilinear(A, cp, x):
-    """Closed form of the multilinear extension, ``f(x) = 1/2 x^T A x + c'^T x``."""
+    """Closed form of the multilinear extension (Def. 2.2, Prop. 2.4), ``f(x) = 1/2 x^T A x + c'^T x``."""
     x = np.asarray(x, dtype=np.float64)
     return 0.5 * x @ (A @ x) + cp @ x
 
@@ -128,11 +128,12 @@ def multilinear(A, cp, x):
 # Lagrangian (section 3.1) with g(x) = x^2 - x (section 4.2)
 # ----------------------------------------------------------------------------------------
 def g(x):
-    """Binarity constraint function g(x) = x^2 - x (zero exactly at 0 and 1)."""
+    """Binarity constraint function g(x) = x^2 - x of section 4.2 (zero exactly at 0 and 1)."""
     return x * x - x
 
 
 def g_prime(x):
+    """g'(x) = 2x - 1 (section 4.2's g), the y-weighted term of dL/dx in Algorithm 1."""
     return 2.0 * x - 1.0
 
 
@@ -150,7 +151,8 @@ def g_entropy(x):
 
 
 def g_entropy_prime(x):
-    """log(x / (1 - x)), unbounded at 0 and 1: taken at x clamped to [ENTROPY_EPS, 1 - ENTROPY_EPS]."""
+    """Derivative of the entropy g of section 3.1, log(x / (1 - x)), unbounded at 0 and 1: taken at
+    x clamped to [ENTROPY_EPS, 1 - ENTROPY_EPS]."""
     xc = np.clip(np.asarray(x, dtype=np.float64), ENTROPY_EPS, 1.0 - ENTROPY_EPS)
     return np.log(xc) - np.log1p(-xc)
 
@@ -295,12 +297,13 @@ def certificate(A, cp, ybar, x):
 
 
 def round_bits(X):
-    """Binary candidate of each restart: b_i = [x_i > 1/2] (ties go to 0, the x <= 1/2 side)."""
+    """Rounding of section 4.2: b_i = [x_i > 1/2] for each restart (ties go to 0, the x <= 1/2 side)."""
     return (np.asarray(X) > 0.5).astype(np.uint8)
 
 
 def eval_points(T, K):
-    """Iteration counts t at which candidates are evaluated: K, 2K, ... and T (never t=0)."""
+    """Iteration counts t at which candidates are evaluated (best retention of section 4.2, on
+    the schedule this implementation reads into it): K, 2K, ... and T (never t=0)."""
     pts = list(range(K, T + 1, K))
     if T > 0 and (not pts or pts[-1] != T):
         pts.append(T)
@@ -375,7 +378,8 @@ def run(Q, c, restarts, iters, alpha, beta, ybar, delta=0.01, grad_tol=None, eva
 # exhaustive minimum (Lemma 2.3: the minimum over the box is attained at a vertex)
 # ----------------------------------------------------------------------------------------
 def brute_force(Q, c, chunk=1 << 15):
-    """min F over all 2^n binary points (n <= 24), and every minimiser (as an array of ints)."""
+    """min F over all 2^n binary points (n <= 24; Lemma 2.3: the box minimum is attained there),
+    and every minimiser (as an array of ints)."""
     Q = np.asarray(Q, dtype=np.int64)
     n = Q.shape[0]
     if n > 24:
