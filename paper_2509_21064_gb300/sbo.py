@@ -26,8 +26,10 @@ DUAL_COORDINATE, DUAL_SINGLE = 0, 1
 KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR, KERNEL_MAXK = 0, 1, 2, 3, 4, 5
 
 # every symbol include/sbo.h declares
-EXPORTS = ["sbo_create_dense", "sbo_create_dense_i8", "sbo_create_csr", "sbo_create_maxkcut", "sbo_gda_start", "sbo_gda_start_xy", "sbo_gda_run", "sbo_gda", "sbo_sync",
-           "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace", "sbo_lagrangian", "sbo_lagrangian_noalloc", "sbo_dual_bound",
+EXPORTS = ["sbo_create_dense", "sbo_create_dense_i8", "sbo_create_csr", "sbo_create_maxkcut",
+           "sbo_gda_start", "sbo_gda_start_xy", "sbo_gda_run", "sbo_gda", "sbo_sync",
+           "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace",
+           "sbo_lagrangian", "sbo_lagrangian_noalloc", "sbo_dual_bound",
            "sbo_set_option", "sbo_info", "sbo_launch_count", "sbo_destroy", "sbo_last_error", "sbo_version",
            "sbo_group_create", "sbo_group_start", "sbo_group_run", "sbo_group_sync", "sbo_group_set_option",
            "sbo_group_launch_count", "sbo_group_destroy"]
