@@ -111,3 +111,30 @@ def test_run_finds_the_brute_force_max_k_cut_of_small_graphs():
                       eval_every=10, seed=seed)
         assert out["F_star"] == -best
         assert K.cut_value(i, j, w, out["parts_star"]) == best
+
+
+def test_hand_worked_step_takes_both_updates_at_the_old_point():
+    """One step worked by hand (k = 3, two vertices joined by one edge of weight 1; the updates of
+    section 3.2 / Eq. 5, simultaneous):
+
+    Z_:,0 = (0, ln 2, ln 5)  ->  s0 = softmax = (1, 2, 5)/8;   y0 = 1
+    Z_:,1 = (ln 3, 0, ln 4)  ->  s1 = (3, 1, 4)/8;             y1 = 2
+    dL/dX_:,i = 2 (W X)_i + 2 y_i s_i:   h0 = 2 s1 + 2 s0 = (1, 3/4, 9/4),
+                                         h1 = 2 s0 + 4 s1 = (7/4, 1, 13/4)
+    dL/dZ_:,i = s_i * (h_i - <s_i, h_i>):  <s0, h0> = 55/32, <s1, h1> = 77/32
+        dZ0 = (-23/256, -31/128, 85/256),   dZ1 = (-63/256, -45/256, 27/64)
+    g_i = |s_i|^2 - 1:  g0 = 30/64 - 1 = -17/32,  g1 = 26/64 - 1 = -19/32
+    alpha = 1/2, beta = 1/4:  Z' - Z = -alpha dZ,  y' = y + beta g(s) at the OLD point:
+        y0' = 1 - 17/128 = 111/128,  y1' = 2 - 19/128 = 237/128.
+    Taking the dual step at the new point softmax(Z') instead changes y' by about 1e-2."""
+    Wm = K.weight_matrix(2, np.array([0]), np.array([1]), np.array([1]))
+    Z = np.array([[[0.0, np.log(2.0), np.log(5.0)], [np.log(3.0), 0.0, np.log(4.0)]]])
+    Y = np.array([[1.0, 2.0]])
+    Zn, Yn, DZ = K.gda_step_k(Wm, Z, Y, 0.5, 0.25)
+    dz = np.array([[[-23 / 256, -31 / 128, 85 / 256], [-63 / 256, -45 / 256, 27 / 64]]])
+    assert np.max(np.abs(DZ - dz)) <= 1e-12
+    assert np.max(np.abs((Zn - Z) + 0.5 * dz)) <= 1e-12
+    assert np.max(np.abs(Yn - np.array([[111 / 128, 237 / 128]]))) <= 1e-12
+    # the same step at the new point would be visibly different: the pin can tell them apart
+    Gnew = np.sum(K.softmax(Zn) ** 2, axis=2) - 1.0
+    assert np.min(np.abs((Y + 0.25 * Gnew) - Yn)) > 1e-3
