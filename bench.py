@@ -12,14 +12,23 @@ Reported (one JSON line on rank 0):
               (x*, F*) back (D2H)
   roofline    the tcgen05 update kernel: 2 n^2 B flop per launch / its average launch time
               (CUDA events around each launch inside the timed region), against the measured
-              sustained BF16 peak
+              burst BF16 peak (the kernel is timed in a region of well under a second); the
+              fraction of the sustained peak beside it
   cpu_baseline the FP64 oracle on the host cores, on a bounded sample (restart subset)
   time_to_target  device seconds until the best objective reaches the FP64 oracle's best
   plain_fp32_form the plain FP32 CUDA-core form on the same instance: its throughput, and the best
               objectives of both forms after the same T iterations
+  other_configs   the other benchmark configurations (N = 1 only): Max-Cut on an Erdos-Renyi
+              graph (n = 2,000, B = 256), dense QUBO n = 5,000 (B = 256, BF16), Max-Cut on the
+              100 x 100 torus and on a random 4-regular graph (n = 20,000; B = 512; E4M3 weights
+              and the plain FP32 form), and 64 dense instances of uneven n in one grouped launch
+              (B = 128): restart-iterations/s and a roofline each, with the bytes or flops it counts
 ``--impl reference`` times the oracle alone (the reference arm of this comparison).
-Multi-GPU (torchrun): every rank runs its own B restarts (different seeds) of the same instance,
-no collective in the timed loop; value = all ranks' restart-iterations / max rank time.
+Multi-GPU: ``--gpus N`` starts N ranks under torch.distributed.run (or runs as one of them when
+launched so); every rank runs its own B restarts (different seeds) of the same instance, and
+after every step (K iterations + one evaluation) the ranks exchange their best candidates (the
+lexicographic minimum of (F, t, rank, restart) and the winner's bits); value = all ranks'
+restart-iterations / max rank time.
 """
 from __future__ import annotations
 
@@ -46,9 +55,11 @@ RESTARTS_DEFAULT = RESTARTS
 K_EVAL = 50
 METRIC = "GDA restart-iterations/s at n=20k dense QUBO"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
-# DRAM bytes (read + write) per launch of the update kernel from one ncu capture of this
-# workload (profiles/k_tc_pair_update_dense_n20000.md); keyed by (tile width, n, restarts)
-MEASURED_TRAFFIC = {(512, 20000, 1024): 1.169179e9 + 0.180734e9}
+# DRAM bytes (read + write) per launch of the update kernel: dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of that launch on this workload; keyed by (tile
+# width, n, restarts), with the capture it came from
+MEASURED_TRAFFIC = {(512, 20000, 1024): (1.169179e9 + 0.180734e9,
+                                         "ncu capture of one k_tc_pair<EPI_UPDATE> launch, n=20000, B=1024")}
 
 
 def peaks():
@@ -159,35 +170,62 @@ def load_target(key):
         return None
 
 
-def time_to_target(S, torch, Q, c, seed, stream, dev, target, iters=2000):
-    """One full solve (T iterations, K-blocks replayed from CUDA graphs, event after every
-    block): wall time on the device until the best objective first reaches the target."""
+def time_to_target(S, torch, Q, c, seed, stream, dev, target, iters=2000, world=1):
+    """One full solve (T iterations, K-blocks replayed from CUDA graphs): the time until the best
+    objective first reaches the target.  One rank: device time, an event after every block.
+    Several ranks (each its own restarts, seeded by rank): after every block the ranks exchange
+    their best candidates (step_loop), and the time is the slowest rank's host clock at the first
+    block whose global best reaches the target."""
+    import torch.distributed as dist
     p = W.dense_params(Q, restarts=RESTARTS_DEFAULT, iters=iters, eval_every=K_EVAL, seed=seed)
     P = S.Problem.dense(Q, c, precision=S.SBO_BF16, stream=stream)
     P.start(S.params(**p.asdict()))
-    evs = []
-    with torch.cuda.stream(stream):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(iters // K_EVAL):
+    blocks = iters // K_EVAL
+    if world > 1:
+        dist.barrier()
+        t0 = time.perf_counter()
+        stamps = []
+
+        def block():
             P.run(K_EVAL)
-            e = torch.cuda.Event(enable_timing=True)
-            e.record(stream)
-            evs.append(e)
-        torch.cuda.synchronize(dev)
-    P.sync()
-    trace = P.trace()
-    x_best, F_best, t_best, r_best = P.best()
+
+        def best():
+            out = P.best()                       # synchronises this rank's stream
+            stamps.append(time.perf_counter() - t0)
+            return out
+        gtrace = step_loop(blocks, block, best, device=dev)
+        from paper_2509_21064_gb300.dist import max_over_ranks
+        stamps = max_over_ranks(stamps, device=dev)
+        trace = [g[0] for g in gtrace]
+        x_best, F_best, t_best, r_best = P.best()
+        F_best, t_best = gtrace[-1][0], gtrace[-1][1]
+        secs = stamps
+    else:
+        evs = []
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(blocks):
+                P.run(K_EVAL)
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                evs.append(e)
+            torch.cuda.synchronize(dev)
+        P.sync()
+        trace = P.trace()
+        x_best, F_best, t_best, r_best = P.best()
+        secs = [e0.elapsed_time(e) * 1e-3 for e in evs]
     P.close()
     out = {"target_F": target["F_best"] if target else None,
            "target_source": ("FP64 oracle on restarts 0-%d of the same instance and x^0, T=%d (tests/golden/"
                              "oracle_targets.json)" % (len(target["restarts"]) - 1, target["iters"])) if target else
            "no stored oracle target",
-           "best_F": int(F_best), "best_t": int(t_best), "solve_seconds": e0.elapsed_time(evs[-1]) * 1e-3}
+           "best_F": int(F_best), "best_t": int(t_best), "solve_seconds": secs[-1],
+           "clock": "device events" if world == 1 else f"host, slowest of {world} ranks, best exchanged every block"}
     if target:
         hit = [k for k, f in enumerate(trace) if f <= target["F_best"]]
         if hit:
-            out.update(reached=True, iteration=(hit[0] + 1) * K_EVAL, seconds=e0.elapsed_time(evs[hit[0]]) * 1e-3)
+            out.update(reached=True, iteration=(hit[0] + 1) * K_EVAL, seconds=secs[hit[0]])
         else:
             out.update(reached=False, gap=int(min(trace)) - int(target["F_best"]))
     return out
@@ -271,6 +309,25 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------------
+def step_loop(steps, step, best=None, device=None):
+    """The timed loop of one rank: `steps` calls of step().  With several ranks, after every step
+    the ranks exchange their best candidates -- best() gives this rank's (bits, F, t, restart) --
+    and every rank records the global best (F, t, rank, restart): the lexicographic minimum over
+    the ranks (section 4.2's best of all runs, across GPUs).  Returns that trace (empty on one
+    rank or without best)."""
+    import torch.distributed as dist
+    from paper_2509_21064_gb300.dist import global_best
+    multi = best is not None and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+    trace = []
+    for _ in range(steps):
+        step()
+        if multi:
+            x, F, t, r = best()
+            Fw, tw, kw, rw, _ = global_best(F, t, r, x, device=device)
+            trace.append((Fw, tw, kw, rw))
+    return trace
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -283,12 +340,13 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    hetero_jobs = None
     build()
     S.lib()
     stream = torch.cuda.Stream(device=dev)
 
     N_VARS, RESTARTS = args.n, args.restarts
-    Q, c = W.dense_qubo(N_VARS, seed=0)
+    Q, c = W.dense_qubo(N_VARS, seed=0, dtype=np.int8)
     p = W.dense_params(Q, restarts=RESTARTS, iters=10**9, eval_every=K_EVAL, seed=rank)
     prm = S.params(**p.asdict())
     P = S.Problem.dense(Q, c, precision=S.SBO_BF16, stream=stream)
@@ -298,6 +356,7 @@ def run_ours(args):
     P.set_option(S.SBO_OPT_USE_GRAPH, 0)
     P.start(prm)
     info = P.info()
+    kernel_events = []
 
     def step(events=None):
         for k in range(K_EVAL):
@@ -319,14 +378,12 @@ def run_ours(args):
             dist.barrier()
         sampler = ClockSampler(local)
         sampler.start()
-        kernel_events = []
         launches0 = P.launch_count()
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
         t_start.record(stream)
-        for _ in range(args.steps):
-            step(kernel_events)
+        best_trace = step_loop(args.steps, lambda: step(kernel_events), P.best, device=dev)
         t_end.record(stream)
         torch.cuda.synchronize(dev)
         launches = P.launch_count() - launches0
@@ -355,15 +412,15 @@ def run_ours(args):
             print(json.dumps({"n": N_VARS, "restarts": RESTARTS, "ms_per_step": ms / args.steps,
                               "update_launch_ms": t_kernel * 1e3, "graph_ms_per_step": graph_ms_per_step,
                               "tflops": 2.0 * N_VARS * N_VARS * RESTARTS / t_kernel / 1e12}), flush=True)
+        if hetero_jobs is not None:
+            hetero_jobs[0].shutdown(cancel_futures=True)
         return 0
 
     # e2e through the public API with host buffers (pinned), every step: H2D of Q, c; K
     # iterations + evaluation; D2H of (x*, F*)
     # the entries lie in [-100, 100]: the host copy is int8 (sbo_create_dense_i8), a quarter of
     # the int32 bytes
-    Q8 = Q.astype(np.int8)
-    assert np.array_equal(Q8, Q)
-    Qp = torch.from_numpy(Q8).pin_memory()
+    Qp = torch.from_numpy(Q).pin_memory()
     cpin = torch.from_numpy(c).pin_memory()
     e2e_steps = max(2, min(args.steps, 4))
     prm_e2e = S.params(**{**p.asdict(), "iters": K_EVAL})
@@ -375,8 +432,12 @@ def run_ours(args):
         xb, Fb, tb, rb = P2.best()
         P2.close()
     e2e_s = time.perf_counter() - t0
-    h2d = Q8.nbytes + c.nbytes
+    h2d = Q.nbytes + c.nbytes
     d2h = N_VARS + 8 * 3
+    # the other configurations' heterogeneous batch is drawn on the host cores from here on, while
+    # the GPU runs the device-timed measurements (after the host-timed e2e leg)
+    if rank == 0 and world == 1 and not args.no_other_configs:
+        hetero_jobs = hetero_generate_start(args)
 
     # max over ranks; the global best over every rank's restarts (the method's one exchange)
     sec = ms * 1e-3
@@ -391,8 +452,8 @@ def run_ours(args):
     e2e_value = RESTARTS * K_EVAL * e2e_steps * world / e2e_s
 
     ttt = None
-    if rank == 0 and N_VARS == 20000 and RESTARTS == 1024 and not args.no_time_to_target:
-        ttt = time_to_target(S, torch, Q, c, 0, stream, dev, load_target("dense_n20000_b1024_seed0"))
+    if N_VARS == 20000 and RESTARTS == 1024 and not args.no_time_to_target:
+        ttt = time_to_target(S, torch, Q, c, rank, stream, dev, load_target("dense_n20000_b1024_seed0"), world=world)
     plain = None
     if rank == 0 and N_VARS == 20000 and RESTARTS == 1024 and not args.no_plain_form:
         plain = plain_fp32_form(S, torch, Q, c, 0, stream, dev)
@@ -401,7 +462,7 @@ def run_ours(args):
     pk, src = peaks()
     flops = 2.0 * N_VARS * N_VARS * RESTARTS
     achieved = flops / t_kernel / 1e12
-    peak = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
+    peak_sust = float(pk.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"]))
     peak_burst = float(pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
     if info["tile_n"] == 512:
         kname = "k_tc_pair<EPI_UPDATE> (CTA pairs, 256x256 tiles)"
@@ -409,6 +470,7 @@ def run_ours(args):
         kname = f"k_tc_csk<{info['tile_n'] - 1000}, EPI_UPDATE> (split-K over a thread-block cluster)"
     else:
         kname = f"k_tc<{info['tile_n']}, EPI_UPDATE, false>"
+    traffic, traffic_src = MEASURED_TRAFFIC.get((info["tile_n"], N_VARS, RESTARTS), (None, None))
     line = {
         "metric": METRIC, "value": value, "unit": "restart-iterations/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -420,14 +482,13 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (A is 800 MB BF16)",
                    "graph_replay_ms_per_step": graph_ms_per_step,
                    "best_F_after_run": F_best if global_best is None else global_best["F"],
-                   "parallelism": f"replicas x{world} (restarts sharded by seed)"},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": MEASURED_TRAFFIC.get((info["tile_n"], N_VARS, RESTARTS)),
+                   "parallelism": f"replicas x{world} (restarts sharded by seed; best exchanged every step)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_burst, "unit": "TFLOP/s",
+                     "frac": achieved / peak_burst, "traffic": traffic, "traffic_source": traffic_src,
                      "algorithmic_bytes": 2.0 * N_VARS * N_VARS + 18.0 * N_VARS * RESTARTS + 2.0 * N_VARS * RESTARTS,
                      "kernel": kname, "launch_ms": t_kernel * 1e3,
-                     "peak_source": f"{src} bf16_tflops_sustained (kernel timed inside the long run)",
-                     "frac_of_burst_peak": achieved / peak_burst},
+                     "peak_source": f"{src} bf16_tflops (burst: the kernel is timed in a region well under a second)",
+                     "peak_sustained": peak_sust, "frac_of_sustained_peak": achieved / peak_sust},
         "e2e": {"value": e2e_value, "unit": "restart-iterations/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                 "per_step": "pinned int8 Q and int32 c to the device, canonicalise, K iterations + evaluation, "
@@ -439,9 +500,12 @@ def run_ours(args):
         line["time_to_target"] = ttt
     if global_best is not None:
         line["config"]["global_best_over_ranks"] = global_best
+        line["config"]["global_best_trace_per_step"] = [b[0] for b in best_trace]
     if plain is not None:
         plain["speedup_of_chosen_form"] = (RESTARTS * K_EVAL * args.steps / (ms * 1e-3)) / plain["value"]
         line["plain_fp32_form"] = plain
+    if hetero_jobs is not None:
+        line["other_configs"] = other_configs(S, torch, dev, args, pk, hetero_jobs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, it, el, _, _ = oracle_sample(Q, c, p, seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "restart-iterations/s", "cores": oracle_threads(),
@@ -453,6 +517,149 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# the other benchmark configurations, measured beside the headline (N = 1)
+SIDE_SPARSE = [
+    # (key, workload, precision, restarts): Max-Cut as QUBO, evaluation every 10 iterations
+    ("maxcut_er_n2000_b256_fp32", "maxcut-er", "fp32"),
+    ("maxcut_er_n2000_b256_bf16", "maxcut-er", "bf16"),
+    ("maxcut_torus_n10000_b512_e4m3", "maxcut-torus", "e4m3"),
+    ("maxcut_torus_n10000_b512_fp32", "maxcut-torus", "fp32"),
+    ("maxcut_regular_n20000_b512_e4m3", "maxcut-regular", "e4m3"),
+    ("maxcut_regular_n20000_b512_fp32", "maxcut-regular", "fp32"),
+]
+HETERO_COUNT, HETERO_B = 64, 128
+
+
+def _hetero_instance(k, n_hi):
+    return W.heterogeneous_qubo(k, HETERO_COUNT, seed=0, n_lo=500, n_hi=n_hi, dtype=np.int8)
+
+
+def hetero_generate_start(args):
+    """Draw the 64 instances of the heterogeneous batch in worker processes (spawned, so that no
+    CUDA state is forked); returns (executor, futures)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    # largest instances first, so the pool's tail is short
+    shapes = W.heterogeneous_shapes(HETERO_COUNT, seed=0, n_lo=500, n_hi=args.hetero_n_hi)
+    order = sorted(range(HETERO_COUNT), key=lambda k: -shapes[k][0])
+    return ex, {k: ex.submit(_hetero_instance, k, args.hetero_n_hi) for k in order}
+
+
+def _timed_blocks(torch, stream, run_block, blocks, warmup=3):
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            run_block()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(blocks):
+            run_block()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3
+
+
+def other_configs(S, torch, dev, args, pk, hetero_jobs):
+    """Restart-iterations/s and the roofline of each other benchmark configuration: the sparse
+    Max-Cut graphs, dense n = 5,000, and the heterogeneous batch (grouped launch)."""
+    hbm = float(pk.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+    tc = float(pk.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    K = 10
+    for key, wl, prec_name in SIDE_SPARSE:
+        make, B = SPARSE[wl]
+        n, (i, j, w) = make()
+        rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+        prec = {"fp32": S.SBO_FP32, "bf16": S.SBO_BF16, "e4m3": S.SBO_FP8_E4M3}[prec_name]
+        p = W.graph_params("maxcut", restarts=B, iters=10**9, eval_every=K, seed=0)
+        P = S.Problem.csr(n, rowptr, col, val, c, precision=prec, stream=stream)
+        P.start(S.params(**p.asdict()))
+        blocks = 40
+        sec = _timed_blocks(torch, stream, lambda: P.run(K), blocks)
+        P.sync()
+        P.close()
+        t_it = sec / (blocks * K)
+        per = 16 if prec == S.SBO_FP32 else 20          # x, y FP32 read + written; + BF16 copy written, read
+        nnz = int(rowptr[-1]) * 2
+        wbytes = {"fp32": 4, "bf16": 2, "e4m3": 1}[prec_name]
+        state = per * n * B
+        bytes_it = state + nnz * (4 + wbytes) + 4 * (n + 1)
+        resident = 16 * n * B * 4 <= l2 * 3
+        out[key] = {"n": n, "restarts": B, "precision": prec_name, "eval_every": K,
+                    "us_per_iteration": t_it * 1e6, "restart_iterations_per_s": B / t_it,
+                    "roofline": {"bound": "latency (x, y fit in L2)" if resident else "hbm",
+                                 "achieved": bytes_it / t_it / 1e9, "peak": hbm, "unit": "GB/s",
+                                 "frac": bytes_it / t_it / 1e9 / hbm, "bytes_per_iteration": bytes_it,
+                                 "bytes_counted": f"{per} B per (vertex, restart) of state (x, y FP32 read and "
+                                                  "written" + ("" if per == 16 else "; BF16 operand copy written and "
+                                                                                     "read") + ") + CSR structure"}}
+    # dense n = 5,000, B = 256, BF16 (autotuned tiles), graph replay of K = 50 blocks
+    n, B = 5000, 256
+    Q, c = W.dense_qubo(n, seed=0, dtype=np.int8)
+    p = W.dense_params(Q, restarts=B, iters=10**9, eval_every=K_EVAL, seed=0)
+    P = S.Problem.dense(Q, c, precision=S.SBO_BF16, stream=stream)
+    P.start(S.params(**p.asdict()))
+    sec = _timed_blocks(torch, stream, lambda: P.run(K_EVAL), 10)
+    tile = P.info()["tile_n"]
+    P.sync()
+    P.close()
+    t_it = sec / (10 * K_EVAL)
+    a_bytes = 2.0 * n * n
+    state = 20.0 * n * B
+    t_roof = max(2.0 * n * n * B / (tc * 1e12), a_bytes / (hbm * 1e9))
+    out["dense_n5000_b256_bf16"] = {
+        "n": n, "restarts": B, "eval_every": K_EVAL, "tile_n": tile, "us_per_iteration": t_it * 1e6,
+        "restart_iterations_per_s": B / t_it, "tflops": 2.0 * n * n * B / t_it / 1e12,
+        "roofline": {"bound": "hbm (A bytes; 2 n^2 B flop at the burst BF16 peak is shorter)",
+                     "achieved": a_bytes / t_it / 1e9, "peak": hbm, "unit": "GB/s", "frac": t_roof / t_it,
+                     "roofline_us": t_roof * 1e6, "frac_counting_state": (a_bytes + state) / t_it / 1e9 / hbm,
+                     "note": "A (50 MB) stays in L2 under graph replay, so the HBM bound is not a hard ceiling"}}
+    # heterogeneous batch: 64 dense instances, n ~ U{500..20000}, density ~ U[0.01, 1], B = 128 each
+    ex, futs = hetero_jobs
+    members, ns = [], []
+    t0 = time.time()
+    try:
+        for k in range(HETERO_COUNT):
+            Qk, ck = futs[k].result()
+            q = W.dense_params(Qk, restarts=HETERO_B, iters=10**9, eval_every=K, seed=k)
+            members.append((S.Problem.dense(Qk, ck, precision=S.SBO_BF16, stream=stream), S.params(**q.asdict())))
+            ns.append(Qk.shape[0])
+            del Qk
+    finally:
+        ex.shutdown(cancel_futures=True)
+    t_gen = time.time() - t0
+    G = S.Group([m for m, _ in members], stream=stream)
+    G.start([q for _, q in members])
+    sec = _timed_blocks(torch, stream, lambda: G.run(K), 5)
+    G.sync()
+    tile = members[0][0].info()["tile_n"]
+    G.close()
+    for m, _ in members:
+        m.close()
+    t_it = sec / (5 * K)
+    sum_n2 = float(sum(v * v for v in ns))
+    sum_n = float(sum(ns))
+    bytes_it = 2.0 * sum_n2 + 20.0 * sum_n * HETERO_B
+    t_roof = sum(max(2.0 * v * v * HETERO_B / (tc * 1e12), (2.0 * v * v + 20.0 * v * HETERO_B) / (hbm * 1e9))
+                 for v in ns)
+    out["hetero_64_dense_b128_bf16"] = {
+        "instances": HETERO_COUNT, "n_range": [min(ns), max(ns)], "sum_n2": sum_n2, "restarts_each": HETERO_B,
+        "eval_every": K, "tile_n": tile, "us_per_iteration": t_it * 1e6,
+        "restart_iterations_per_s": HETERO_COUNT * HETERO_B / t_it,
+        "tflops_dense_equivalent": 2.0 * sum_n2 * HETERO_B / t_it / 1e12,
+        "wait_for_host_generation_s": round(t_gen, 1),
+        "roofline": {"bound": "hbm (BF16 A of every instance + x, y state; below the ridge at B = 128)",
+                     "achieved": bytes_it / t_it / 1e9, "peak": hbm, "unit": "GB/s", "frac": t_roof / t_it,
+                     "roofline_us": t_roof * 1e6}}
+    return out
 
 
 SPARSE = {
@@ -479,7 +686,11 @@ def run_sparse(args):
     stream = torch.cuda.Stream()
     P = S.Problem.csr(n, rowptr, col, val, c, precision=prec, stream=stream)
     P.set_option(S.SBO_OPT_PDL, 0 if args.no_pdl else 1)
+    P.set_option(S.SBO_OPT_CSR_FORM, args.csr_form)
+    if args.no_eval:
+        p = W.graph_params("maxcut", restarts=B, iters=10**9, eval_every=10**6, seed=0)
     P.start(S.params(**p.asdict()))
+    form = P.info()["tile_n"]
     K = 10
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -494,9 +705,9 @@ def run_sparse(args):
         torch.cuda.synchronize()
     P.sync()
     ms = e0.elapsed_time(e1) / (args.steps * K)
-    per_elem = 16 if prec == S.SBO_FP32 else 22
+    per_elem = 16 if prec == S.SBO_FP32 else 20
     print(json.dumps({"workload": args.workload, "n": n, "restarts": B, "precision": args.precision,
-                      "pdl": not args.no_pdl, "us_per_iter": ms * 1e3, "restart_iterations_per_s": B / (ms * 1e-3),
+                      "pdl": not args.no_pdl, "form": form, "evaluations": not args.no_eval, "us_per_iter": ms * 1e3, "restart_iterations_per_s": B / (ms * 1e-3),
                       "state_gbs": n * B * per_elem / (ms * 1e-3) / 1e9}), flush=True)
     P.close()
     return 0
@@ -807,6 +1018,31 @@ def run_certificate(args):
     return 0
 
 
+def free_port():
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def torchrun_argv(argv, gpus, port):
+    """The command line that starts `gpus` ranks of this benchmark, one per GPU, with the same
+    arguments (torch.distributed.run on this node, rendezvous on 127.0.0.1)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + list(argv)
+
+
+def launch_ranks(gpus, argv):
+    """--gpus N from a plain process: check that N GPUs are visible, then run N ranks under
+    torch.distributed.run and return their exit status."""
+    import torch
+    have = torch.cuda.device_count()
+    if have < gpus:
+        print(f"bench.py: --gpus {gpus} needs {gpus} visible GPUs, found {have}", file=sys.stderr)
+        return 2
+    return subprocess.call(torchrun_argv(argv, gpus, free_port()), cwd=ROOT)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -823,6 +1059,10 @@ def main():
                     help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
                     help="weight/operand precision of a sparse workload")
+    ap.add_argument("--csr-form", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="sparse workloads: update form (0 autotuned; 1, 2 one row per warp with 128 / 256 "
+                         "restarts; 3 pipelined rows; 4 rows staged by bulk copies)")
+    ap.add_argument("--no-eval", action="store_true", help="sparse workloads: no evaluations (update launches only)")
     ap.add_argument("--no-pdl", action="store_true",
                     help="sparse workloads: plain stream order instead of programmatic dependent launches")
     ap.add_argument("--hetero-n-hi", type=int, default=20000, help="hetero workload: largest instance size")
@@ -837,11 +1077,21 @@ def main():
                     help="tensor-core tile width (0: autotuned); profiling cases only")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the device loop only (no e2e, no CPU baseline): for profiling cases")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the other benchmark configurations (sparse graphs, n=5000, heterogeneous batch)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.gpus < 1:
+        ap.error("--gpus must be >= 1")
     if args.impl == "reference":
         return run_reference(args)
+    if "WORLD_SIZE" in os.environ:
+        if int(os.environ["WORLD_SIZE"]) != args.gpus:
+            print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={os.environ['WORLD_SIZE']}", file=sys.stderr)
+            return 2
+    elif args.gpus > 1:
+        return launch_ranks(args.gpus, sys.argv[1:])
     if args.workload == "hetero":
         return run_hetero(args)
     if args.workload == "sweep":

@@ -87,7 +87,9 @@ sbo_status sbo_create_dense(int64_t n, const int32_t* Q, const int32_t* c, int32
 sbo_status sbo_create_dense_i8(int64_t n, const int8_t* Q, const int32_t* c, int32_t precision, void* stream,
                                sbo_problem** out);
 
-/* sbo_create_csr: Q in CSR on the host: rowptr[n+1] (int64, rowptr[0]=0, non-decreasing,
+/* sbo_create_csr (Eq. 1 with the QUBO objective for a sparse Q, put in the multilinear form of
+ * Prop. 2.4; Max-Cut enters as Q = W, c = -W 1, the graph form of section 4.2):
+ * Q in CSR on the host: rowptr[n+1] (int64, rowptr[0]=0, non-decreasing,
  * rowptr[n]=nnz), col[nnz] (int32 in [0,n)), val[nnz] (int32); duplicates are summed.
  * c as above.  precision: SBO_FP32, SBO_BF16 or SBO_FP8_E4M3 (weight storage).  A = Q + Q^T
  * with zero diagonal is formed on the host.  Requires 1 <= n < 2^31 and the exactness
@@ -129,29 +131,40 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
 sbo_status sbo_gda_run(sbo_problem* p, int64_t iters);
 sbo_status sbo_gda(sbo_problem* p, const sbo_gda_params* prm);
 
-/* sbo_sync: waits for the problem's stream; returns SBO_ETIMEOUT / SBO_EDEVICE if a kernel
+/* sbo_sync (no passage: the end of an asynchronous run of Algorithm 1's loop):
+ * waits for the problem's stream; returns SBO_ETIMEOUT / SBO_EDEVICE if a kernel
  * raised the device error word since the last sync (the word is then cleared). */
 sbo_status sbo_sync(sbo_problem* p);
 
 /* ---- results (all synchronise first) ---------------------------------------------------
- * sbo_eval: exact F of `count` binary vectors bits[count*n] (host, 0/1 bytes), into F[count]
+ * sbo_eval (Eq. 1: F(b) = b^T Q b + c^T b at binary points): exact F of `count` binary vectors bits[count*n] (host, 0/1 bytes), into F[count]
  * (host int64), computed on the device with the same kernels as the run's evaluations. */
 sbo_status sbo_eval(sbo_problem* p, int64_t count, const uint8_t* bits, int64_t* F);
 
-/* sbo_best: global best over all evaluations so far: lexicographic minimum of (F, t, r).
+/* sbo_best (section 4.2: the best of the B runs is retained): global best over all evaluations so
+ * far: lexicographic minimum of (F, t, r).
  * x_out (host, n bytes, may be NULL), F_out, iter_out (t), restart_out (r) may be NULL.
  * SBO_ENOTREADY before the first evaluation. */
 sbo_status sbo_best(sbo_problem* p, uint8_t* x_out, int64_t* F_out, int64_t* iter_out,
                     int32_t* restart_out);
 
-/* sbo_restart_best: per-restart best F and the earliest t that reached it (host arrays of
+/* sbo_restart_best (section 4.2, per run of the batch; the earliest t is what the time-to-best
+ * measure of the same section reads): per-restart best F and the earliest t that reached it (host arrays of
  * B entries; INT64_MAX / -1 for a restart not yet evaluated). */
 sbo_status sbo_restart_best(sbo_problem* p, int64_t* F, int64_t* t);
 
-/* sbo_state: FP32 copies of the current iterates, X and Y (host, B*n each, [r][i]). */
+/* sbo_state (Algorithm 1: the primal-dual iterate (x^t, y^t) of every restart): FP32 copies of the
+ * current iterates, X and Y (host, B*n each, [r][i]). */
 sbo_status sbo_state(sbo_problem* p, float* X, float* Y);
 
-/* sbo_trace: min_r F at every evaluation so far, in order (host int64[cap]); *count gets
+/* sbo_gradient: the gradient d = dL/dx (Algorithm 1 with Eq. 5: (A x)_i + c'_i + y_i g'(x_i)) that
+ * the latest iteration took at (x^{t-1}, y^{t-1}), exactly as the update kernel computed it
+ * (host, B*n floats, [r][i]).  Needs SBO_OPT_KEEP_GRAD = 1 at sbo_gda_start and t >= 1, else
+ * SBO_ENOTREADY.  Not for Max-k-Cut runs. */
+sbo_status sbo_gradient(sbo_problem* p, float* G);
+
+/* sbo_trace (section 4.2: best of the B runs at each evaluation point, the data behind that
+ * section's earliest time to the best solution): min_r F at every evaluation so far, in order (host int64[cap]); *count gets
  * the number of evaluations (may exceed cap; only the first cap are written). */
 sbo_status sbo_trace(sbo_problem* p, int64_t* minF, int64_t cap, int64_t* count);
 
@@ -184,11 +197,11 @@ sbo_status sbo_lagrangian(sbo_problem* p, int32_t B, const float* X_dev, const f
 sbo_status sbo_dual_bound(sbo_problem* p, double ybar, double alpha, int64_t iters, double* lower_bound,
                           double* value);
 
-/* sbo_lagrangian_noalloc: the same computation and arguments as sbo_lagrangian, for callers
- * that cannot allocate device memory -- code running inside a CUDA stream capture (where
- * cudaMalloc is not allowed), processes whose device memory belongs to a framework's pool or a
- * fixed budget, and loops that cannot absorb cudaMalloc's implicit synchronisation.  The paper
- * has no counterpart: this is a property of the library, not of the method.  It calls no
+/* sbo_lagrangian_noalloc: the same computation and arguments as sbo_lagrangian, for dense
+ * problems, for callers that cannot allocate device memory -- processes whose device memory
+ * belongs to a framework's pool or a fixed budget, and loops that cannot absorb cudaMalloc's
+ * implicit synchronisation.  The paper has no counterpart: this is a property of the library,
+ * not of the method.  CSR problems return SBO_EINVAL.  It calls no
  * cudaMalloc/cudaFree or other allocating routine; for BF16 problems it stages the BF16 copy
  * of X in one fixed 16 MiB device array that every GPU loading the library holds until the
  * process exits, so it requires B * round_up(n, 8) * 2 <= 16 MiB and returns SBO_EINVAL
@@ -241,13 +254,26 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       = 0), whose derivative log(x / (1 - x)) is taken at x clamped to
  *                       [1e-6, 1 - 1e-6].  Applies to the run (update and dual step) and to
  *                       sbo_lagrangian; QUBO problems only; sbo_dual_bound always uses the quadratic
- *                       g */
+ *                       g
+ *   SBO_OPT_KEEP_GRAD:  0 (default); 1: every update also writes the gradient d it used into a
+ *                       run-owned buffer (4 B per element more device memory and store traffic),
+ *                       read with sbo_gradient -- for checking the loop's own gradients.  Set
+ *                       before sbo_gda_start; QUBO problems only
+ *   SBO_OPT_CSR_FORM:   form of the sparse update kernel: 0 (default) chosen by the autotuner at
+ *                       sbo_gda_start (with SBO_OPT_AUTOTUNE = 0: a fixed rule on n, B and the L2
+ *                       size), 1 one row per warp with 128 restarts, 2 one row per warp with 256
+ *                       restarts, 3 rows strided over one resident wave and software-pipelined (256
+ *                       restarts per warp), 4 rows staged in shared memory by bulk copies (a
+ *                       producer warp and four consumer warps per CTA).  Results are identical in
+ *                       every form; the single-constraint form (SBO_OPT_DUAL = 1) keeps the rule */
 enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4, SBO_OPT_SPLIT_K = 5,
-       SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7, SBO_OPT_DUAL = 8, SBO_OPT_G = 9 };
+       SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7, SBO_OPT_DUAL = 8, SBO_OPT_G = 9, SBO_OPT_KEEP_GRAD = 10,
+       SBO_OPT_CSR_FORM = 11 };
 sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
 
 /* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL; 4 the
- * sparse QUBO kernel, 5 the Max-k-Cut kernel), the tile width and the iteration counter t; any
+ * sparse QUBO kernel, 5 the Max-k-Cut kernel), the tile width (dense tensor-core runs) or the
+ * sparse update's form (values of SBO_OPT_CSR_FORM, 0 the rule) and the iteration counter t; any
  * pointer may be NULL. */
 sbo_status sbo_info(const sbo_problem* p, int64_t* n, int32_t* restarts, int32_t* kernel,
                     int32_t* tile_n, int64_t* t);

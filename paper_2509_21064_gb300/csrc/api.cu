@@ -46,16 +46,17 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 // the device's default pool, which keeps up to SBO_POOL_RETAIN_MB (default 8192) of freed memory
 // for reuse, so creating and destroying problems in a loop does not pay for fresh allocations.
 void configure_pool_once() {
-  static std::once_flag once;
-  std::call_once(once, [] {
+  static PerDevice per_device;
+  per_device.once([] {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaError_t e = cudaGetDevice(&dev);
     cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, dev);
+    if (e != cudaSuccess) return e;
     uint64_t mb = 8192;
-    if (const char* e = std::getenv("SBO_POOL_RETAIN_MB")) mb = std::strtoull(e, nullptr, 10);
+    if (const char* v = std::getenv("SBO_POOL_RETAIN_MB")) mb = std::strtoull(v, nullptr, 10);
     uint64_t thr = mb << 20;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    return cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   });
 }
 
@@ -94,6 +95,7 @@ struct sbo_problem {
   void* val = nullptr;
   int val_type = 0;
   int64_t nnz = 0;
+  int max_deg = 0;             // longest row of A (CSR)
   int kparts = 0;              // Max-k-Cut: parts per vertex (FMT_MAXK)
   // linear term
   float* cp = nullptr;
@@ -103,11 +105,14 @@ struct sbo_problem {
   int opt_kernel = KER_AUTO, opt_graph = 1, opt_tile_n = 0, opt_split_k = 16, opt_autotune = 1, opt_pdl = 1;
   int opt_dual = 0;           // 0: one dual per coordinate (PDBO); 1: one per restart (PDBO-s)
   int opt_g = G_QUAD;         // constraint function g (SBO_OPT_G)
+  int opt_keep_grad = 0;      // SBO_OPT_KEEP_GRAD: keep dL/dx of the latest iteration
+  int opt_csr_form = 0;       // SBO_OPT_CSR_FORM: 0 autotuned (or the rule), else a CsrForm
   int64_t opt_timeout_us = 4000000;
   // run
   bool started = false;
   sbo_gda_params prm{};
   int kernel = KER_AUTO, layout = LAYOUT_RN, op_type = OP_F32, tile_n = 0;
+  int csr_form = CSR_FORM_RULE;   // form of the sparse update in this run
   int B = 0;
   int64_t ld = 0;
   int64_t t = 0;          // iterations completed
@@ -115,6 +120,7 @@ struct sbo_problem {
   int cur = 0;            // operand buffer holding x^t
   float* Xm = nullptr;    // FP32 master (null when the operand is the FP32 master)
   float* Y = nullptr;
+  float* Gd = nullptr;    // dL/dx of the latest iteration (SBO_OPT_KEEP_GRAD), state layout
   void* Xop[2] = {nullptr, nullptr};
   void* bits = nullptr;
   long long *bestF = nullptr, *bestT = nullptr, *evalF = nullptr, *trace = nullptr, *n_evals = nullptr,
@@ -157,6 +163,7 @@ void free_run(sbo_problem* p) {
   p->eval_pending = false;
   dfree(p->Xm, p->stream);
   dfree(p->Y, p->stream);
+  dfree(p->Gd, p->stream);
   dfree(p->Xop[0], p->stream);
   dfree(p->Xop[1], p->stream);
   dfree(p->bits, p->stream);
@@ -232,6 +239,7 @@ EpiArgs base_args(const sbo_problem* p) {
   a.F2 = p->F2;
   a.err = p->err;
   a.gkind = p->opt_g;
+  a.Gd = p->Gd;
   if (p->single) {
     a.mu = p->mu;
     a.gpart = p->gpart;
@@ -251,7 +259,11 @@ cudaError_t contract(sbo_problem* p, const EpiArgs& a, int mode, int which_x, cu
     case KER_SIMT: return launch_simt(static_cast<const float*>(p->A), p->lda, a, mode, s);
     case KER_TC: return launch_tc(p->plan, which_x, nullptr, a, mode, timeout_ns(p), s);
     case KER_CSR:
-      return launch_csr(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, mode, pdl && p->opt_pdl != 0, s);
+      if (mode == EPI_UPDATE && p->csr_form == CSR_FORM_STAGED && !a.mu)
+        return launch_csr_staged(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, p->max_deg, p->sms,
+                                 pdl && p->opt_pdl != 0, timeout_ns(p), s);
+      return launch_csr(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, mode, pdl && p->opt_pdl != 0, s,
+                        p->csr_form);
     case KER_MAXK: return launch_maxk(p->rowptr, p->col, static_cast<const float*>(p->val), a, p->kparts, mode, s);
     default: return cudaErrorInvalidValue;
   }
@@ -423,6 +435,7 @@ sbo_status run_tiny(sbo_problem* p, int64_t steps) {
   a.e0 = p->n_evals_host;
   a.trace_cap = p->trace_cap;
   a.evalF = p->evalF;
+  a.G = p->Gd;
   cudaError_t e = launch_tiny(a, p->stream);
   ++p->launches;
   if (e != cudaSuccess) return cuda_fail(e, "tiny-n launch");
@@ -483,18 +496,22 @@ std::string tune_key(const sbo_problem* p) {
   return k.str();
 }
 
-bool tune_cache_lookup(const std::string& key, int* tile) {
+// A tile decision is the tile code, plus 10000 x the cluster size for the cluster split-K codes.
+bool valid_tile_code(int t) {
+  const int code = t % 10000;
+  return code == 64 || code == 128 || code == 256 || code == 512 ||
+         ((code == 1064 || code == 1128 || code == 1256) && t / 10000 >= 2 && t / 10000 <= 8);
+}
+
+bool tune_cache_lookup(const std::string& key, int* tile, bool (*valid)(int) = valid_tile_code) {
   const std::string path = tune_cache_path();
   if (path.empty()) return false;
   std::ifstream f(path);
   std::string k;
   int t = 0;
   bool found = false;
-  // a value is the tile code, plus 10000 x the cluster size for the cluster split-K codes
   while (f >> k >> t) {
-    const int code = t % 10000;
-    if (k == key && (code == 64 || code == 128 || code == 256 || code == 512 ||
-                     ((code == 1064 || code == 1128 || code == 1256) && t / 10000 >= 2 && t / 10000 <= 8))) {
+    if (k == key && valid(t)) {
       *tile = t;
       found = true;
     }
@@ -571,6 +588,84 @@ sbo_status tune_tile(sbo_problem* p, int* out) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) { best_ms = ms; best = tn >= 1000 ? tn + 10000 * pl.csk : tn; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != SBO_OK) return st;
+  st = read_err(p);
+  if (st != SBO_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best;
+    tune_cache_store(key, best);
+  }
+  *out = best;
+  return SBO_OK;
+}
+
+// Autotuner of the sparse update's form: times the update launch in every form (one row per warp
+// with 128 or 256 restarts, pipelined rows of 256, rows staged in shared memory by bulk copies) on
+// this run's own buffers, before x^0 is written, and keeps the fastest.  Kept per (device, graph
+// size, restarts, precision, g) for the process and in the persistent record of tune_tile.
+sbo_status tune_csr_form(sbo_problem* p, int* out) {
+  static std::mutex mu;
+  static std::map<std::string, int> cache;
+  std::string key;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown";
+    for (auto& ch : name)
+      if (ch == ' ') ch = '_';
+    std::ostringstream k;
+    k << "csr1:" << name << ":sms" << p->sms << ":n" << p->n << ":nnz" << p->nnz << ":deg" << p->max_deg << ":B"
+      << p->B << ":op" << p->op_type << ":g" << p->opt_g;
+    key = k.str();
+  }
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) { *out = it->second; return SBO_OK; }
+    int t = 0;
+    if (tune_cache_lookup(key, &t, [](int v) { return v >= CSR_FORM_ROW1 && v <= CSR_FORM_STAGED; })) {
+      cache[key] = t;
+      *out = t;
+      return SBO_OK;
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SBO_CUDA(cudaEventCreate(&e0));
+  SBO_CUDA(cudaEventCreate(&e1));
+  EpiArgs a = base_args(p);
+  a.Xin = p->Xop[0];
+  a.Xout = p->Xop[1];
+  a.bits_out = p->bits;
+  int best = CSR_FORM_RULE;
+  float best_ms = 1e30f;
+  sbo_status st = SBO_OK;
+  for (int f : {CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_STAGED}) {
+    int D, S, rc;
+    size_t sm;
+    if (f == CSR_FORM_STAGED && !csr_staged_shape(p->ld, p->op_type, p->max_deg, &D, &S, &rc, &sm)) continue;
+    auto launch = [&]() {
+      return f == CSR_FORM_STAGED
+                 ? launch_csr_staged(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, p->max_deg, p->sms,
+                                     p->opt_pdl != 0, timeout_ns(p), p->stream)
+                 : launch_csr(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, EPI_UPDATE, p->opt_pdl != 0,
+                              p->stream, f);
+    };
+    cudaError_t e = launch();
+    const int reps = 10;
+    if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
+    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    p->launches += reps + 1;
+    if (e != cudaSuccess) { st = cuda_fail(e, "sparse autotuner launch"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = f; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -814,6 +909,7 @@ sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const i
   p->fmt = FMT_CSR;
   p->prec = precision;
   p->nnz = (int64_t)cc.size();
+  for (int64_t i = 0; i < n; ++i) p->max_deg = std::max<int>(p->max_deg, rp[i + 1] - rp[i]);
   auto bail = [&](sbo_status s) { free_all(p); delete p; return s; };
   // weights in the storage type (exact by the checks above)
   std::vector<uint8_t> vbytes;
@@ -956,6 +1052,11 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       if (value < 0 || value > 64) return fail(SBO_EINVAL, "split-K factor must be in [0, 64]");
       p->opt_split_k = (int)value;
       return SBO_OK;
+    case SBO_OPT_KEEP_GRAD: p->opt_keep_grad = value != 0; return SBO_OK;
+    case SBO_OPT_CSR_FORM:
+      if (value < 0 || value > CSR_FORM_STAGED) return fail(SBO_EINVAL, "sparse form must be 0..4");
+      p->opt_csr_form = (int)value;
+      return SBO_OK;
     case SBO_OPT_TIMEOUT_US:
       if (value < 1) return fail(SBO_EINVAL, "timeout must be >= 1 us");
       p->opt_timeout_us = value;
@@ -980,6 +1081,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
     if (p->opt_dual != 0) return fail(SBO_EINVAL, "Max-k-Cut runs the per-vertex dual");
     if (x0 || y0) return fail(SBO_EINVAL, "Max-k-Cut starts from its own random logits (x0, y0 must be NULL)");
     if (p->opt_g != G_QUAD) return fail(SBO_EINVAL, "Max-k-Cut uses the quadratic constraint function");
+    if (p->opt_keep_grad) return fail(SBO_EINVAL, "Max-k-Cut runs do not keep the gradient");
     ker = KER_MAXK;
   } else if (p->fmt == FMT_CSR) {
     if (p->opt_kernel != KER_AUTO) return fail(SBO_EINVAL, "CSR problems use the CSR kernel only");
@@ -1024,6 +1126,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   };
   if (need_master) al((void**)&p->Xm, xelems * 4);
   al((void**)&p->Y, elems * 4);
+  if (p->opt_keep_grad) al((void**)&p->Gd, elems * 4);
   if (ker != KER_TINY) {
     al(&p->Xop[0], xelems * op_elt);
     al(&p->Xop[1], xelems * op_elt);
@@ -1058,6 +1161,7 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   // zero every buffer so padding never holds stale values; sentinels for bests and trace
   if (p->Xm) cudaMemsetAsync(p->Xm, 0, xelems * 4, s);
   cudaMemsetAsync(p->Y, 0, elems * 4, s);
+  if (p->Gd) cudaMemsetAsync(p->Gd, 0, elems * 4, s);
   for (void* b : {p->Xop[0], p->Xop[1]})
     if (b) cudaMemsetAsync(b, 0, xelems * op_elt, s);
   if (p->bits) cudaMemsetAsync(p->bits, 0, elems * (ker == KER_CSR ? 1 : op_elt), s);
@@ -1106,6 +1210,22 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
     attach_workspace(p, &p->plan);
   } else {
     p->tile_n = 0;
+  }
+  p->csr_form = CSR_FORM_RULE;
+  if (ker == KER_CSR && !p->single) {
+    if (p->opt_csr_form != 0) {
+      p->csr_form = p->opt_csr_form;
+    } else if (p->opt_autotune) {
+      int f = CSR_FORM_RULE;
+      sbo_status st2 = tune_csr_form(p, &f);   // on the zeroed state, before x^0 is written
+      if (st2 != SBO_OK) { free_run(p); return st2; }
+      p->csr_form = f;
+    }
+    int D, S, rc;
+    size_t sm;
+    if (p->csr_form == CSR_FORM_STAGED && !csr_staged_shape(p->ld, p->op_type, p->max_deg, &D, &S, &rc, &sm))
+      p->csr_form = CSR_FORM_RULE;
+    p->tile_n = p->csr_form;   // reported by sbo_info
   }
   float* x0d = nullptr;
   float* y0d = nullptr;
@@ -1365,6 +1485,24 @@ sbo_status sbo_state(sbo_problem* p, float* X, float* Y) {
   }
   dfree(tmp, s);
   if (e != cudaSuccess) return cuda_fail(e, "state read-back");
+  return read_err(p);
+}
+
+sbo_status sbo_gradient(sbo_problem* p, float* G) {
+  g_last_error.clear();
+  if (!p || !G) return fail(SBO_EINVAL, "problem or G is NULL");
+  if (!p->started) return fail(SBO_ENOTREADY, "sbo_gda_start has not been called");
+  if (!p->Gd) return fail(SBO_ENOTREADY, "the run was started without SBO_OPT_KEEP_GRAD");
+  if (p->t < 1) return fail(SBO_ENOTREADY, "no iteration has run yet");
+  cudaStream_t s = p->stream;
+  float* tmp = nullptr;
+  SBO_CUDA(dalloc(&tmp, (size_t)p->B * p->n, s));
+  cudaError_t e = launch_gather_state(p->Gd, (int)p->n, p->B, p->ld, p->layout, tmp, s);
+  ++p->launches;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G, tmp, sizeof(float) * p->B * p->n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(tmp, s);
+  if (e != cudaSuccess) return cuda_fail(e, "gradient read-back");
   return read_err(p);
 }
 

@@ -55,6 +55,9 @@ struct EpiArgs {
   float* gpart;
   int64_t gpart_ld;
   int gkind;               // constraint function g (GKind)
+  // EPI_UPDATE: when non-null, the gradient d = dL/dx at (x^t, y^t) that the step used, written at
+  // the state index of every element (the loop's own gradient, kept for parity checks)
+  float* Gd;
 };
 
 __device__ __forceinline__ float g_val(float x, int kind) {

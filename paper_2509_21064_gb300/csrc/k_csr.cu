@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
           float yn;
           const float xn = pdbo_update(x, y, d, gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
           const bool live = r0 + k < B;   // padding restarts keep their zeros
+          if (a.Gd) a.Gd[idx + k] = live ? d : 0.0f;
           set_comp(xn4, k, live ? xn : 0.0f);
           set_comp(yn4, k, live ? yn : 0.0f);
           set_comp(b4, k, (live && xn > 0.5f) ? 1.0f : 0.0f);
@@ -356,16 +357,20 @@ static int64_t csr_resident_blocks(CsrKernel k) {
 
 template <int MODE, int OPT>
 static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const void* val, int vt,
-                                const EpiArgs& a, bool pdl, cudaStream_t s) {
-  const int NV = csr_nv(a.n, a.B);
+                                const EpiArgs& a, int form, bool pdl, cudaStream_t s) {
   const bool single = MODE == EPI_UPDATE && a.mu != nullptr;
   const bool ent = MODE != EPI_EVAL && a.gkind == G_ENTROPY;
-  // the update strides pipelined rows when x and y (16 B per element) overflow three quarters of
-  // L2: measured on a 4-regular graph, n = 20,000, B = 512, 44.1 -> 41.9 us per iteration, while
-  // the L2-resident torus (n = 10,000) went 17.7 -> 18.2 us
+  // the update's form: chosen by the autotuner (CSR_FORM_*), or by the rule below.  The rule
+  // strides pipelined rows when x and y (16 B per element) overflow three quarters of L2: measured
+  // on a 4-regular graph, n = 20,000, B = 512, 44.1 -> 41.9 us per iteration, while the
+  // L2-resident torus (n = 10,000) went 17.7 -> 18.2 us.  The single-constraint form keeps the
+  // rule (its rows of partial sums are sized by it).
+  const bool forced = MODE == EPI_UPDATE && !single && form >= CSR_FORM_ROW1 && form <= CSR_FORM_PIPE2;
+  const int NV = forced ? (form == CSR_FORM_ROW1 ? 1 : 2) : csr_nv(a.n, a.B);
   const int64_t l2 = device_l2_bytes();
-  const bool pipe = MODE == EPI_EVAL || (MODE == EPI_UPDATE && NV == 2 && l2 > 0 &&
-                                          (int64_t)a.n * a.B * 16 * 4 > l2 * 3);
+  const bool pipe = MODE == EPI_EVAL ||
+                    (MODE == EPI_UPDATE && (forced ? form == CSR_FORM_PIPE2
+                                                   : NV == 2 && l2 > 0 && (int64_t)a.n * a.B * 16 * 4 > l2 * 3));
   CsrKernel kern;
   if constexpr (MODE == EPI_EVAL) {
     kern = NV == 1 ? csr_kernel<MODE, 1, OPT, true>(single, ent) : csr_kernel<MODE, 2, OPT, true>(single, ent);
@@ -405,18 +410,18 @@ static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const
 }
 
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
-                       const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s) {
+                       const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s, int form) {
   if (a.ld % 8 != 0) return cudaErrorInvalidValue;  // vector accesses need 16-byte rows
   if (mode == EPI_UPDATE) {
-    return op_type == OP_F32 ? launch_csr_v<EPI_UPDATE, OP_F32>(rowptr, col, val, val_type, a, pdl, s)
-                             : launch_csr_v<EPI_UPDATE, OP_BF16>(rowptr, col, val, val_type, a, pdl, s);
+    return op_type == OP_F32 ? launch_csr_v<EPI_UPDATE, OP_F32>(rowptr, col, val, val_type, a, form, pdl, s)
+                             : launch_csr_v<EPI_UPDATE, OP_BF16>(rowptr, col, val, val_type, a, form, pdl, s);
   }
   if (mode == EPI_EVAL) {
-    return launch_csr_v<EPI_EVAL, OP_U8>(rowptr, col, val, val_type, a, pdl, s);   // candidate bytes
+    return launch_csr_v<EPI_EVAL, OP_U8>(rowptr, col, val, val_type, a, 0, pdl, s);   // candidate bytes
   }
   if (mode == EPI_LAGR) {
-    return op_type == OP_F32 ? launch_csr_v<EPI_LAGR, OP_F32>(rowptr, col, val, val_type, a, pdl, s)
-                             : launch_csr_v<EPI_LAGR, OP_BF16>(rowptr, col, val, val_type, a, pdl, s);
+    return op_type == OP_F32 ? launch_csr_v<EPI_LAGR, OP_F32>(rowptr, col, val, val_type, a, 0, pdl, s)
+                             : launch_csr_v<EPI_LAGR, OP_BF16>(rowptr, col, val, val_type, a, 0, pdl, s);
   }
   return cudaErrorInvalidValue;
 }

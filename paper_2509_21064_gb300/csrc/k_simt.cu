@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(256) k_simt(const float* __restrict__ A, int64
         const float d = g + a.cp[i] + y * g_der(x, a.gkind);
         float yn;
         const float xn = pdbo_update(x, y, d, gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+        if (a.Gd) a.Gd[idx] = d;
         if (a.Xm) a.Xm[idx] = xn;
         static_cast<float*>(a.Xout)[idx] = xn;
         if (a.mu) gsum += gx;

@@ -504,9 +504,8 @@ cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_ov
 }
 
 static cudaError_t ensure_attrs() {
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
+  static PerDevice per_device;
+  return per_device.once([] {
     cudaError_t r = cudaSuccess;
     r = r == cudaSuccess ? set_attr<64, EPI_UPDATE>() : r;
     r = r == cudaSuccess ? set_attr<64, EPI_EVAL>() : r;
@@ -517,9 +516,8 @@ static cudaError_t ensure_attrs() {
     r = r == cudaSuccess ? set_attr<256, EPI_UPDATE>() : r;
     r = r == cudaSuccess ? set_attr<256, EPI_EVAL>() : r;
     r = r == cudaSuccess ? set_attr<256, EPI_LAGR>() : r;
-    attr_err = r;
+    return r;
   });
-  return attr_err;
 }
 
 cudaError_t launch_tc_group(const TcInst* d_insts, int n_insts, int num_tiles, int tile_n, int mode, int epi_variant,

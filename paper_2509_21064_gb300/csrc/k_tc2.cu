@@ -388,32 +388,45 @@ cudaError_t set_pair_attr() {
 
 }  // namespace
 
+// Resident clusters of two CTAs on device `dev` (the current one), after setting the kernels'
+// shared-memory attributes; 0 when the kernel cannot run there.
+static int query_pair_clusters(int dev) {
+  if (set_pair_attr<EPI_UPDATE>() != cudaSuccess || set_pair_attr<EPI_EVAL>() != cudaSuccess) return 0;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(sms & ~1));
+  cfg.blockDim = dim3(P_THREADS);
+  cfg.dynamicSmemBytes = P_SMEM;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = 2;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_tc_pair<EPI_UPDATE>, &cfg) != cudaSuccess) n = 0;
+  cudaGetLastError();
+  return n;
+}
+
 bool tc_pair_supported(int* max_clusters) {
-  static int cached = -1;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cached = 0;
-    if (set_pair_attr<EPI_UPDATE>() != cudaSuccess || set_pair_attr<EPI_EVAL>() != cudaSuccess) return;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(sms & ~1));
-    cfg.blockDim = dim3(P_THREADS);
-    cfg.dynamicSmemBytes = P_SMEM;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = 2;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_tc_pair<EPI_UPDATE>, &cfg) == cudaSuccess) cached = n;
-    cudaGetLastError();
-  });
-  if (max_clusters) *max_clusters = cached;
-  return cached > 0;
+  // per device: the attributes and the occupancy query belong to the current device's context
+  static std::mutex mu;
+  static std::vector<std::pair<int, int>> cache;   // (device, resident clusters)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(mu);
+  int clusters = -1;
+  for (const auto& c : cache)
+    if (c.first == dev) clusters = c.second;
+  if (clusters < 0) {
+    clusters = query_pair_clusters(dev);
+    cache.push_back({dev, clusters});
+  }
+  if (max_clusters) *max_clusters = clusters;
+  return clusters > 0;
 }
 
 cudaError_t launch_tc_pair(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,

@@ -23,7 +23,10 @@
 // reaches both cluster barriers, which all CTAs therefore reach in bounded time.
 #include <cudaTypedefs.h>
 
+#include <array>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "tc_common.cuh"
 
@@ -274,15 +277,28 @@ cudaLaunchConfig_t csk_config(int grid, int S, cudaLaunchAttribute* attr, cudaSt
   return cfg;
 }
 
-// Clusters of S CTAs of this kernel that fit on the device at once (0 if none).
+// Clusters of S CTAs of this kernel that fit on the current device at once (0 if none), queried
+// once per (device, S): the attributes and the occupancy answer belong to the device's context.
 template <int BN>
 int csk_max_clusters(int S) {
   static std::mutex mu;
-  static int cache[9] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
-  std::lock_guard<std::mutex> lock(mu);
+  static std::vector<std::pair<int, std::array<int, 9>>> cache;   // (device, answer per S)
   if (S < 2 || S > 8) return 0;
-  if (cache[S] >= 0) return cache[S];
-  cache[S] = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  std::array<int, 9>* row = nullptr;
+  for (auto& c : cache)
+    if (c.first == dev) row = &c.second;
+  if (!row) {
+    std::array<int, 9> fresh;
+    fresh.fill(-1);
+    cache.push_back({dev, fresh});
+    row = &cache.back().second;
+  }
+  int& slot = (*row)[S];
+  if (slot >= 0) return slot;
+  slot = 0;
   if (csk_set_attr<BN, EPI_UPDATE>() != cudaSuccess || csk_set_attr<BN, EPI_EVAL>() != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -290,9 +306,9 @@ int csk_max_clusters(int S) {
   cudaLaunchAttribute attr;
   cudaLaunchConfig_t cfg = csk_config<BN>(S * 16, S, &attr, nullptr);
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_tc_csk<BN, EPI_UPDATE>, &cfg) == cudaSuccess) cache[S] = n;
+  if (cudaOccupancyMaxActiveClusters(&n, k_tc_csk<BN, EPI_UPDATE>, &cfg) == cudaSuccess) slot = n;
   cudaGetLastError();
-  return cache[S];
+  return slot;
 }
 
 template <int BN, int MODE>
@@ -321,9 +337,8 @@ cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int
   if (!plan.ready || plan.csk < 2 || plan.csk > 8 || plan.pair) return cudaErrorInvalidValue;
   if (mode != EPI_UPDATE && mode != EPI_EVAL) return cudaErrorInvalidValue;
   // shared-memory attributes (also set by the occupancy query, which a cached decision skips)
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [] {
+  static PerDevice per_device;
+  const cudaError_t attr_err = per_device.once([] {
     cudaError_t r = cudaSuccess;
     r = r == cudaSuccess ? csk_set_attr<64, EPI_UPDATE>() : r;
     r = r == cudaSuccess ? csk_set_attr<64, EPI_EVAL>() : r;
@@ -331,7 +346,7 @@ cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int
     r = r == cudaSuccess ? csk_set_attr<128, EPI_EVAL>() : r;
     r = r == cudaSuccess ? csk_set_attr<256, EPI_UPDATE>() : r;
     r = r == cudaSuccess ? csk_set_attr<256, EPI_EVAL>() : r;
-    attr_err = r;
+    return r;
   });
   if (attr_err != cudaSuccess) return attr_err;
   CskParams P;

@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(1024) k_tiny(TinyArgs a) {
       for (int k = 0; k < n; ++k) g = fmaf(Ai[k], xr[k], g);
       const float d = g + cps[i] + y * g_der(x, a.gkind);
       xn = pdbo_update(x, y, d, g_val(x, a.gkind), a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+      if (a.G) a.G[r * a.ld + i] = d;
     }
     __syncthreads();
     if (active) xs[rr * n + i] = xn;

@@ -1,12 +1,12 @@
 // sbo_lagrangian_noalloc: the Lagrangian value/gradient entry point for callers that must not
 // allocate device memory.
 //
-// Who needs it: code that runs while a stream is being captured into a CUDA graph (cudaMalloc
-// is not permitted there), processes whose device memory is owned by a framework's pool or a
-// fixed budget (an allocation behind the pool's back breaks its accounting), and latency-bound
-// loops that cannot afford the implicit synchronisation of cudaMalloc/cudaFree.  sbo_lagrangian
-// keeps a growing BF16 operand buffer per handle and may allocate it on any call; this variant
-// uses a fixed scratch array instead and never allocates.
+// Who needs it: processes whose device memory is owned by a framework's pool or a fixed budget
+// (an allocation behind the pool's back breaks its accounting, or fails once the budget is
+// spent), and latency-bound loops that cannot afford the implicit synchronisation of
+// cudaMalloc/cudaFree.  sbo_lagrangian keeps a growing BF16 operand buffer per handle and may
+// allocate it on any call; this variant uses a fixed scratch array instead and never allocates.
+// Dense problems only (FP32 or BF16).
 //
 // The scratch is a file-scope __device__ array of SCRATCH_BYTES.  Every GPU that loads the
 // library holds it until the process exits.  Host code cannot use the array's name as a device

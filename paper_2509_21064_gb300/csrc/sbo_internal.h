@@ -4,12 +4,38 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/sbo.h"
 #include "common.cuh"
 
 namespace sbo {
+
+// Runs a set-up step once per device: function attributes and memory-pool settings belong to the
+// context of the device that was current when they were set, so a process that uses several GPUs
+// needs them on each.  The first result on a device is returned to every later caller on it.
+class PerDevice {
+ public:
+  template <class F>
+  cudaError_t once(F&& f) {
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu_);
+    for (const auto& d : done_)
+      if (d.first == dev) return d.second;
+    const cudaError_t r = f();
+    done_.push_back({dev, r});
+    return r;
+  }
+
+ private:
+  std::mutex mu_;
+  std::vector<std::pair<int, cudaError_t>> done_;
+};
 
 enum Format : int { FMT_DENSE = 0, FMT_CSR = 1, FMT_MAXK = 2 };
 enum Kernel : int { KER_AUTO = 0, KER_SIMT = 1, KER_TC = 2, KER_TINY = 3, KER_CSR = 4, KER_MAXK = 5 };
@@ -59,13 +85,24 @@ struct TinyArgs {
   long long* trace;        // min_r F per evaluation, written at trace[e0 + e]
   int64_t e0, trace_cap;
   long long* evalF;        // scratch [B], F of the current evaluation
+  float* G;                // if non-null: dL/dx of the latest iteration, [B][ld]
 };
 cudaError_t launch_tiny(const TinyArgs& a, cudaStream_t s);
 // k_csr.cu  (variable-major state); pdl: launch as a programmatic dependent of the previous kernel.
 // csr_partial_rows: blocks along the rows (= rows of single-constraint partial sums) at most.
+// form (update only): CSR_FORM_RULE picks restarts per warp and the pipelined rows from n, B and
+// L2; the others force one: one row per warp with 128 / 256 restarts, pipelined rows of 256.
+enum CsrForm : int { CSR_FORM_RULE = 0, CSR_FORM_ROW1 = 1, CSR_FORM_ROW2 = 2, CSR_FORM_PIPE2 = 3, CSR_FORM_STAGED = 4 };
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
-                       const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s);
+                       const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s, int form = CSR_FORM_RULE);
 int csr_partial_rows(int64_t n, int B);
+// k_csr_staged.cu: the update with every row's operands staged in shared memory by bulk copies
+// (CSR_FORM_STAGED); max_deg is the largest row length of A.  csr_staged_shape reports its stage
+// layout and false when it does not apply (fewer than four stages fit).
+bool csr_staged_shape(int64_t ld, int op_type, int max_deg, int* D, int* S, int* rc, size_t* smem);
+cudaError_t launch_csr_staged(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
+                              const EpiArgs& a, int op_type, int max_deg, int sms, bool pdl, uint64_t timeout_ns,
+                              cudaStream_t s);
 // k_maxk.cu  (Max-k-Cut: Z, X as [(i k + j) ld + r], y and parts as [i ld + r]; Z in EpiArgs::Xm)
 cudaError_t launch_maxk(const int32_t* rowptr, const int32_t* col, const float* w, const EpiArgs& a, int kp, int mode,
                         cudaStream_t s);

@@ -155,6 +155,7 @@ __device__ __forceinline__ void epi_update(const EpiArgs& a, int64_t i, bool row
         const float d = g[j] + cpi + y * g_der(x, GK);
         float yn;
         const float xn = pdbo_update(x, y, d, gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+        if (a.Gd) a.Gd[idx] = d;
         a.Xm[idx] = xn;
         static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);
         if (a.bits_out)
@@ -174,6 +175,7 @@ __device__ __forceinline__ void epi_update(const EpiArgs& a, int64_t i, bool row
         const float d = g[j] + cpi + y * g_der(x, GK);
         float yn;
         const float xn = pdbo_update(x, y, d, g_val(x, GK), a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+        if (a.Gd) a.Gd[idx] = d;
         a.Xm[idx] = xn;
         a.Y[idx] = yn;
         static_cast<__nv_bfloat16*>(a.Xout)[idx] = __float2bfloat16_rn(xn);

@@ -20,7 +20,8 @@ STATUS_NAMES = ["SBO_OK", "SBO_EINVAL", "SBO_ENOMEM", "SBO_ECUDA", "SBO_ETIMEOUT
                 "SBO_ERANGE", "SBO_EDEVICE"]
 SBO_FP32, SBO_BF16, SBO_FP8_E4M3 = 0, 1, 2
 SBO_OPT_KERNEL, SBO_OPT_USE_GRAPH, SBO_OPT_TILE_N, SBO_OPT_TIMEOUT_US, SBO_OPT_SPLIT_K, SBO_OPT_AUTOTUNE, \
-    SBO_OPT_PDL, SBO_OPT_DUAL, SBO_OPT_G = 1, 2, 3, 4, 5, 6, 7, 8, 9
+    SBO_OPT_PDL, SBO_OPT_DUAL, SBO_OPT_G, SBO_OPT_KEEP_GRAD, SBO_OPT_CSR_FORM = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11
+CSR_FORM_AUTO, CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_STAGED = 0, 1, 2, 3, 4
 G_QUADRATIC, G_ENTROPY = 0, 1
 DUAL_COORDINATE, DUAL_SINGLE = 0, 1
 KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR, KERNEL_MAXK = 0, 1, 2, 3, 4, 5
@@ -28,7 +29,7 @@ KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR, KERNEL_MAXK = 0, 1
 # every symbol include/sbo.h declares
 EXPORTS = ["sbo_create_dense", "sbo_create_dense_i8", "sbo_create_csr", "sbo_create_maxkcut",
            "sbo_gda_start", "sbo_gda_start_xy", "sbo_gda_run", "sbo_gda", "sbo_sync",
-           "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_trace",
+           "sbo_eval", "sbo_best", "sbo_restart_best", "sbo_state", "sbo_gradient", "sbo_trace",
            "sbo_lagrangian", "sbo_lagrangian_noalloc", "sbo_dual_bound",
            "sbo_set_option", "sbo_info", "sbo_launch_count", "sbo_destroy", "sbo_last_error", "sbo_version",
            "sbo_group_create", "sbo_group_start", "sbo_group_run", "sbo_group_sync", "sbo_group_set_option",
@@ -86,6 +87,7 @@ def lib():
         "sbo_best": (st, [_P, _U8P, _I64P, _I64P, _I32P]),
         "sbo_restart_best": (st, [_P, _I64P, _I64P]),
         "sbo_state": (st, [_P, _F32P, _F32P]),
+        "sbo_gradient": (st, [_P, _F32P]),
         "sbo_trace": (st, [_P, _I64P, ctypes.c_int64, _I64P]),
         "sbo_lagrangian": (st, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P]),
         "sbo_lagrangian_noalloc": (st, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P]),
@@ -242,6 +244,13 @@ def sbo_state(h, B, n, k=1):
     return X, Y
 
 
+def sbo_gradient(h, B, n):
+    """dL/dx (B x n) that the latest iteration used (runs started with SBO_OPT_KEEP_GRAD = 1)."""
+    G = np.zeros((B, n), dtype=np.float32)
+    _check(lib().sbo_gradient(h, _ptr(G, ctypes.c_float)), "sbo_gradient")
+    return G
+
+
 def sbo_trace(h, cap=1 << 16):
     out = np.zeros(cap, dtype=np.int64)
     cnt = ctypes.c_int64()
@@ -338,6 +347,9 @@ class Problem:
 
     def state(self):
         return sbo_state(self.h, self.restarts, self.n, self.k)
+
+    def gradient(self):
+        return sbo_gradient(self.h, self.restarts, self.n)
 
     def dual_bound(self, ybar, alpha, iters):
         self.restarts = 1

@@ -9,7 +9,7 @@ import oracle as O
 import workloads as W
 from paper_2509_21064_gb300 import sbo as S
 from paper_2509_21064_gb300.build import build as build_lib
-from _helpers import gpu_trajectory, normwise, to_gda_params
+from _helpers import bf16_round as _bf16, gpu_trajectory, normwise, to_gda_params
 
 pytestmark = pytest.mark.gpu
 
@@ -20,12 +20,6 @@ def _lib():
     S.lib()
 
 
-def _bf16(x):
-    """Round to the nearest BF16 value (ties to even), as the tensor-core and BF16 sparse paths
-    round the contraction operand x."""
-    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
-    return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def _oracle_traj(A, cp, p, steps, operand_bf16=False):

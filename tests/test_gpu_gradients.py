@@ -1,0 +1,175 @@
+"""The GDA loop's own gradients against the FP64 oracle, iteration by iteration, on every kernel.
+
+Each update kernel keeps the gradient d^t = dL/dx (x^t, y^t) it used (SBO_OPT_KEEP_GRAD), and the
+tests read it back after every one of the first 50 iterations (the branch-free window: y stays
+positive, so no discrete decision of Algorithm 1 can flip).  Two comparisons per iteration:
+
+  own point   d^t against the oracle's dL/dx (section 3.1 Lagrangian) evaluated at the GPU's own
+              x^t, y^t, with the contraction fed the same operand (x rounded to BF16 on the BF16
+              paths).  Only FP32 accumulation order separates the two.
+  trajectory  d^t against the oracle's own D^t of Algorithm 1 from the same x^0, within the
+              method's tolerances of 1e-5 (FP32 contraction) and 2e-2 (BF16 / E4M3 contraction).
+Each kernel's bounds (BOUNDS) are about four times the errors measured on GB300, so that a
+regression shows long before those tolerances are reached.
+
+Errors of x and y are normwise: ||v_gpu - v_oracle||_inf / ||v_oracle||_inf per (iteration,
+restart).  The gradient is a sum whose terms cancel as the iteration approaches a stationary point
+(on Max-Cut its norm falls by two orders of magnitude within 50 iterations while its summands keep
+their size), and rounding errors scale with the summands; so its error is measured against them:
+||d_gpu - d_oracle||_inf / || |A||x| + |c'| + |y g'(x)| ||_inf per (iteration, restart).  The plain
+normwise error of d is recorded beside it.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from paper_2509_21064_gb300 import sbo as S
+from paper_2509_21064_gb300.build import build as build_lib
+from _helpers import (gpu_gradient_trajectory, gradient_scale, normwise, oracle_trajectory, own_point_gradient,
+                      report, scaled_error, to_gda_params)
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 50
+# largest accepted error per kernel: (d at the GPU's own point, d, x, y against the oracle
+# trajectory); about four times the error measured on GB300, rounded up to one digit, never above
+# the method's tolerance (1e-5 FP32 contraction, 2e-2 BF16 / E4M3 contraction)
+BOUNDS = {
+    "tiny": (5e-07, 6e-07, 1e-06, 3e-06),
+    "simt": (8e-07, 1e-06, 2e-06, 5e-06),
+    "tc64": (2e-07, 2e-03, 5e-03, 2e-04),
+    "tc128": (2e-07, 2e-03, 4e-03, 2e-04),
+    "tc256": (2e-07, 3e-03, 4e-03, 2e-04),
+    "pair512": (4e-07, 2e-03, 4e-03, 2e-04),
+    "csk1064": (2e-07, 2e-03, 5e-03, 2e-04),
+    "csk1128": (2e-07, 9e-04, 5e-03, 3e-04),
+    "csk1256": (2e-07, 2e-03, 4e-03, 2e-04),
+    "csr_fp32": (5e-07, 5e-07, 2e-06, 6e-06),
+    "csr_bf16": (8e-08, 5e-03, 2e-02, 2e-04),
+    "csr_e4m3": (8e-08, 5e-03, 2e-02, 2e-04),
+}
+
+
+def _own_error(A, cp, gx, gy, gd, mixed):
+    """Largest error of the kept gradients d^t against the oracle's gradient at the GPU's own
+    (x^t, y^t), scaled by the magnitude of the gradient's summands; all iterations at once."""
+    T, B, n = gd.shape
+    X, Y = gx[:T].reshape(T * B, n), gy[:T].reshape(T * B, n)
+    ref = own_point_gradient(A, cp, X, Y, operand_bf16=mixed)
+    return scaled_error(gd.reshape(T * B, n), ref, gradient_scale(A, cp, X, Y, operand_bf16=mixed)).max()
+
+
+def _traj_d_error(A, cp, gd, ox, oy, od):
+    """Largest error of the kept gradients against the oracle's own D^t, scaled by the magnitude
+    of the oracle gradient's summands at the oracle's (x^t, y^t)."""
+    T, B, n = gd.shape
+    X, Y = ox[:T].reshape(T * B, n), oy[:T].reshape(T * B, n)
+    return scaled_error(gd.reshape(T * B, n), od.reshape(T * B, n), gradient_scale(A, cp, X, Y)).max()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib()
+    S.lib()
+
+
+# kernel -> (format, n, restarts, precision, kernel option, tile option)
+KERNELS = {
+    "tiny": ("dense", 20, 32, S.SBO_FP32, S.KERNEL_TINY, 0),
+    "simt": ("dense", 200, 70, S.SBO_FP32, S.KERNEL_SIMT, 0),
+    "tc64": ("dense", 300, 100, S.SBO_BF16, S.KERNEL_TC, 64),
+    "tc128": ("dense", 333, 129, S.SBO_BF16, S.KERNEL_TC, 128),
+    "tc256": ("dense", 260, 300, S.SBO_BF16, S.KERNEL_TC, 256),
+    "pair512": ("dense", 600, 520, S.SBO_BF16, S.KERNEL_TC, 512),
+    "csk1064": ("dense", 700, 100, S.SBO_BF16, S.KERNEL_TC, 1064),
+    "csk1128": ("dense", 2000, 200, S.SBO_BF16, S.KERNEL_TC, 1128),
+    "csk1256": ("dense", 1000, 256, S.SBO_BF16, S.KERNEL_TC, 1256),
+    "csr_fp32": ("er", 2000, 256, S.SBO_FP32, 0, 0),
+    "csr_bf16": ("er", 2000, 256, S.SBO_BF16, 0, 0),
+    "csr_e4m3": ("er", 2000, 256, S.SBO_FP8_E4M3, 0, 0),
+}
+
+
+def _problem(fmt, n, B, prec, seed):
+    """(Problem, A, c', params) for a dense QUBO or Max-Cut on an Erdos-Renyi graph."""
+    if fmt == "dense":
+        Q, c = W.dense_qubo(n, seed=seed)
+        A, cp = O.canonicalize(Q, c)
+        p = W.dense_params(Q, restarts=B, iters=1000, eval_every=10, seed=seed + 1)
+        return S.Problem.dense(Q, c, precision=prec), A, cp, p
+    i, j, w = W.maxcut_er(n, 6.0, seed=seed)
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    A, cp = O.canonicalize_csr(n, rowptr, col, val, c)
+    p = W.graph_params("maxcut", restarts=B, iters=2000, eval_every=10, seed=seed + 1)
+    return S.Problem.csr(n, rowptr, col, val, c, precision=prec), A, cp, p
+
+
+def _errors(gx, gy, gd, A, cp, p, mixed, restarts=None, X0=None):
+    """Max normwise errors over the first len(gd) iterations: own-point gradient, and gradient,
+    x and y against the oracle trajectory (optionally on a restart subset, x^0 given)."""
+    steps = len(gd)
+    own = _own_error(A, cp, gx, gy, gd, mixed)
+    ox, oy, od = oracle_trajectory(None, None, p, steps, X0=X0, A=A, cp=cp, restarts=restarts)
+    return {"own_d": own, "d": _traj_d_error(A, cp, gd, ox, oy, od), "d_normwise": normwise(gd, od).max(),
+            "x": normwise(gx, ox).max(), "y": normwise(gy, oy).max()}
+
+
+@pytest.mark.parametrize("name", list(KERNELS))
+def test_loop_gradient_every_iteration_every_kernel(name):
+    fmt, n, B, prec, kernel, tile = KERNELS[name]
+    P, A, cp, p = _problem(fmt, n, B, prec, seed=n)
+    with P:
+        if kernel:
+            P.set_option(S.SBO_OPT_KERNEL, kernel)
+        if tile:
+            P.set_option(S.SBO_OPT_TILE_N, tile)
+        gx, gy, gd = gpu_gradient_trajectory(P, to_gda_params(p), STEPS)
+        info = P.info()
+        if tile:
+            assert info["tile_n"] == tile          # the kernel asked for is the one that ran
+        if fmt != "dense":
+            assert info["kernel"] == S.KERNEL_CSR
+    mixed = prec != S.SBO_FP32
+    err = _errors(gx, gy, gd, A, cp, p, mixed)
+    report("loop_gradient", kernel=name, n=n, restarts=B, **err)
+    b_own, b_d, b_x, b_y = BOUNDS[name]
+    assert err["own_d"] <= b_own and err["d"] <= b_d and err["x"] <= b_x and err["y"] <= b_y, err
+
+
+def test_hand_worked_gradients_are_exact():
+    """The hand-worked Algorithm-1 case with the perturbation rule (tests/golden): the kept
+    gradient equals the printed d exactly on the SIMT path (every number is dyadic)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "gda_steps_hand.json")) as f:
+        cases = json.load(f)["cases"]
+    for g in cases:
+        Q = np.array(g["Q"], dtype=np.int32)
+        c = np.array(g["c"], dtype=np.int32)
+        prm = S.params(restarts=1, iters=len(g["x"]), alpha=g["alpha"], beta=g["beta"], ybar=g["y0"][0],
+                       delta=g["delta"], grad_tol=g["grad_tol"], eval_every=1000)
+        with S.Problem.dense(Q, c, precision=S.SBO_FP32) as P:
+            P.set_option(S.SBO_OPT_KERNEL, S.KERNEL_SIMT)
+            P.set_option(S.SBO_OPT_KEEP_GRAD, 1)
+            P.start(prm, np.array(g["x0"], np.float32)[None, :], np.array(g["y0"], np.float32)[None, :])
+            for t in range(len(g["x"])):
+                P.run(1)
+                assert np.array_equal(P.gradient()[0], np.array(g["d"][t], np.float32)), (g["name"], t)
+
+
+def test_gradient_needs_the_option_and_an_iteration():
+    Q, c = W.dense_qubo(40, seed=1)
+    with S.Problem.dense(Q, c, precision=S.SBO_FP32) as P:
+        P.start(S.params(4, 0, 0.1, 0.1, 2.5, seed=3))
+        P.run(1)
+        with pytest.raises(S.SboError) as e:
+            P.gradient()
+        assert e.value.status == S.SBO_ENOTREADY
+        P.set_option(S.SBO_OPT_KEEP_GRAD, 1)
+        P.start(S.params(4, 0, 0.1, 0.1, 2.5, seed=3))
+        with pytest.raises(S.SboError) as e:
+            P.gradient()
+        assert e.value.status == S.SBO_ENOTREADY
+        P.run(1)
+        assert P.gradient().shape == (4, 40)

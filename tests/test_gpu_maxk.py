@@ -1,7 +1,7 @@
 """Max-k-Cut (appendix on Max-k-Cut) through the C ABI against the FP64 oracle ``oracle.maxkcut``.
 
 There is no discrete branch inside the iteration (softmax keeps X on the simplex, no perturbation
-rule), so the FP32 trajectory stays within 1e-4 (normwise per restart) of the oracle's over the
+rule), so the FP32 trajectory stays within 1e-5 (normwise per restart) of the oracle's over the
 first 30 iterations.  Objectives are exact: the GPU's evaluation of given parts equals the
 oracle's cut, and the best record is the cut of its own parts."""
 import numpy as np
@@ -11,9 +11,13 @@ import oracle.maxkcut as K
 import workloads as W
 from paper_2509_21064_gb300 import sbo as S
 from paper_2509_21064_gb300.build import build as build_lib
-from _helpers import gpu_trajectory, normwise, to_gda_params
+from _helpers import gpu_trajectory, normwise, report, to_gda_params
 
 pytestmark = pytest.mark.gpu
+
+# FP32 throughout: measured on GB300 (k = 3 and 5) 3.6e-7 in x and 1.2e-6 in y over 30 iterations;
+# held to the FP32 tolerance of the other paths
+TOL = 1e-5
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -39,12 +43,14 @@ def test_maxk_trajectory_matches_the_oracle(k):
         assert P.info()["kernel"] == S.KERNEL_MAXK
         Wm = K.weight_matrix(n, i, j, w)
         Z, Y = K.init_state_k(n, k, p.restarts, p.seed, p.ybar)
+        ex = ey = 0.0
         for t in range(31):
-            if t in (0, 1, 10, 30):
-                X = K.softmax(Z)
-                assert normwise(gx[t].reshape(p.restarts, -1), X.reshape(p.restarts, -1)).max() <= 1e-4, t
-                assert normwise(gy[t], Y).max() <= 1e-4, t
+            X = K.softmax(Z)
+            ex = max(ex, normwise(gx[t].reshape(p.restarts, -1), X.reshape(p.restarts, -1)).max())
+            ey = max(ey, normwise(gy[t], Y).max())
             Z, Y, _ = K.gda_step_k(Wm, Z, Y, p.alpha, p.beta)
+        report("maxk_trajectory", k=k, x=ex, y=ey)
+        assert ex <= TOL and ey <= TOL, (ex, ey)
         assert np.allclose(gx[30].sum(axis=2), 1.0, atol=1e-5)
         P.start(prm)
         P.run(30)

@@ -351,34 +351,6 @@ def test_autograd_function_matches_the_oracle_gradient():
         assert normwise(Yt.grad.cpu().numpy(), w[:, None] * GY_o).max() <= 1e-6
 
 
-def test_full_size_dense_n20000_sampled_restarts():
-    """Dense QUBO n=20000, 1024 restarts (the headline launch configuration): three BF16
-    iterations, then restarts 0, 517 and 1023 against the oracle run on those restarts alone
-    (restarts are independent), and their exact objectives at t=3."""
-    n, B = 20000, 1024
-    Q, c = W.dense_qubo(n, seed=0)
-    p = W.dense_params(Q, restarts=B, iters=2000, eval_every=3, seed=0)
-    prm = to_gda_params(p)
-    with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
-        P.start(prm)
-        P.run(3)
-        X, Y = P.state()
-        Fr, tr = P.restart_best()
-        assert P.info()["tile_n"] in (64, 128, 256, 512, 1064, 1128, 1256)
-    sample = [0, 517, 1023]
-    A, cp = O.canonicalize(Q, c)
-    del Q
-    X0, _ = O.init_state(n, B, p.seed, p.ybar)
-    ox, oy, _ = oracle_trajectory(None, None, p, 3, X0=X0[sample], A=A, cp=cp)
-    assert normwise(X[sample], ox[3]).max() <= TOL_MIXED
-    assert normwise(Y[sample], oy[3]).max() <= TOL_MIXED
-    Qs = W.dense_qubo(n, seed=0)[0]
-    for k, r in enumerate(sample):
-        b = O.round_bits(X[r])
-        assert tr[r] == 3
-        assert Fr[r] == O.objective(Qs, c, b)
-
-
 def test_mis_on_regular_graph_exact_objective():
     """MIS as QUBO (appendix on MIS, lambda = 4) through the sparse path: the reported best is an
     exact objective of its own bits; an independent best set has F = -|S|."""
@@ -451,23 +423,36 @@ def test_dense_n5000_bf16_lagrangian_and_autograd():
 
 
 @pytest.mark.parametrize("case", range(3))
-@pytest.mark.parametrize("path", ["tiny", "simt", "tc", "csr32", "csr_bf16"])
+@pytest.mark.parametrize("path", ["tiny", "simt", "tc", "tc512", "tc1064", "tc1128", "tc1256", "csr32", "csr_bf16"])
 def test_hand_worked_iterations_on_every_kernel(case, path):
     """The hand-worked Algorithm-1 iterations of tests/golden (perturbation rule with both
-    boundary equalities, active projection, plain steps) reproduced exactly by every kernel:
-    every number is dyadic and exact in FP32 and BF16."""
+    boundary equalities, active projection, plain steps) reproduced exactly by every kernel,
+    iterates and the gradient d each step used: every number is dyadic and exact in FP32 and BF16.
+    The CTA-pair (512) and cluster split-K (1064, 1128, 1256) kernels need more rows than the
+    hand-worked problem has: it is embedded in a problem of 600 variables whose other rows and
+    columns are zero, so the worked coordinates see exactly the worked sums."""
     import json
     import os
     with open(os.path.join(os.path.dirname(__file__), "golden", "gda_steps_hand.json")) as f:
         g = json.load(f)["cases"][case]
     Q = np.array(g["Q"], dtype=np.int32)
     c = np.array(g["c"], dtype=np.int32)
+    m = Q.shape[0]
+    x0 = np.array(g["x0"], dtype=np.float32)[None, :]
+    y0 = np.array(g["y0"], dtype=np.float32)[None, :]
+    tile = int(path[2:]) if path.startswith("tc") and len(path) > 2 else 0
+    if tile:
+        n = 600
+        Qp = np.zeros((n, n), np.int32)
+        Qp[:m, :m] = Q
+        Q = Qp
+        c = np.concatenate([c, np.zeros(n - m, np.int32)])
+        x0 = np.concatenate([x0, np.full((1, n - m), 0.375, np.float32)], axis=1)
+        y0 = np.concatenate([y0, np.full((1, n - m), float(g["y0"][0]), np.float32)], axis=1)
     n = Q.shape[0]
     T = len(g["x"])
     prm = S.params(restarts=1, iters=T, alpha=g["alpha"], beta=g["beta"], ybar=g["y0"][0], delta=g["delta"],
                    grad_tol=g["grad_tol"], eval_every=1000)
-    x0 = np.array(g["x0"], dtype=np.float32)[None, :]
-    y0 = np.array(g["y0"], dtype=np.float32)[None, :]
     if path.startswith("csr"):
         rows, cols = np.nonzero(Q)
         rowptr = np.zeros(n + 1, np.int64)
@@ -475,15 +460,22 @@ def test_hand_worked_iterations_on_every_kernel(case, path):
         P = S.Problem.csr(n, np.cumsum(rowptr), cols.astype(np.int32), Q[rows, cols], c,
                           precision=S.SBO_FP32 if path == "csr32" else S.SBO_BF16)
     else:
-        P = S.Problem.dense(Q, c, precision=S.SBO_BF16 if path == "tc" else S.SBO_FP32)
-        P.set_option(S.SBO_OPT_KERNEL, {"tiny": S.KERNEL_TINY, "simt": S.KERNEL_SIMT, "tc": S.KERNEL_TC}[path])
+        P = S.Problem.dense(Q, c, precision=S.SBO_BF16 if path.startswith("tc") else S.SBO_FP32)
+        P.set_option(S.SBO_OPT_KERNEL, {"tiny": S.KERNEL_TINY, "simt": S.KERNEL_SIMT}.get(path, S.KERNEL_TC))
+        if tile:
+            P.set_option(S.SBO_OPT_TILE_N, tile)
     with P:
+        P.set_option(S.SBO_OPT_KEEP_GRAD, 1)
         P.start(prm, x0, y0)
+        if tile:
+            assert P.info()["tile_n"] == tile
         for t in range(T):
             P.run(1)
             X, Y = P.state()
-            assert np.array_equal(X[0], np.array(g["x"][t], dtype=np.float32)), (t, X)
-            assert np.array_equal(Y[0], np.array(g["y"][t], dtype=np.float32)), (t, Y)
+            D = P.gradient()
+            assert np.array_equal(X[0, :m], np.array(g["x"][t], dtype=np.float32)), (t, X[0, :m])
+            assert np.array_equal(Y[0, :m], np.array(g["y"][t], dtype=np.float32)), (t, Y[0, :m])
+            assert np.array_equal(D[0, :m], np.array(g["d"][t], dtype=np.float32)), (t, D[0, :m])
 
 
 @pytest.mark.parametrize("kind", ["tc", "csr"])

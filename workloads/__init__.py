@@ -11,6 +11,8 @@ from .generators import (  # noqa: F401
     maxcut_regular,
     mis_regular,
     heterogeneous_qubos,
+    heterogeneous_qubo,
+    heterogeneous_shapes,
     iter_heterogeneous_qubos,
     csr_from_edges,
     maxcut_qubo,

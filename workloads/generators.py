@@ -41,11 +41,14 @@ def _rng(seed: int, tag: int) -> np.random.Generator:
 # dense QUBO
 # ----------------------------------------------------------------------------------------
 def dense_qubo(n: int, seed: int = 0, lo: int = -100, hi: int = 100, density: float = 1.0,
-               rng: np.random.Generator | None = None):
-    """Return ``(Q, c)``: ``Q`` int32 n x n symmetric with zero diagonal, ``c`` int32 n.
+               rng: np.random.Generator | None = None, dtype=np.int32):
+    """Return ``(Q, c)``: ``Q`` n x n symmetric with zero diagonal (``dtype``: int32, or int8 for
+    the entries drawn here, which all fit), ``c`` int32 n.
 
     ``M`` is symmetric with every upper-triangle entry (diagonal included) uniform in
     ``[lo, hi]``; pairs ``i < j`` are kept with probability ``density``; ``c = diag(M)``.
+    The draws: an n x n int8 matrix R (row-major), then, if density < 1, a uint32 per entry in
+    blocks of 2048 rows (kept when below density * 2^32); M takes R's upper triangle.
     """
     if not (-128 <= lo <= hi <= 127):
         raise ValueError("dense_qubo draws int8 entries; use lo, hi within [-128, 127]")
@@ -53,32 +56,57 @@ def dense_qubo(n: int, seed: int = 0, lo: int = -100, hi: int = 100, density: fl
         rng = _rng(seed, _TAG_DENSE)
     R = rng.integers(lo, hi + 1, size=(n, n), dtype=np.int8)
     if density < 1.0:
-        keep = np.empty((n, n), dtype=bool)
         blk = 2048
         thr = np.uint32(min(int(density * 2**32), 2**32 - 1))
         for r0 in range(0, n, blk):
             r1 = min(n, r0 + blk)
-            keep[r0:r1] = rng.integers(0, 2**32, size=(r1 - r0, n), dtype=np.uint32) < thr
-        R[~keep] = 0
-        del keep
-    M = np.triu(R)
-    M += np.triu(R, 1).T          # disjoint supports: no int8 overflow
-    del R
-    c = np.diagonal(M).astype(np.int32).copy()
-    np.fill_diagonal(M, 0)
-    Q = M.astype(np.int32)
+            drop = rng.integers(0, 2**32, size=(r1 - r0, n), dtype=np.uint32) >= thr
+            R[r0:r1][drop] = 0
+            del drop
+    # mirror the upper triangle onto the lower one in place, one cache-sized tile pair at a time
+    t = 1024
+    for b0 in range(0, n, t):
+        b1 = min(n, b0 + t)
+        D = R[b0:b1, b0:b1]
+        D[...] = np.triu(D) + np.triu(D, 1).T          # disjoint supports: no int8 overflow
+        for c0 in range(b1, n, t):
+            c1 = min(n, c0 + t)
+            R[c0:c1, b0:b1] = R[b0:b1, c0:c1].T
+    c = np.diagonal(R).astype(np.int32).copy()
+    np.fill_diagonal(R, 0)
+    Q = R if np.dtype(dtype) == np.int8 else R.astype(dtype)
     return Q, c
+
+
+def heterogeneous_shapes(count: int, seed: int = 0, n_lo: int = 500, n_hi: int = 20000, dens_lo: float = 0.01,
+                         dens_hi: float = 1.0):
+    """(n_k, density_k) of the ``count`` instances of a heterogeneous batch: n ~ U{n_lo..n_hi},
+    density ~ U[dens_lo, dens_hi]."""
+    rng = _rng(seed, _TAG_HETERO)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        d = float(rng.uniform(dens_lo, dens_hi))
+        out.append((n, d))
+    return out
+
+
+def heterogeneous_qubo(k: int, count: int, seed: int = 0, n_lo: int = 500, n_hi: int = 20000,
+                       dens_lo: float = 0.01, dens_hi: float = 1.0, lo: int = -100, hi: int = 100, dtype=np.int32):
+    """Instance k of a heterogeneous batch (``dense_qubo`` at the k-th drawn size and density), from
+    a generator of its own, so that instances can be drawn independently of one another (in
+    parallel, or one at a time)."""
+    n, d = heterogeneous_shapes(count, seed, n_lo, n_hi, dens_lo, dens_hi)[k]
+    rng = np.random.Generator(np.random.PCG64([int(seed) & (2**63 - 1), _TAG_HETERO, 1 + int(k)]))
+    return dense_qubo(n, lo=lo, hi=hi, density=d, rng=rng, dtype=dtype)
 
 
 def iter_heterogeneous_qubos(count: int, seed: int = 0, n_lo: int = 500, n_hi: int = 20000,
                              dens_lo: float = 0.01, dens_hi: float = 1.0, lo: int = -100, hi: int = 100):
-    """Yield ``count`` dense QUBOs ``(Q, c)`` with n ~ U{n_lo..n_hi} and density ~ U[dens_lo,
-    dens_hi], one at a time (at n_hi = 20,000 the whole batch is ~35 GB of int32 on the host)."""
-    rng = _rng(seed, _TAG_HETERO)
-    for _ in range(count):
-        n = int(rng.integers(n_lo, n_hi + 1))
-        d = float(rng.uniform(dens_lo, dens_hi))
-        yield dense_qubo(n, lo=lo, hi=hi, density=d, rng=rng)
+    """Yield the ``count`` dense QUBOs ``(Q, c)`` of a heterogeneous batch one at a time (at
+    n_hi = 20,000 the whole batch is ~35 GB of int32 on the host)."""
+    for k in range(count):
+        yield heterogeneous_qubo(k, count, seed, n_lo, n_hi, dens_lo, dens_hi, lo, hi)
 
 
 def heterogeneous_qubos(count: int, seed: int = 0, n_lo: int = 500, n_hi: int = 20000,
