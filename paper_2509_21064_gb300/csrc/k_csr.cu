@@ -146,11 +146,13 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
     }
     // the row's own state first: independent of the gathers
     float4 xo[NV], yo[NV];
+    uint32_t own_bits[NV];   // EPI_EVAL: the row's own candidate bytes, four restarts per word
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const int64_t r0 = rbase + 128 * v;
       xo[v] = make_float4(0.f, 0.f, 0.f, 0.f);
       yo[v] = xo[v];
+      own_bits[v] = 0u;
       if (r0 < B) {
         const int64_t idx = i * ld + r0;
         if (MODE == EPI_UPDATE) {
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
           yo[v] = SINGLE ? *reinterpret_cast<const float4*>(a.mu + r0)    // the restarts' duals
                        : *reinterpret_cast<const float4*>(a.Y + idx);
         } else if (MODE == EPI_EVAL) {
-          xo[v] = load4<OPT>(Xin, idx);   // EPI_EVAL: the row's own bits
+          own_bits[v] = __ldg(reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(Xin) + idx));
         } else {
           // EPI_LAGR: the caller's restart-major FP32 x and y, [r][n]
 #pragma unroll
@@ -173,6 +175,50 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
     float4 acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (MODE == EPI_EVAL) {
+      // exact objective of 0/1 candidates: (A b)_i in integers -- the weights are integers (exact in
+      // their storage type) and the candidate bytes are unpacked with shifts, four restarts per
+      // 32-bit word, so no value is converted between float and integer per element
+      int ai[NV][4];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ai[v][k] = 0;
+      for (int eb = e0; eb < e1; eb += 32) {
+        int mycol = col0;
+        float myval = val0;
+        if (eb != e0) {
+          const int k = eb + lane;
+          mycol = k < e1 ? __ldg(col + k) : 0;
+          myval = k < e1 ? load_val(val, k, vt) : 0.0f;
+        }
+        const int wint = __float2int_rn(myval);
+        const int cnt = min(32, e1 - eb);
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+          const int64_t j = __shfl_sync(0xffffffffu, mycol, q);
+          const int w = __shfl_sync(0xffffffffu, wint, q);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const int64_t r0 = rbase + 128 * v;
+            if (r0 < B) {
+              const uint32_t word =
+                  __ldg(reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(Xin) + j * ld + r0));
+#pragma unroll
+              for (int k = 0; k < 4; ++k) ai[v][k] += w * (int)((word >> (8 * k)) & 1u);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int64_t r0 = rbase + 128 * v;
+        if (r0 >= B) continue;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (r0 + k < B && ((own_bits[v] >> (8 * k)) & 1u)) f2[v][k] += (long long)ai[v][k] + cp2;
+      }
+    } else {
     for (int eb = e0; eb < e1; eb += 32) {
       int mycol = col0;
       float myval = val0;
@@ -199,13 +245,15 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
         }
       }
     }
+    }
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
+    for (int v = 0; v < NV && MODE != EPI_EVAL; ++v) {
       const int64_t r0 = rbase + 128 * v;
       if (r0 >= B) continue;
       const int64_t idx = i * ld + r0;
       if (MODE == EPI_UPDATE) {
-        float4 xn4, yn4, b4;
+        float4 xn4, yn4;
+        uint32_t bw = 0u;   // candidate bytes b = [x^{t+1} > 1/2], four restarts per word
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const float x = comp(xo[v], k), y = comp(yo[v], k);
@@ -217,18 +265,14 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
           if (a.Gd) a.Gd[idx + k] = live ? d : 0.0f;
           set_comp(xn4, k, live ? xn : 0.0f);
           set_comp(yn4, k, live ? yn : 0.0f);
-          set_comp(b4, k, (live && xn > 0.5f) ? 1.0f : 0.0f);
+          bw |= (uint32_t)(live && xn > 0.5f) << (8 * k);
           if (SINGLE) set_comp(gs[v], k, comp(gs[v], k) + (live ? gx : 0.0f));
         }
         if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = xn4;
         store4<OPT>(a.Xout, idx, xn4);
         if (!SINGLE) *reinterpret_cast<float4*>(a.Y + idx) = yn4;
-        if (a.bits_out) store4<OP_U8>(a.bits_out, idx, b4);   // candidates as bytes
-      } else if (MODE == EPI_EVAL) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (r0 + k < B && comp(xo[v], k) != 0.0f) f2[v][k] += (long long)comp(acc[v], k) + cp2;
-      } else {
+        if (a.bits_out) *reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(a.bits_out) + idx) = bw;
+      } else if (MODE == EPI_LAGR) {
         // Lagrangian of section 3.1: dL/dx = A x + c' + y (2x - 1), dL/dy = g(x), and the row's
         // share 1/2 x (A x) + c' x + y g(x) of L, summed per restart below
 #pragma unroll

@@ -94,3 +94,4 @@ def test_row_sums_span_tiles(second, ok):
     with S.Problem.dense(Q, None, precision=S.SBO_FP32) as P:
         F = P.eval(bits)
     assert F.tolist() == O.objective_batch(Q, np.zeros(n, np.int32), bits).tolist()
+
