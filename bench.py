@@ -582,6 +582,7 @@ def other_configs(S, torch, dev, args, pk, hetero_jobs):
         p = W.graph_params("maxcut", restarts=B, iters=10**9, eval_every=K, seed=0)
         P = S.Problem.csr(n, rowptr, col, val, c, precision=prec, stream=stream)
         P.start(S.params(**p.asdict()))
+        form = P.info()["tile_n"]     # the sparse update's form chosen by the autotuner
         blocks = 40
         sec = _timed_blocks(torch, stream, lambda: P.run(K), blocks)
         P.sync()
@@ -593,7 +594,7 @@ def other_configs(S, torch, dev, args, pk, hetero_jobs):
         state = per * n * B
         bytes_it = state + nnz * (4 + wbytes) + 4 * (n + 1)
         resident = 16 * n * B * 4 <= l2 * 3
-        out[key] = {"n": n, "restarts": B, "precision": prec_name, "eval_every": K,
+        out[key] = {"n": n, "restarts": B, "precision": prec_name, "eval_every": K, "update_form": form,
                     "us_per_iteration": t_it * 1e6, "restart_iterations_per_s": B / t_it,
                     "roofline": {"bound": "latency (x, y fit in L2)" if resident else "hbm",
                                  "achieved": bytes_it / t_it / 1e9, "peak": hbm, "unit": "GB/s",
@@ -687,6 +688,7 @@ def run_sparse(args):
     P = S.Problem.csr(n, rowptr, col, val, c, precision=prec, stream=stream)
     P.set_option(S.SBO_OPT_PDL, 0 if args.no_pdl else 1)
     P.set_option(S.SBO_OPT_CSR_FORM, args.csr_form)
+    P.set_option(S.SBO_OPT_EVAL_MODE, args.eval_mode)
     if args.no_eval:
         p = W.graph_params("maxcut", restarts=B, iters=10**9, eval_every=10**6, seed=0)
     P.start(S.params(**p.asdict()))
@@ -707,7 +709,8 @@ def run_sparse(args):
     ms = e0.elapsed_time(e1) / (args.steps * K)
     per_elem = 16 if prec == S.SBO_FP32 else 20
     print(json.dumps({"workload": args.workload, "n": n, "restarts": B, "precision": args.precision,
-                      "pdl": not args.no_pdl, "form": form, "evaluations": not args.no_eval, "us_per_iter": ms * 1e3, "restart_iterations_per_s": B / (ms * 1e-3),
+                      "pdl": not args.no_pdl, "form": form, "evaluations": not args.no_eval,
+                      "eval_mode": args.eval_mode, "us_per_iter": ms * 1e3, "restart_iterations_per_s": B / (ms * 1e-3),
                       "state_gbs": n * B * per_elem / (ms * 1e-3) / 1e9}), flush=True)
     P.close()
     return 0
@@ -1059,10 +1062,13 @@ def main():
                     help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
                     help="weight/operand precision of a sparse workload")
-    ap.add_argument("--csr-form", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--csr-form", type=int, default=0, choices=list(range(8)),
                     help="sparse workloads: update form (0 autotuned; 1, 2 one row per warp with 128 / 256 "
-                         "restarts; 3 pipelined rows; 4 rows staged by bulk copies)")
+                         "restarts; 3 pipelined rows; 4 rows staged by bulk copies; 5-7: 1-3 with L2 "
+                         "eviction priorities)")
     ap.add_argument("--no-eval", action="store_true", help="sparse workloads: no evaluations (update launches only)")
+    ap.add_argument("--eval-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="sparse workloads: evaluation scheduling (0, 2 beside the next block; 1 in line)")
     ap.add_argument("--no-pdl", action="store_true",
                     help="sparse workloads: plain stream order instead of programmatic dependent launches")
     ap.add_argument("--hetero-n-hi", type=int, default=20000, help="hetero workload: largest instance size")

@@ -264,11 +264,17 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       size), 1 one row per warp with 128 restarts, 2 one row per warp with 256
  *                       restarts, 3 rows strided over one resident wave and software-pipelined (256
  *                       restarts per warp), 4 rows staged in shared memory by bulk copies (a
- *                       producer warp and four consumer warps per CTA).  Results are identical in
- *                       every form; the single-constraint form (SBO_OPT_DUAL = 1) keeps the rule */
+ *                       producer warp and four consumer warps per CTA), 5, 6, 7 the forms 1, 2, 3
+ *                       with L2 eviction priorities for state that overflows L2 (each row's own x
+ *                       and y evict-first, the operand written for the next iteration evict-last).
+ *                       Results are identical in every form; the single-constraint form
+ *                       (SBO_OPT_DUAL = 1) keeps the rule
+ *   SBO_OPT_EVAL_MODE:  scheduling of the evaluations of sparse and Max-k-Cut runs replayed from
+ *                       graphs with K >= 2: 0 (default) and 2 on a graph branch beside the next
+ *                       block's steps, 1 in line after each block.  Results are identical in both */
 enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4, SBO_OPT_SPLIT_K = 5,
        SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7, SBO_OPT_DUAL = 8, SBO_OPT_G = 9, SBO_OPT_KEEP_GRAD = 10,
-       SBO_OPT_CSR_FORM = 11 };
+       SBO_OPT_CSR_FORM = 11, SBO_OPT_EVAL_MODE = 12 };
 sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
 
 /* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL; 4 the

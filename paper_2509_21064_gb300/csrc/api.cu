@@ -107,6 +107,7 @@ struct sbo_problem {
   int opt_g = G_QUAD;         // constraint function g (SBO_OPT_G)
   int opt_keep_grad = 0;      // SBO_OPT_KEEP_GRAD: keep dL/dx of the latest iteration
   int opt_csr_form = 0;       // SBO_OPT_CSR_FORM: 0 autotuned (or the rule), else a CsrForm
+  int opt_eval_mode = 0;      // SBO_OPT_EVAL_MODE: 0 the rule (beside), 1 in line, 2 beside
   int64_t opt_timeout_us = 4000000;
   // run
   bool started = false;
@@ -325,17 +326,18 @@ int64_t next_eval_after(const sbo_problem* p, int64_t t) {
 }
 
 // Evaluations are deferred across blocks only where every step leaves the bits alone (K >= 2) and
-// the evaluation runs well beside the steps: sparse and Max-k-Cut runs replayed from graphs whose
-// state fits in three quarters of L2, so that the steps, like the evaluation, wait on latency
-// rather than on DRAM.  Measured per iteration with K = 10 (FP32): Max-Cut ER n = 2,000, B = 256 5.76 -> 5.14 us
-// and the 100 x 100 torus, B = 512 16.99 -> 16.41 us deferred; the 4-regular graph n = 20,000,
-// B = 512, whose 164 MB of x and y stream from DRAM, 42.95 -> 43.48 us, so it is not deferred.
+// the evaluation runs well beside the steps: sparse and Max-k-Cut runs replayed from graphs.  A
+// block then leaves its last iteration's candidates pending and the next block evaluates them on
+// a second graph branch beside its first K - 1 steps.  Measured per iteration with K = 10 (FP32):
+// Max-Cut ER n = 2,000, B = 256 5.76 -> 5.14 us and the 100 x 100 torus, B = 512 16.99 -> 16.41 us;
+// the 4-regular graph n = 20,000, B = 512, whose x and y stream from DRAM, 40.85 -> 39.98 us (E4M3
+// 40.03 -> 39.28) with the streaming update forms.  Evaluating inside the next block's first update
+// instead (one pass over the graph for both) measured slower on every graph (4-regular E4M3 41.4,
+// torus 17.5 us): the fused kernel's registers cost it occupancy.  SBO_OPT_EVAL_MODE 1 forces the
+// evaluation in line.
 bool defer_evals(const sbo_problem* p) {
-  // bytes read and written per element: x and y (FP32); Max-k-Cut: Z and X (k floats each) and y
-  const int64_t per = p->kernel == KER_MAXK ? 16 * (int64_t)p->kparts + 8 : 16;
-  const int64_t state = p->n * (int64_t)p->B * per;
   return (p->kernel == KER_CSR || p->kernel == KER_MAXK) && p->prm.eval_every >= 2 && p->opt_graph &&
-         state * 4 <= p->l2_bytes * 3;
+         p->opt_eval_mode != 1;
 }
 
 // Evaluate the deferred candidates (those of iteration t) on the problem's stream.
@@ -604,8 +606,8 @@ sbo_status tune_tile(sbo_problem* p, int* out) {
 }
 
 // Autotuner of the sparse update's form: times the update launch in every form (one row per warp
-// with 128 or 256 restarts, pipelined rows of 256, rows staged in shared memory by bulk copies) on
-// this run's own buffers, before x^0 is written, and keeps the fastest.  Kept per (device, graph
+// with 128 or 256 restarts, pipelined rows of 256, each with and without the L2 eviction
+// priorities) on this run's own buffers, before x^0 is written, and keeps the fastest.  Kept per (device, graph
 // size, restarts, precision, g) for the process and in the persistent record of tune_tile.
 sbo_status tune_csr_form(sbo_problem* p, int* out) {
   static std::mutex mu;
@@ -619,7 +621,7 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
     for (auto& ch : name)
       if (ch == ' ') ch = '_';
     std::ostringstream k;
-    k << "csr1:" << name << ":sms" << p->sms << ":n" << p->n << ":nnz" << p->nnz << ":deg" << p->max_deg << ":B"
+    k << "csr2:" << name << ":sms" << p->sms << ":n" << p->n << ":nnz" << p->nnz << ":deg" << p->max_deg << ":B"
       << p->B << ":op" << p->op_type << ":g" << p->opt_g;
     key = k.str();
   }
@@ -628,7 +630,7 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
     auto it = cache.find(key);
     if (it != cache.end()) { *out = it->second; return SBO_OK; }
     int t = 0;
-    if (tune_cache_lookup(key, &t, [](int v) { return v >= CSR_FORM_ROW1 && v <= CSR_FORM_STAGED; })) {
+    if (tune_cache_lookup(key, &t, [](int v) { return v >= CSR_FORM_ROW1 && v <= CSR_FORM_PIPE2_STREAM; })) {
       cache[key] = t;
       *out = t;
       return SBO_OK;
@@ -644,7 +646,16 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
   int best = CSR_FORM_RULE;
   float best_ms = 1e30f;
   sbo_status st = SBO_OK;
-  for (int f : {CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_STAGED}) {
+  // (the staged form, measured two to three times slower than these on every graph here, is not a
+  // candidate: it stays available through SBO_OPT_CSR_FORM).  The streaming forms are candidates
+  // only when x and y (16 B per element) overflow three quarters of L2: on L2-resident state their
+  // evict-first loads and stores send the next iteration's state to DRAM (100 x 100 torus, B = 512,
+  // E4M3: 15.9 -> 18.4 us per iteration), which launches timed back to back on one buffer do not
+  // always show.
+  const bool streams = p->n * (int64_t)p->B * 16 * 4 > p->l2_bytes * 3;
+  for (int f : {CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_ROW1_STREAM, CSR_FORM_ROW2_STREAM,
+                CSR_FORM_PIPE2_STREAM}) {
+    if (csr_form_streams(f) && !streams) continue;
     int D, S, rc;
     size_t sm;
     if (f == CSR_FORM_STAGED && !csr_staged_shape(p->ld, p->op_type, p->max_deg, &D, &S, &rc, &sm)) continue;
@@ -1053,8 +1064,12 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       p->opt_split_k = (int)value;
       return SBO_OK;
     case SBO_OPT_KEEP_GRAD: p->opt_keep_grad = value != 0; return SBO_OK;
+    case SBO_OPT_EVAL_MODE:
+      if (value < 0 || value > 2) return fail(SBO_EINVAL, "evaluation mode must be 0..2");
+      p->opt_eval_mode = (int)value;
+      return SBO_OK;
     case SBO_OPT_CSR_FORM:
-      if (value < 0 || value > CSR_FORM_STAGED) return fail(SBO_EINVAL, "sparse form must be 0..4");
+      if (value < 0 || value > CSR_FORM_PIPE2_STREAM) return fail(SBO_EINVAL, "sparse form must be 0..7");
       p->opt_csr_form = (int)value;
       return SBO_OK;
     case SBO_OPT_TIMEOUT_US:

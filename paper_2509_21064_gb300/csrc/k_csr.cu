@@ -60,6 +60,32 @@ __device__ __forceinline__ void store4(void* p, int64_t idx, float4 v) {
     *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(p) + idx) = raw;
   }
 }
+// L2 eviction priorities for the update's own-state traffic (the "streaming" forms): x and y of a
+// row are read and written once per iteration, while the operand rows are gathered by every
+// neighbour, so when the state overflows L2 the former are marked evict-first and the operand
+// written for the next iteration evict-last.
+__device__ __forceinline__ uint64_t l2_policy_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld_policy4(const float* ptr, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(ptr), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_policy4(float* ptr, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(ptr), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(pol)
+               : "memory");
+}
 __device__ __forceinline__ float comp(const float4& v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
 __device__ __forceinline__ void set_comp(float4& v, int k, float s) {
   if (k == 0) v.x = s; else if (k == 1) v.y = s; else if (k == 2) v.z = s; else v.w = s;
@@ -67,9 +93,14 @@ __device__ __forceinline__ void set_comp(float4& v, int k, float s) {
 
 // GK: constraint function g; SINGLE: one dual per restart (both uniform per launch, so each
 // combination is its own instantiation and the per-element code carries no test of them).
-template <int MODE, int NV, int OPT, int GK, bool SINGLE, bool PIPE>
+// HINT: the streaming forms (L2 eviction priorities on the update's own x and y, see above).
+template <int MODE, int NV, int OPT, int GK, bool SINGLE, bool PIPE, bool HINT>
 __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                              const void* __restrict__ val, int vt, EpiArgs a) {
+  constexpr bool UPD = MODE == EPI_UPDATE;
+  constexpr bool OBJ = MODE == EPI_EVAL;     // accumulates 2F per restart
+  const uint64_t pol_first = HINT ? l2_policy_first() : 0ull;
+  const uint64_t pol_last = HINT ? l2_policy_last() : 0ull;
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
   const int64_t warp0 = (int64_t)blockIdx.x * warps_per_block + (threadIdx.x >> 5);
@@ -112,7 +143,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
     col0 = k < e1 ? __ldg(col + k) : 0;
     val0 = k < e1 ? load_val(val, k, vt) : 0.0f;
     cpi = a.cp[i];
-    if (MODE == EPI_EVAL) cp2 = 2 * (long long)a.cp64[i];
+    if (OBJ) cp2 = 2 * (long long)a.cp64[i];
   }
   // Programmatic dependent launch (a no-op when launched without it): wait until the previous
   // kernel of the stream has completed and its writes are visible, then let the next one be
@@ -138,7 +169,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
       ncol = k < f1 ? __ldg(col + k) : 0;
       nval = k < f1 ? load_val(val, k, vt) : 0.0f;
       ncpi = a.cp[i1];
-      if (MODE == EPI_EVAL) ncp2 = 2 * (long long)a.cp64[i1];
+      if (OBJ) ncp2 = 2 * (long long)a.cp64[i1];
       if (i2 < n) {
         g0 = __ldg(rowptr + i2);
         g1 = __ldg(rowptr + i2 + 1);
@@ -155,10 +186,15 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
       own_bits[v] = 0u;
       if (r0 < B) {
         const int64_t idx = i * ld + r0;
-        if (MODE == EPI_UPDATE) {
-          xo[v] = a.Xm ? *reinterpret_cast<const float4*>(a.Xm + idx) : load4<OP_F32>(Xin, idx);
-          yo[v] = SINGLE ? *reinterpret_cast<const float4*>(a.mu + r0)    // the restarts' duals
-                       : *reinterpret_cast<const float4*>(a.Y + idx);
+        if (UPD) {
+          if (HINT) {
+            xo[v] = a.Xm ? ld_policy4(a.Xm + idx, pol_first) : load4<OP_F32>(Xin, idx);
+            yo[v] = SINGLE ? *reinterpret_cast<const float4*>(a.mu + r0) : ld_policy4(a.Y + idx, pol_first);
+          } else {
+            xo[v] = a.Xm ? *reinterpret_cast<const float4*>(a.Xm + idx) : load4<OP_F32>(Xin, idx);
+            yo[v] = SINGLE ? *reinterpret_cast<const float4*>(a.mu + r0)    // the restarts' duals
+                         : *reinterpret_cast<const float4*>(a.Y + idx);
+          }
         } else if (MODE == EPI_EVAL) {
           own_bits[v] = __ldg(reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(Xin) + idx));
         } else {
@@ -251,7 +287,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
       const int64_t r0 = rbase + 128 * v;
       if (r0 >= B) continue;
       const int64_t idx = i * ld + r0;
-      if (MODE == EPI_UPDATE) {
+      if (UPD) {
         float4 xn4, yn4;
         uint32_t bw = 0u;   // candidate bytes b = [x^{t+1} > 1/2], four restarts per word
 #pragma unroll
@@ -268,9 +304,16 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
           bw |= (uint32_t)(live && xn > 0.5f) << (8 * k);
           if (SINGLE) set_comp(gs[v], k, comp(gs[v], k) + (live ? gx : 0.0f));
         }
-        if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = xn4;
-        store4<OPT>(a.Xout, idx, xn4);
-        if (!SINGLE) *reinterpret_cast<float4*>(a.Y + idx) = yn4;
+        if (HINT) {
+          if (a.Xm) st_policy4(a.Xm + idx, xn4, pol_first);
+          if (OPT == OP_F32) st_policy4(static_cast<float*>(a.Xout) + idx, xn4, pol_last);
+          else store4<OPT>(a.Xout, idx, xn4);
+          if (!SINGLE) st_policy4(a.Y + idx, yn4, pol_first);
+        } else {
+          if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = xn4;
+          store4<OPT>(a.Xout, idx, xn4);
+          if (!SINGLE) *reinterpret_cast<float4*>(a.Y + idx) = yn4;
+        }
         if (a.bits_out) *reinterpret_cast<uint32_t*>(static_cast<uint8_t*>(a.bits_out) + idx) = bw;
       } else if (MODE == EPI_LAGR) {
         // Lagrangian of section 3.1: dL/dx = A x + c' + y (2x - 1), dL/dy = g(x), and the row's
@@ -299,7 +342,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
       f1 = g1;
     }
   }
-  if ((MODE == EPI_UPDATE && SINGLE) || (MODE == EPI_LAGR && a.L)) {
+  if ((UPD && SINGLE) || (MODE == EPI_LAGR && a.L)) {
     // single-constraint form: the block's warps cover the same restarts; their sums of g go to
     // shared memory and are added in warp order into this block's row of partial sums.
     // Lagrangian: the same per-block sums of the rows' shares of L, added to L[r] atomically
@@ -317,7 +360,7 @@ __global__ void __launch_bounds__(256) k_csr(const int32_t* __restrict__ rowptr,
       else a.gpart[(int64_t)blockIdx.x * a.gpart_ld + rb + t] = sum;
     }
   }
-  if (MODE == EPI_EVAL) {
+  if (OBJ) {
     // the block's warps cover the same restarts: each warp's sums go to its row of shared
     // memory, a thread per restart adds the rows, then one atomic per restart per block
     __shared__ long long red[8][128 * NV];
@@ -354,10 +397,15 @@ int csr_partial_rows(int64_t n, int B) {
 
 using CsrKernel = void (*)(const int32_t*, const int32_t*, const void*, int, EpiArgs);
 
-template <int MODE, int NV, int OPT, bool PIPE>
+template <int MODE, int NV, int OPT, bool PIPE, bool HINT = false>
 static CsrKernel csr_kernel(bool single, bool ent) {
-  if (single) return ent ? k_csr<MODE, NV, OPT, G_ENTROPY, true, PIPE> : k_csr<MODE, NV, OPT, G_QUAD, true, PIPE>;
-  return ent ? k_csr<MODE, NV, OPT, G_ENTROPY, false, PIPE> : k_csr<MODE, NV, OPT, G_QUAD, false, PIPE>;
+  if constexpr (HINT) {   // never with the single-constraint form
+    return ent ? k_csr<MODE, NV, OPT, G_ENTROPY, false, PIPE, HINT> : k_csr<MODE, NV, OPT, G_QUAD, false, PIPE, HINT>;
+  } else {
+    if (single)
+      return ent ? k_csr<MODE, NV, OPT, G_ENTROPY, true, PIPE, false> : k_csr<MODE, NV, OPT, G_QUAD, true, PIPE, false>;
+    return ent ? k_csr<MODE, NV, OPT, G_ENTROPY, false, PIPE, false> : k_csr<MODE, NV, OPT, G_QUAD, false, PIPE, false>;
+  }
 }
 
 // L2 capacity of the current device (queried once per device).
@@ -409,18 +457,28 @@ static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const
   // on a 4-regular graph, n = 20,000, B = 512, 44.1 -> 41.9 us per iteration, while the
   // L2-resident torus (n = 10,000) went 17.7 -> 18.2 us.  The single-constraint form keeps the
   // rule (its rows of partial sums are sized by it).
-  const bool forced = MODE == EPI_UPDATE && !single && form >= CSR_FORM_ROW1 && form <= CSR_FORM_PIPE2;
-  const int NV = forced ? (form == CSR_FORM_ROW1 ? 1 : 2) : csr_nv(a.n, a.B);
+  // The streaming forms (CSR_FORM_*_STREAM) are the same with the L2 eviction priorities (HINT)
+  // on the own state.
+  const bool hint = MODE == EPI_UPDATE && !single && csr_form_streams(form);
+  const int base = csr_form_base(form);
+  const bool forced = MODE == EPI_UPDATE && !single && base >= CSR_FORM_ROW1 && base <= CSR_FORM_PIPE2;
+  const int NV = forced ? (base == CSR_FORM_ROW1 ? 1 : 2) : csr_nv(a.n, a.B);
   const int64_t l2 = device_l2_bytes();
   const bool pipe = MODE == EPI_EVAL ||
-                    (MODE == EPI_UPDATE && (forced ? form == CSR_FORM_PIPE2
+                    (MODE == EPI_UPDATE && (forced ? base == CSR_FORM_PIPE2
                                                    : NV == 2 && l2 > 0 && (int64_t)a.n * a.B * 16 * 4 > l2 * 3));
   CsrKernel kern;
   if constexpr (MODE == EPI_EVAL) {
+    // pipelined rows over one resident wave: the grid, and with it the closing atomics, stays bounded
     kern = NV == 1 ? csr_kernel<MODE, 1, OPT, true>(single, ent) : csr_kernel<MODE, 2, OPT, true>(single, ent);
   } else if constexpr (MODE == EPI_UPDATE) {
-    kern = pipe ? csr_kernel<MODE, 2, OPT, true>(single, ent)
-                : NV == 1 ? csr_kernel<MODE, 1, OPT, false>(single, ent) : csr_kernel<MODE, 2, OPT, false>(single, ent);
+    if (hint)
+      kern = pipe ? csr_kernel<MODE, 2, OPT, true, true>(single, ent)
+                  : NV == 1 ? csr_kernel<MODE, 1, OPT, false, true>(single, ent)
+                            : csr_kernel<MODE, 2, OPT, false, true>(single, ent);
+    else
+      kern = pipe ? csr_kernel<MODE, 2, OPT, true>(single, ent)
+                  : NV == 1 ? csr_kernel<MODE, 1, OPT, false>(single, ent) : csr_kernel<MODE, 2, OPT, false>(single, ent);
   } else {
     kern = NV == 1 ? csr_kernel<MODE, 1, OPT, false>(single, ent) : csr_kernel<MODE, 2, OPT, false>(single, ent);
   }

@@ -91,8 +91,13 @@ cudaError_t launch_tiny(const TinyArgs& a, cudaStream_t s);
 // k_csr.cu  (variable-major state); pdl: launch as a programmatic dependent of the previous kernel.
 // csr_partial_rows: blocks along the rows (= rows of single-constraint partial sums) at most.
 // form (update only): CSR_FORM_RULE picks restarts per warp and the pipelined rows from n, B and
-// L2; the others force one: one row per warp with 128 / 256 restarts, pipelined rows of 256.
-enum CsrForm : int { CSR_FORM_RULE = 0, CSR_FORM_ROW1 = 1, CSR_FORM_ROW2 = 2, CSR_FORM_PIPE2 = 3, CSR_FORM_STAGED = 4 };
+// L2; the others force one: one row per warp with 128 / 256 restarts, pipelined rows of 256, rows
+// staged in shared memory; the *_STREAM forms are the first three with L2 eviction priorities on
+// the own state (evict-first x and y, evict-last operand), for state that overflows L2.
+enum CsrForm : int { CSR_FORM_RULE = 0, CSR_FORM_ROW1 = 1, CSR_FORM_ROW2 = 2, CSR_FORM_PIPE2 = 3, CSR_FORM_STAGED = 4,
+                     CSR_FORM_ROW1_STREAM = 5, CSR_FORM_ROW2_STREAM = 6, CSR_FORM_PIPE2_STREAM = 7 };
+inline bool csr_form_streams(int form) { return form >= CSR_FORM_ROW1_STREAM && form <= CSR_FORM_PIPE2_STREAM; }
+inline int csr_form_base(int form) { return csr_form_streams(form) ? form - 4 : form; }
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
                        const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s, int form = CSR_FORM_RULE);
 int csr_partial_rows(int64_t n, int B);

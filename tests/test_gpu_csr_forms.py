@@ -1,6 +1,7 @@
 """Every form of the sparse update kernel (SBO_OPT_CSR_FORM: one row per warp with 128 or 256
-restarts, pipelined rows, rows staged in shared memory by bulk copies) computes the same sums in
-the same order, so all of them give bit-identical runs; the staged form is also held to the FP64
+restarts, pipelined rows, each of them with or without L2 eviction priorities, rows staged in shared
+memory by bulk copies) computes the same sums in the same order, so all of them give bit-identical
+runs; the staged form is also held to the FP64
 oracle.  The graphs cover ragged restart chunks (B = 200), two chunks of restarts per row (B = 600,
 the second one short), isolated vertices, and hub vertices whose rows span several stages."""
 import numpy as np
@@ -14,7 +15,8 @@ from _helpers import gpu_trajectory, normwise, oracle_trajectory, to_gda_params
 
 pytestmark = pytest.mark.gpu
 
-FORMS = [S.CSR_FORM_ROW1, S.CSR_FORM_ROW2, S.CSR_FORM_PIPE2, S.CSR_FORM_STAGED]
+FORMS = [S.CSR_FORM_ROW1, S.CSR_FORM_ROW2, S.CSR_FORM_PIPE2, S.CSR_FORM_ROW1_STREAM, S.CSR_FORM_ROW2_STREAM,
+         S.CSR_FORM_PIPE2_STREAM, S.CSR_FORM_STAGED]
 
 
 @pytest.fixture(scope="module", autouse=True)

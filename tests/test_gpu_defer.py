@@ -21,11 +21,12 @@ def _lib():
     S.lib()
 
 
-def _run(n, csr, prec, prm, graph, chunks, peek):
+def _run(n, csr, prec, prm, graph, chunks, peek, eval_mode=S.EVAL_MODE_RULE):
     rowptr, col, val, c = csr
     seen = []
     with S.Problem.csr(n, rowptr, col, val, c, precision=prec) as P:
         P.set_option(S.SBO_OPT_USE_GRAPH, int(graph))
+        P.set_option(S.SBO_OPT_EVAL_MODE, eval_mode)
         P.start(prm)
         for k in chunks:
             P.run(k)
@@ -54,14 +55,15 @@ def _same(a, b):
                                          (2, 31, (5, 4, 22)), (10, 95, (40, 40, 15))])
 @pytest.mark.parametrize("peek", [False, True])
 @pytest.mark.parametrize("prec", [S.SBO_FP32, S.SBO_BF16])
-def test_deferred_evaluations_match_immediate_ones(K, T, chunks, peek, prec):
+@pytest.mark.parametrize("mode", [S.EVAL_MODE_RULE, S.EVAL_MODE_INLINE])
+def test_deferred_evaluations_match_immediate_ones(K, T, chunks, peek, prec, mode):
     """Erdos-Renyi n = 3001, B = 200 (ragged rows and restart chunks)."""
     n = 3001
     i, j, w = W.maxcut_er(n, 6.0, seed=3)
     csr = W.maxcut_qubo(n, i, j, w)
     p = W.graph_params("maxcut", restarts=200, iters=T, eval_every=K, seed=5)
     prm = to_gda_params(p)
-    a = _run(n, csr, prec, prm, 1, chunks, peek)
+    a = _run(n, csr, prec, prm, 1, chunks, peek, mode)
     b = _run(n, csr, prec, prm, 0, chunks, peek)
     _same(a, b)
     x_star, F_star = a[4][0], a[4][1]
@@ -79,6 +81,21 @@ def test_deferred_evaluations_on_the_torus_with_two_restart_groups_per_warp():
     prm = to_gda_params(p)
     a = _run(n, csr, S.SBO_FP32, prm, 1, (10,) * 8, False)
     b = _run(n, csr, S.SBO_FP32, prm, 0, (10,) * 8, False)
+    _same(a, b)
+
+
+@pytest.mark.parametrize("prec", [S.SBO_FP32, S.SBO_FP8_E4M3])
+def test_deferred_evaluations_on_the_regular_graph(prec):
+    """Random 4-regular graph, n = 20,000, B = 512: x and y overflow L2 (the streaming update
+    forms), the evaluations run beside the next block; the run split into blocks of one evaluation
+    each (as the benchmark drives it) gives what in-line evaluation gives."""
+    n = 20000
+    i, j, w = W.maxcut_regular(n, 4, seed=0)
+    csr = W.maxcut_qubo(n, i, j, w)
+    p = W.graph_params("maxcut", restarts=512, iters=70, eval_every=10, seed=2)
+    prm = to_gda_params(p)
+    a = _run(n, csr, prec, prm, 1, (10,) * 7, False)    # no reads between calls: nothing flushes
+    b = _run(n, csr, prec, prm, 0, (10,) * 7, False)
     _same(a, b)
 
 
