@@ -659,15 +659,22 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
     int D, S, rc;
     size_t sm;
     if (f == CSR_FORM_STAGED && !csr_staged_shape(p->ld, p->op_type, p->max_deg, &D, &S, &rc, &sm)) continue;
+    // the launches alternate the operand buffers as the run does, so that what one launch writes
+    // (with its L2 priority) is what the next one gathers
+    int par = 0;
     auto launch = [&]() {
+      EpiArgs b = a;
+      b.Xin = p->Xop[par];
+      b.Xout = p->Xop[par ^ 1];
+      par ^= 1;
       return f == CSR_FORM_STAGED
-                 ? launch_csr_staged(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, p->max_deg, p->sms,
+                 ? launch_csr_staged(p->rowptr, p->col, p->val, p->val_type, b, p->op_type, p->max_deg, p->sms,
                                      p->opt_pdl != 0, timeout_ns(p), p->stream)
-                 : launch_csr(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, EPI_UPDATE, p->opt_pdl != 0,
+                 : launch_csr(p->rowptr, p->col, p->val, p->val_type, b, p->op_type, EPI_UPDATE, p->opt_pdl != 0,
                               p->stream, f);
     };
     cudaError_t e = launch();
-    const int reps = 10;
+    const int reps = 20;
     if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
     for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch();
     if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
