@@ -271,10 +271,17 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       (SBO_OPT_DUAL = 1) keeps the rule
  *   SBO_OPT_EVAL_MODE:  scheduling of the evaluations of sparse and Max-k-Cut runs replayed from
  *                       graphs with K >= 2: 0 (default) and 2 on a graph branch beside the next
- *                       block's steps, 1 in line after each block.  Results are identical in both */
+ *                       block's steps, 1 in line after each block.  Results are identical in both
+ *   SBO_OPT_STEPS_PER_LAUNCH: largest number of GDA iterations one launch of the cluster split-K
+ *                       kernel runs (tile codes 1064-1256, per-coordinate duals): 0 (default)
+ *                       4,096, 1 one launch per iteration.  The iterations of a launch meet at a
+ *                       grid-wide barrier, which needs every cluster of the launch resident at
+ *                       once (the kernel is chosen only where they fit in one wave); work of other
+ *                       streams that holds SMs longer than SBO_OPT_TIMEOUT_US makes the launch
+ *                       return early with SBO_ETIMEOUT.  Results are identical for every value */
 enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4, SBO_OPT_SPLIT_K = 5,
        SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7, SBO_OPT_DUAL = 8, SBO_OPT_G = 9, SBO_OPT_KEEP_GRAD = 10,
-       SBO_OPT_CSR_FORM = 11, SBO_OPT_EVAL_MODE = 12 };
+       SBO_OPT_CSR_FORM = 11, SBO_OPT_EVAL_MODE = 12, SBO_OPT_STEPS_PER_LAUNCH = 13 };
 sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value);
 
 /* sbo_info: n, restarts of the current run, the kernel chosen (values of SBO_OPT_KERNEL; 4 the

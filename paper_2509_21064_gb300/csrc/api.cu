@@ -109,6 +109,7 @@ struct sbo_problem {
   int opt_csr_form = 0;       // SBO_OPT_CSR_FORM: 0 autotuned (or the rule), else a CsrForm
   int opt_eval_mode = 0;      // SBO_OPT_EVAL_MODE: 0 the rule (beside), 1 in line, 2 beside
   int64_t opt_timeout_us = 4000000;
+  int64_t opt_steps_per_launch = 0;   // cluster split-K iterations per launch (0: 4,096)
   // run
   bool started = false;
   sbo_gda_params prm{};
@@ -139,6 +140,8 @@ struct sbo_problem {
   TcPlan plan{};
   float* tc_ws = nullptr;      // split-K partial tiles of the tcgen05 contraction
   int* tc_ctr = nullptr;       // split-K arrival counters (zero between launches)
+  unsigned int* tc_gbar = nullptr;   // grid barrier of multi-iteration launches (zero between launches)
+  float* csk_ws = nullptr;           // partial tiles of the cluster split-K kernel
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   // Deferred evaluation (sparse and Max-k-Cut runs with K >= 2): a replayed block leaves the
   // candidates of its last iteration unevaluated (eval_pending; they are those of iteration t), and
@@ -183,6 +186,8 @@ void free_run(sbo_problem* p) {
   p->single = false;
   dfree(p->tc_ws, p->stream);
   dfree(p->tc_ctr, p->stream);
+  dfree(p->tc_gbar, p->stream);
+  dfree(p->csk_ws, p->stream);
   p->started = false;
 }
 
@@ -285,6 +290,44 @@ cudaError_t enqueue_step(sbo_problem* p, bool write_bits, cudaStream_t s) {
   return e;
 }
 
+// Iterations one launch may run: several for the cluster split-K kernel with per-coordinate
+// duals (grid barrier between them), else one.
+int64_t steps_per_launch(const sbo_problem* p) {
+  if (p->kernel != KER_TC || p->plan.csk < 2 || p->plan.pair || p->single || !p->tc_gbar) return 1;
+  return p->opt_steps_per_launch == 0 ? 4096 : p->opt_steps_per_launch;
+}
+
+// Update launches that `steps` iterations take.
+int64_t step_launches(const sbo_problem* p, int64_t steps) {
+  const int64_t per = steps_per_launch(p);
+  return per > 1 ? (steps + per - 1) / per : steps * (p->single ? 2 : 1);
+}
+
+// `steps` iterations; the last one writes the candidate bits when write_bits.
+cudaError_t enqueue_steps(sbo_problem* p, int64_t steps, bool write_bits, cudaStream_t s) {
+  const int64_t per = steps_per_launch(p);
+  if (per <= 1) {
+    for (int64_t k = 0; k < steps; ++k) {
+      cudaError_t e = enqueue_step(p, write_bits && k + 1 == steps, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  for (int64_t done = 0; done < steps;) {
+    const int64_t chunk = std::min(per, steps - done);
+    done += chunk;
+    EpiArgs a = base_args(p);
+    a.Xin = p->Xop[p->cur];
+    a.Xout = p->Xop[p->cur ^ 1];
+    a.bits_out = write_bits && done == steps ? p->bits : nullptr;
+    ++p->launches;
+    cudaError_t e = launch_tc_csk(p->plan, p->cur, a, EPI_UPDATE, (int)chunk, timeout_ns(p), s);
+    if (e != cudaSuccess) return e;
+    if (chunk & 1) p->cur ^= 1;
+  }
+  return cudaSuccess;
+}
+
 CommitArgs commit_args(const sbo_problem* p) {
   CommitArgs c;
   std::memset(&c, 0, sizeof(c));
@@ -354,11 +397,8 @@ sbo_status flush_pending(sbo_problem* p) {
 sbo_status run_direct(sbo_problem* p, int64_t steps, bool eval_at_end) {
   sbo_status st = flush_pending(p);
   if (st != SBO_OK) return st;
-  for (int64_t s = 0; s < steps; ++s) {
-    const bool last = s + 1 == steps;
-    cudaError_t e = enqueue_step(p, last && eval_at_end, p->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "GDA step launch");
-  }
+  cudaError_t e0 = enqueue_steps(p, steps, eval_at_end, p->stream);
+  if (e0 != cudaSuccess) return cuda_fail(e0, "GDA step launch");
   p->t += steps;
   if (eval_at_end) {
     cudaError_t e = enqueue_eval(p, p->t - p->t_last_eval, p->stream);
@@ -390,9 +430,13 @@ sbo_status capture_block(sbo_problem* p, int parity, int kind) {
     if (err == cudaSuccess) err = enqueue_eval(p, K, p->cap_side, false);
     if (err == cudaSuccess) err = cudaEventRecord(p->ev_join, p->cap_side);
   }
-  for (int64_t s = 0; s < K && err == cudaSuccess; ++s) {
-    if (kind == BLOCK_BESIDE && s + 1 == K) err = cudaStreamWaitEvent(p->cap_stream, p->ev_join, 0);
-    if (err == cudaSuccess) err = enqueue_step(p, s + 1 == K, p->cap_stream);
+  if (kind == BLOCK_BESIDE) {
+    for (int64_t s = 0; s < K && err == cudaSuccess; ++s) {
+      if (s + 1 == K) err = cudaStreamWaitEvent(p->cap_stream, p->ev_join, 0);
+      if (err == cudaSuccess) err = enqueue_step(p, s + 1 == K, p->cap_stream);
+    }
+  } else if (err == cudaSuccess) {
+    err = enqueue_steps(p, K, true, p->cap_stream);
   }
   if (err == cudaSuccess && kind == BLOCK_EVAL) err = enqueue_eval(p, K, p->cap_stream);
   cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
@@ -468,6 +512,8 @@ int heuristic_tile(const sbo_problem* p) {
 }
 
 void attach_workspace(sbo_problem* p, TcPlan* plan) {
+  plan->gbar = p->tc_gbar;
+  plan->csk_ws = p->csk_ws;
   if (p->tc_ws && p->tc_ctr && p->opt_split_k >= 2) {
     plan->ws = p->tc_ws;
     plan->counters = p->tc_ctr;
@@ -494,7 +540,8 @@ std::string tune_key(const sbo_problem* p) {
   for (auto& ch : name)
     if (ch == ' ') ch = '_';
   std::ostringstream k;
-  k << "v3:" << name << ":sms" << p->sms << ":n" << p->n << ":B" << p->B << ":split" << p->opt_split_k;
+  k << "v4:" << name << ":sms" << p->sms << ":n" << p->n << ":B" << p->B << ":split" << p->opt_split_k
+    << (p->opt_steps_per_launch == 1 ? ":one" : "");
   return k.str();
 }
 
@@ -575,17 +622,24 @@ sbo_status tune_tile(sbo_problem* p, int* out) {
       continue;
     pl.pair = tn == 512;
     if (tn >= 1000) {
-      pl.csk = tc_csk_factor(width, pl.num_tiles, (int)((p->n + 63) / 64), p->sms);
+      pl.csk = p->csk_ws ? tc_csk_factor(width, pl.num_tiles, (int)((p->n + 63) / 64), p->sms) : 0;
       if (pl.csk < 2) continue;
     }
     attach_workspace(p, &pl);
+    // `reps` iterations the way the run would take them: one launch of the cluster kernel when
+    // its iterations share a launch, else one launch each
+    const int reps = 4;
+    const bool multi = pl.csk >= 2 && !p->single && pl.gbar && p->opt_steps_per_launch != 1;
     cudaError_t e = launch_tc(pl, 0, nullptr, a, EPI_UPDATE, timeout_ns(p), p->stream);
-    const int reps = 3;
     if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
-    for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch_tc(pl, 0, nullptr, a, EPI_UPDATE, timeout_ns(p), p->stream);
+    if (multi) {
+      if (e == cudaSuccess) e = launch_tc_csk(pl, 0, a, EPI_UPDATE, reps, timeout_ns(p), p->stream);
+    } else {
+      for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch_tc(pl, 0, nullptr, a, EPI_UPDATE, timeout_ns(p), p->stream);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    p->launches += reps + 1;
+    p->launches += multi ? 2 : reps + 1;
     if (e != cudaSuccess) { st = cuda_fail(e, "autotuner launch"); break; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -717,6 +771,8 @@ sbo_status read_err(sbo_problem* p) {
   SBO_CUDA(cudaMemcpy(&w, p->err, sizeof(w), cudaMemcpyDeviceToHost));
   if (w) {
     SBO_CUDA(cudaMemset(p->err, 0, sizeof(uint32_t)));
+    // a launch that gave up may have left the grid barrier's words raised
+    if (p->tc_gbar) SBO_CUDA(cudaMemset(p->tc_gbar, 0, 3 * sizeof(unsigned int)));
     if (w & ERR_TIMEOUT) return fail(SBO_ETIMEOUT, "a bounded device-side wait expired; the kernel returned early");
     return fail(SBO_EDEVICE, "a device-side bounds check failed (input out of range)");
   }
@@ -1079,6 +1135,10 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       if (value < 0 || value > CSR_FORM_PIPE2_STREAM) return fail(SBO_EINVAL, "sparse form must be 0..7");
       p->opt_csr_form = (int)value;
       return SBO_OK;
+    case SBO_OPT_STEPS_PER_LAUNCH:
+      if (value < 0 || value > (1 << 20)) return fail(SBO_EINVAL, "steps per launch must be in [0, 2^20]");
+      p->opt_steps_per_launch = value;
+      return SBO_OK;
     case SBO_OPT_TIMEOUT_US:
       if (value < 1) return fail(SBO_EINVAL, "timeout must be >= 1 us");
       p->opt_timeout_us = value;
@@ -1208,6 +1268,18 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
       }
       cudaMemsetAsync(p->tc_ctr, 0, sizeof(int) * p->sms * TC_WS_COUNTERS_PER_TILE, s);
     }
+    if ((e = dalloc(&p->tc_gbar, 3, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->tc_gbar, 0, 3 * sizeof(unsigned int), s)) != cudaSuccess) {
+      free_run(p);
+      return cuda_fail(e, "grid barrier words");
+    }
+    // the cluster split-K kernel serves problems with at most sms / 2 tiles (fewest at width 256)
+    if ((int64_t)((p->n + 127) / 128) * ((p->B + 255) / 256) * 2 <= p->sms &&
+        (e = dalloc(&p->csk_ws, (size_t)p->sms * 256 * 128, s)) != cudaSuccess) {
+      free_run(p);
+      return e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation of the cluster workspace failed")
+                                            : cuda_fail(e, "cudaMalloc");
+    }
     int tn = p->opt_tile_n;
     std::string why;
     if (tn == 0 && p->opt_autotune) {
@@ -1224,8 +1296,9 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
     if (e != cudaSuccess) { free_run(p); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
     p->plan.pair = tn == 512;
     if (tn >= 1000) {
-      p->plan.csk = tuned_csk >= 2 ? tuned_csk
-                                   : tc_csk_factor(tile_width(tn), p->plan.num_tiles, (int)((p->n + 63) / 64), p->sms);
+      p->plan.csk = !p->csk_ws   ? 0
+                    : tuned_csk >= 2 ? tuned_csk
+                                     : tc_csk_factor(tile_width(tn), p->plan.num_tiles, (int)((p->n + 63) / 64), p->sms);
       if (p->plan.csk < 2) tn = tile_width(tn);   // too many tiles for clusters: plain tiles
     }
     p->tile_n = tn;
@@ -1324,7 +1397,7 @@ sbo_status sbo_gda_run(sbo_problem* p, int64_t iters) {
       }
       cudaError_t e = cudaGraphLaunch(slot[par], p->stream);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-      p->launches += K * (p->single ? 2 : 1) + (kind == BLOCK_DEFER ? 0 : 2);
+      p->launches += step_launches(p, K) + (kind == BLOCK_DEFER ? 0 : 2);
       if (K & 1) p->cur ^= 1;
       if (kind == BLOCK_BESIDE) {   // the pending candidates of the block's first iteration
         p->t_last_eval = p->t;

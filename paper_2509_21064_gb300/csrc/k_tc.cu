@@ -477,7 +477,7 @@ cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_ov
   if (plan.pair && !map_override && (mode == EPI_UPDATE || mode == EPI_EVAL))
     return launch_tc_pair(plan, which_x, a, mode, timeout_ns, s);
   if (plan.csk >= 2 && !map_override && (mode == EPI_UPDATE || mode == EPI_EVAL))
-    return launch_tc_csk(plan, which_x, a, mode, timeout_ns, s);
+    return launch_tc_csk(plan, which_x, a, mode, 1, timeout_ns, s);
   TcParams P;
   P.mapA = plan.mapA;
   P.mapX = map_override ? *map_override : plan.mapX[which_x];

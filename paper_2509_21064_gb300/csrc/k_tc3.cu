@@ -1,5 +1,5 @@
 // Dense contraction for problems with fewer output tiles than SMs: split-K inside a thread-block
-// cluster, reduced through distributed shared memory.
+// cluster, several GDA iterations per launch.
 //
 // With B restarts and n rows there are ceil(n/128) * ceil(B/BN) tiles of the accumulator; when
 // that is well below the SM count (n = 5,000 with B = 256 gives 40 tiles of 128 x 256 on 152
@@ -7,20 +7,31 @@
 // Here a cluster of S CTAs shares one tile:
 //   * CTA s of the cluster runs k-blocks [s KB/S, (s+1) KB/S) with the same warp-specialised
 //     TMA / tcgen05.mma pipeline as k_tc.cu (one accumulator of BN TMEM columns);
-//   * its epilogue warps copy the partial accumulator into the CTA's own (now idle) stage
-//     buffers, column-major [column][row];
-//   * after a cluster barrier, CTA s owns the 32-column chunks [s NC/S, (s+1) NC/S) of the tile
-//     (NC = BN/32): it sums the S partials of those columns in split order 0..S-1, reading every
-//     CTA's shared memory with ld.shared::cluster (lane = row, so each load of a warp is one
-//     contiguous 128-byte run), so the sum does not depend on timing, and applies the PDBO
-//     update / exact objective to them;
+//   * CTA s owns the 32-column chunks [s NC/S, (s+1) NC/S) of the tile (NC = BN/32).  Its
+//     epilogue warps copy the partial accumulator, column-major [column][row], into its own (now
+//     idle) stage buffers for the columns it owns and into its slice of a workspace in L2 for the
+//     others;
+//   * after a cluster barrier, CTA s sums the S partials of its columns in split order 0..S-1
+//     (so the sum does not depend on timing) and applies the PDBO update / exact objective to
+//     them.  Each warp takes whole restart columns (all 128 rows, four consecutive rows per
+//     lane): every partial read, state load and state store of a warp is one contiguous 512-byte
+//     run of 16-byte accesses, and a batch of columns issues all its loads before any is used;
 //   * a second cluster barrier keeps every CTA's shared memory alive until all reads are done.
-// The epilogue is thereby spread over S SMs instead of one, and no partial tile goes through
-// global memory.  (Measured against two alternatives on n = 2,000-5,000, B = 256: pushing the
-// partials to their owners with st.shared::cluster, and 16-byte row-major pulls, were both
-// slower than these one-word pulls.)  Every mbarrier wait is bounded (globaltimer budget); a CTA
-// that gives up sets ERR_TIMEOUT, drains its own copies and MMAs, skips the reduction and still
-// reaches both cluster barriers, which all CTAs therefore reach in bounded time.
+// The partials went through distributed shared memory before (ld.shared::cluster): timestamps
+// showed the SM-to-SM network delivering about 25 GB/s per SM, 3-6 us per iteration for the
+// 48-98 KB each CTA pulls, against the L2 path's far higher bandwidth.
+//
+// An update launch runs `iters` GDA iterations: between two iterations every CTA publishes its
+// part of x^{t+1} (stores fenced for the TMA loads of other CTAs) and meets the others at a grid
+// barrier in global memory; the launch is one wave of clusters, so all CTAs are resident and may
+// wait for one another.  That removes the launch gap, the set-up of TMEM and barriers, and the
+// cold instruction cache of one launch per iteration.
+//
+// Every wait is bounded (globaltimer budget per iteration).  A CTA that gives up sets
+// ERR_TIMEOUT, raises the launch's abort word, drains its own copies and MMAs and skips the
+// reduction; the CTAs of a cluster decide together, from votes exchanged in shared memory,
+// whether to stop after an iteration, so the cluster barriers stay matched and every CTA
+// returns in bounded time.
 #include <cudaTypedefs.h>
 
 #include <array>
@@ -53,10 +64,15 @@ struct CskCfg {
 
 struct CskParams {
   CUtensorMap mapA;
-  CUtensorMap mapX;
-  EpiArgs epi;
+  CUtensorMap mapX[2];     // operand of an iteration by parity (EVAL: mapX[0] is the candidates' map)
+  EpiArgs epi;             // Xout and bits_out are taken from xop / bits_last below
+  void* xop[2];            // operand buffers: iteration j reads xop[w] and writes xop[w ^ 1], w = (x0 + j) & 1
+  void* bits_last;         // candidates written by the last iteration (null: none)
+  unsigned int* gbar;      // grid barrier [arrivals, exits, abort], zero between launches (iters > 1)
+  float* ws;               // partial tiles [tile][split][column][row] (>= tiles * S * BN * 128 floats)
+  int x0, iters;
   int n_tiles, kblocks, S;
-  uint64_t timeout_ns;
+  uint64_t timeout_ns;     // per iteration
 };
 
 __device__ __forceinline__ uint32_t csk_rank() {
@@ -73,12 +89,213 @@ __device__ __forceinline__ uint32_t csk_mapa(uint32_t addr, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
   return r;
 }
-// One word of a cluster peer's shared memory.
-__device__ __forceinline__ float csk_ld_remote(uint32_t cluster_addr) {
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(cluster_addr) : "memory");
+__device__ __forceinline__ float f4_at(const float4& v, int k) {
+  return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+constexpr int CSK_WARPS = CSK_THREADS / 32;
+constexpr int CSK_CB = 4;   // restart columns per warp whose loads are in flight together
+
+// Reduction and epilogue of tile columns [c_begin, c_end) (restarts r0 + c).  Warp w takes the
+// columns c_begin + w + CSK_WARPS t; lane l holds tile rows 4l .. 4l+3 (variables i0 .. i0+3).
+// The S partials of a column are summed in split order.  The state rows are padded to a multiple
+// of 8 elements, so the 16-byte loads at i0 < n stay inside the row; stores of the last, partial
+// group of four rows go element by element.
+template <int BN, int MODE, int GK, bool SINGLE>
+__device__ __forceinline__ void csk_columns(const EpiArgs& a, void* xout, void* bits, const float* part,
+                                            const float* ws_tile, int s, int S, int m_tile, int64_t r0, int c_begin,
+                                            int c_end, int warp, int lane) {
+  const int row0 = 4 * lane;
+  const int64_t i0 = (int64_t)m_tile * TC_BM + row0;
+  const int64_t left = (int64_t)a.n - i0;
+  const int nv = left <= 0 ? 0 : left >= 4 ? 4 : (int)left;   // valid rows of this lane
+  float cpv[4];
+  long long cp2v[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    cpv[k] = k < nv ? a.cp[i0 + k] : 0.0f;
+    cp2v[k] = (MODE == EPI_EVAL && k < nv) ? 2 * (long long)a.cp64[i0 + k] : 0;
+  }
+  for (int cb = c_begin + warp; cb < c_end; cb += CSK_WARPS * CSK_CB) {
+    float4 xv[CSK_CB], yv[CSK_CB], g[CSK_CB];
+    uint2 xb[CSK_CB];
+#pragma unroll
+    for (int t = 0; t < CSK_CB; ++t) {   // state loads (warp-uniform column tests)
+      const int c = cb + CSK_WARPS * t;
+      const int64_t r = r0 + c;
+      const bool ok = c < c_end && r < a.B && nv > 0;
+      const int64_t idx = r * a.ld + i0;
+      xv[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      yv[t] = xv[t];
+      xb[t] = make_uint2(0u, 0u);
+      if (ok) {
+        if (MODE == EPI_UPDATE) {
+          xv[t] = *reinterpret_cast<const float4*>(a.Xm + idx);
+          if (SINGLE) {
+            const float m = a.mu[r];
+            yv[t] = make_float4(m, m, m, m);
+          } else {
+            yv[t] = *reinterpret_cast<const float4*>(a.Y + idx);
+          }
+        } else {
+          xb[t] = *reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(a.Xin) + idx);
+        }
+      }
+      g[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    // The S partials of the batch's columns, summed in split order (the sum does not depend on
+    // timing).  One round of loads per split, issued without a branch between them (columns past
+    // c_end read a valid column and are never used) and pipelined two deep, so that a warp waits
+    // for about one load latency per two splits instead of one per load.
+    int col[CSK_CB];
+#pragma unroll
+    for (int t = 0; t < CSK_CB; ++t) col[t] = min(cb + CSK_WARPS * t, c_end - 1);
+    auto load_round = [&](int sp, float4 (&pv)[CSK_CB]) {
+      // this CTA's own partial of a column is in its shared memory, the others' in L2
+      if (sp == s) {
+#pragma unroll
+        for (int t = 0; t < CSK_CB; ++t) pv[t] = *reinterpret_cast<const float4*>(part + col[t] * TC_BM + row0);
+      } else {
+        const float* wsp = ws_tile + (size_t)sp * BN * TC_BM + row0;
+#pragma unroll
+        for (int t = 0; t < CSK_CB; ++t) pv[t] = __ldcg(reinterpret_cast<const float4*>(wsp + (size_t)col[t] * TC_BM));
+      }
+    };
+    auto add_round = [&](const float4 (&pv)[CSK_CB]) {
+#pragma unroll
+      for (int t = 0; t < CSK_CB; ++t) {
+        g[t].x += pv[t].x;
+        g[t].y += pv[t].y;
+        g[t].z += pv[t].z;
+        g[t].w += pv[t].w;
+      }
+    };
+    float4 pa[CSK_CB], pb[CSK_CB];
+    load_round(0, pa);
+    for (int sp = 0; sp < S; sp += 2) {
+      if (sp + 1 < S) load_round(sp + 1, pb);
+      add_round(pa);
+      if (sp + 1 < S) {
+        if (sp + 2 < S) load_round(sp + 2, pa);
+        add_round(pb);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < CSK_CB; ++t) {
+      const int c = cb + CSK_WARPS * t;
+      const int64_t r = r0 + c;
+      const bool col_ok = c < c_end && r < a.B;   // warp-uniform
+      if (!col_ok) continue;
+      const int64_t idx = r * a.ld + i0;
+      if (MODE == EPI_EVAL) {
+        const float xk[4] = {bf16_lo(xb[t].x), bf16_hi(xb[t].x), bf16_lo(xb[t].y), bf16_hi(xb[t].y)};
+        long long w = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k < nv && xk[k] != 0.0f) w += (long long)f4_at(g[t], k) + cp2v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0 && w != 0) atomicAdd(&a.F2[r], (unsigned long long)w);
+      } else {
+        float xn[4], yn[4], dd[4], gsum = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float x = f4_at(xv[t], k), y = f4_at(yv[t], k);
+          const float gx = g_val(x, GK);
+          dd[k] = f4_at(g[t], k) + cpv[k] + y * g_der(x, GK);
+          xn[k] = pdbo_update(x, y, dd[k], gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn[k]);
+          if (SINGLE && k < nv) gsum += gx;
+        }
+        if (nv == 4) {
+          if (a.Gd) *reinterpret_cast<float4*>(a.Gd + idx) = make_float4(dd[0], dd[1], dd[2], dd[3]);
+          *reinterpret_cast<float4*>(a.Xm + idx) = make_float4(xn[0], xn[1], xn[2], xn[3]);
+          if (!SINGLE) *reinterpret_cast<float4*>(a.Y + idx) = make_float4(yn[0], yn[1], yn[2], yn[3]);
+          *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(xout) + idx) =
+              make_uint2(pack_bf16x2(xn[0], xn[1]), pack_bf16x2(xn[2], xn[3]));
+          if (bits) {
+            float b[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[k] = xn[k] > 0.5f ? 1.0f : 0.0f;
+            *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(bits) + idx) =
+                make_uint2(pack_bf16x2(b[0], b[1]), pack_bf16x2(b[2], b[3]));
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (k < nv) {
+              if (a.Gd) a.Gd[idx + k] = dd[k];
+              a.Xm[idx + k] = xn[k];
+              if (!SINGLE) a.Y[idx + k] = yn[k];
+              static_cast<__nv_bfloat16*>(xout)[idx + k] = __float2bfloat16_rn(xn[k]);
+              if (bits) static_cast<__nv_bfloat16*>(bits)[idx + k] = __float2bfloat16_rn(xn[k] > 0.5f ? 1.0f : 0.0f);
+            }
+          }
+        }
+        if (SINGLE) {
+          // partial sums of g(x^t) over 32 rows (eight lanes), one row of partials per 32 rows
+#pragma unroll
+          for (int o = 1; o < 8; o <<= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
+          if ((lane & 7) == 0) a.gpart[(int64_t)(m_tile * 4 + (lane >> 3)) * a.gpart_ld + r] = gsum;
+        }
+      }
+    }
+  }
+}
+
+template <int BN, int MODE>
+__device__ __forceinline__ void csk_epilogue(const EpiArgs& a, void* xout, void* bits, const float* part,
+                                             const float* ws_tile, int s, int S, int m_tile, int64_t r0, int c_begin,
+                                             int c_end, int warp, int lane) {
+#define CSK_COLUMNS(M, G, SG) \
+  csk_columns<BN, M, G, SG>(a, xout, bits, part, ws_tile, s, S, m_tile, r0, c_begin, c_end, warp, lane)
+  if (MODE == EPI_EVAL) {
+    CSK_COLUMNS(EPI_EVAL, G_QUAD, false);
+  } else if (a.gkind == G_ENTROPY) {
+    if (a.mu) CSK_COLUMNS(EPI_UPDATE, G_ENTROPY, true);
+    else CSK_COLUMNS(EPI_UPDATE, G_ENTROPY, false);
+  } else {
+    if (a.mu) CSK_COLUMNS(EPI_UPDATE, G_QUAD, true);
+    else CSK_COLUMNS(EPI_UPDATE, G_QUAD, false);
+  }
+#undef CSK_COLUMNS
+}
+
+// ---- grid barrier between the iterations of one launch ------------------------------------------
+// Every CTA of the launch is resident at once (the launch is one wave of clusters), so CTAs may
+// wait for one another.  Arrivals only grow within a launch: barrier k (before iteration k) is
+// passed once k * gridDim.x arrivals are counted.  The last CTA to leave the kernel sets the
+// words back to zero for the next launch.  A CTA that gives up waiting raises the abort word,
+// which ends every other CTA's waits too.
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void red_release_gpu_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Orders this thread's earlier generic-proxy stores before later async-proxy (TMA) reads of other
+// CTAs, then before the release that publishes them.
+__device__ __forceinline__ void fence_stores_for_tma() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  __threadfence();
+}
+__device__ __forceinline__ bool grid_wait(const unsigned int* gbar, unsigned int target, uint64_t deadline) {
+  uint32_t spins = 0;
+  while (ld_acquire_gpu(gbar) < target) {
+    if (ld_acquire_gpu(gbar + 2) != 0u) return false;
+    if ((++spins & 15u) == 0u && globaltimer_ns() > deadline) return false;
+    __nanosleep(64);
+  }
+  return true;
+}
+
 template <int BN, int MODE>
 __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant__ CskParams P) {
   using C = CskCfg<BN>;
@@ -87,10 +304,12 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
   uint64_t* bars = reinterpret_cast<uint64_t*>(tiles + C::STAGES * C::STAGE_BYTES);
   uint64_t* full_bar = bars;                   // [STAGES]
   uint64_t* empty_bar = bars + C::STAGES;      // [STAGES]
-  uint64_t* tfull_bar = bars + 2 * C::STAGES;  // accumulator complete
+  uint64_t* tfull_bar = bars + 2 * C::STAGES;  // accumulator complete (one phase per iteration)
   uint64_t* drain_bar = tfull_bar + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain_bar + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+  int* stop_vote = abort_flag + 1;             // [2] this CTA's vote to stop, by iteration parity
+  int* stop_all = abort_flag + 3;              // the cluster's decision, broadcast in the CTA
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -101,8 +320,11 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
   const int kb0 = (int)((int64_t)s * P.kblocks / S);
   const int kb1 = (int)((int64_t)(s + 1) * P.kblocks / S);
   const int nk = kb1 - kb0;
+  // restart columns [c_begin, c_end) of the tile are this CTA's: 32-column chunks s NC/S .. (s+1) NC/S - 1
+  constexpr int NC = BN / 32;
+  const int c_begin = (int)((int)s * NC / S) * 32, c_end = (int)(((int)s + 1) * NC / S) * 32;
   const EpiArgs& a = P.epi;
-  const uint64_t deadline = globaltimer_ns() + P.timeout_ns;
+  const bool multi = P.iters > 1;
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < C::STAGES; ++q) {
@@ -112,10 +334,13 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
     mbar_init(smem_u32(tfull_bar), 1);
     mbar_init(smem_u32(drain_bar), 1);
     *abort_flag = 0;
+    stop_vote[0] = stop_vote[1] = 0;
+    *stop_all = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tma_prefetch_map(&P.mapA);
-    tma_prefetch_map(&P.mapX);
+    tma_prefetch_map(&P.mapX[0]);
+    if (multi) tma_prefetch_map(&P.mapX[1]);
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -129,126 +354,159 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
   const uint32_t tmem_base = *tmem_slot;
   const volatile int* vabort = abort_flag;
 
-  if (warp == 0) {
-    // ------------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      uint32_t issued_mask = 0, issued_parity = 0;
-      bool ok = true;
-      for (int jk = 0; jk < nk; ++jk) {
-        const int kb = kb0 + jk;
-        if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, deadline, vabort)) { ok = false; break; }
-        const uint32_t fb = smem_u32(&full_bar[stage]);
-        mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
-        uint8_t* sa = tiles + stage * C::STAGE_BYTES;
-        tma_load_2d(smem_u32(sa), &P.mapA, fb, kb * TC_BK, m_tile * TC_BM);
-        tma_load_2d(smem_u32(sa + C::A_BYTES), &P.mapX, fb, kb * TC_BK, n_tile * BN);
-        issued_mask |= 1u << stage;
-        issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
-        if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
-      }
-      if (!ok) {
-        atomicOr(a.err, ERR_TIMEOUT);
-        *abort_flag = 1;
-        const uint64_t dl2 = globaltimer_ns() + 200000000ull;
-        const int zero = 0;
-        for (int q = 0; q < C::STAGES; ++q)
-          if (issued_mask & (1u << q)) mbar_wait(smem_u32(&full_bar[q]), (issued_parity >> q) & 1u, dl2, &zero);
-      }
-    }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      bool ok = true, issued_any = false;
-      for (int jk = 0; jk < nk; ++jk) {
-        if (!mbar_wait(smem_u32(&full_bar[stage]), phase, deadline, vabort)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t sa = smem_u32(tiles + stage * C::STAGE_BYTES);
-        const uint32_t sb = sa + C::A_BYTES;
-#pragma unroll
-        for (int kk = 0; kk < TC_BK / 16; ++kk)
-          tc_mma(tmem_base, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), C::IDESC,
-                 (jk > 0 || kk > 0) ? 1u : 0u);
-        issued_any = true;
-        tc_commit(smem_u32(&empty_bar[stage]));
-        if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
-      }
-      if (ok) {
-        tc_commit(smem_u32(tfull_bar));
-      } else {
-        atomicOr(a.err, ERR_TIMEOUT);
-        *abort_flag = 1;
-        if (issued_any) {
-          tc_commit(smem_u32(drain_bar));
+  // pipeline positions carried across iterations by the producer and the MMA issuer
+  int stage = 0;
+  uint32_t phase = 0;
+  uint32_t issued_mask = 0, issued_parity = 0;   // producer: stages with a copy issued, and its phase
+  bool issued_any = false;                       // MMA issuer: an MMA may be in flight
+
+  for (int it = 0; it < P.iters; ++it) {
+    const int w = (P.x0 + it) & 1;
+    const uint64_t deadline = globaltimer_ns() + P.timeout_ns;
+    if (warp == 0) {
+      // ---------------------------------------------------------------- TMA producer
+      if (lane == 0 && *vabort == 0) {
+        // iteration it reads x^{it}, written by every CTA in iteration it - 1
+        bool ok = it == 0 || grid_wait(P.gbar, (unsigned int)it * gridDim.x, deadline);
+        if (ok && it > 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+        for (int jk = 0; ok && jk < nk; ++jk) {
+          const int kb = kb0 + jk;
+          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, deadline, vabort)) { ok = false; break; }
+          const uint32_t fb = smem_u32(&full_bar[stage]);
+          mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
+          uint8_t* sa = tiles + stage * C::STAGE_BYTES;
+          tma_load_2d(smem_u32(sa), &P.mapA, fb, kb * TC_BK, m_tile * TC_BM);
+          tma_load_2d(smem_u32(sa + C::A_BYTES), &P.mapX[w], fb, kb * TC_BK, n_tile * BN);
+          issued_mask |= 1u << stage;
+          issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
+          if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) {
+          atomicOr(a.err, ERR_TIMEOUT);
+          *abort_flag = 1;
+          if (multi) atomicExch(P.gbar + 2, 1u);
+          const uint64_t dl2 = globaltimer_ns() + 200000000ull;
           const int zero = 0;
-          mbar_wait(smem_u32(drain_bar), 0, globaltimer_ns() + 200000000ull, &zero);
+          for (int q = 0; q < C::STAGES; ++q)
+            if (issued_mask & (1u << q)) mbar_wait(smem_u32(&full_bar[q]), (issued_parity >> q) & 1u, dl2, &zero);
+        }
+      }
+    } else if (warp == 1) {
+      // ---------------------------------------------------------------- MMA issuer
+      if (lane == 0 && *vabort == 0) {
+        bool ok = true;
+        for (int jk = 0; jk < nk; ++jk) {
+          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, deadline, vabort)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(tiles + stage * C::STAGE_BYTES);
+          const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk)
+            tc_mma(tmem_base, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), C::IDESC,
+                   (jk > 0 || kk > 0) ? 1u : 0u);
+          issued_any = true;
+          tc_commit(smem_u32(&empty_bar[stage]));
+          if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (ok) {
+          tc_commit(smem_u32(tfull_bar));
+        } else {
+          atomicOr(a.err, ERR_TIMEOUT);
+          *abort_flag = 1;
+          if (multi) atomicExch(P.gbar + 2, 1u);
+          if (issued_any) {
+            tc_commit(smem_u32(drain_bar));
+            const int zero = 0;
+            mbar_wait(smem_u32(drain_bar), 0, globaltimer_ns() + 200000000ull, &zero);
+          }
+        }
+      }
+    } else if (warp >= 4) {
+      // ---------------------------------------------------------------- partial tile -> smem
+      // Every MMA of this CTA's iteration has completed when tfull fires, so the stage buffers are
+      // idle: the accumulator (lane = row) goes to part[column][row].
+      const int wg = (warp - 4) >> 2;
+      const int wq = warp & 3;
+      const int row = wq * 32 + lane;
+      if (*vabort == 0) {
+        if (mbar_wait_warp(smem_u32(tfull_bar), (uint32_t)(it & 1), deadline, vabort, lane)) {
+          tc_fence_after();
+          // columns this CTA owns stay in its shared memory, the others go to its slice of the
+          // workspace in L2, where their owners read them
+          float* part = reinterpret_cast<float*>(tiles);
+          float* mine = P.ws + ((size_t)tile * S + s) * BN * TC_BM;
+          float g[32];
+          for (int c0 = wg * (BN / 2); c0 < (wg + 1) * (BN / 2); c0 += 32) {
+            tmem_ld32(tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, g);
+            float* dst = (c0 >= c_begin && c0 < c_end) ? part : mine;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dst[(c0 + j) * TC_BM + row] = g[j];
+          }
+        } else if (lane == 0) {
+          atomicOr(a.err, ERR_TIMEOUT);
+          *abort_flag = 1;
+          if (multi) atomicExch(P.gbar + 2, 1u);
         }
       }
     }
-  } else if (warp >= 4) {
-    // ------------------------------------------------------------------ partial tile -> smem
-    // Every MMA of this CTA has completed when tfull fires, so the stage buffers are idle: the
-    // accumulator (lane = row) goes to part[column][row].
-    const int wg = (warp - 4) >> 2;
-    const int wq = warp & 3;
-    const int row = wq * 32 + lane;
-    if (mbar_wait_warp(smem_u32(tfull_bar), 0, deadline, vabort, lane)) {
-      tc_fence_after();
-      float* part = reinterpret_cast<float*>(tiles);
-      float g[32];
-      for (int c0 = wg * (BN / 2); c0 < (wg + 1) * (BN / 2); c0 += 32) {
-        tmem_ld32(tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, g);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) part[(c0 + j) * TC_BM + row] = g[j];
-      }
-    } else if (lane == 0) {
-      atomicOr(a.err, ERR_TIMEOUT);
-      *abort_flag = 1;
+
+    __syncwarp();
+    tc_fence_before();
+    csk_cluster_sync();   // every CTA's partial tile is in its shared memory
+    tc_fence_after();
+
+    if (*vabort == 0) {
+      // -------------------------------------------------------------- reduction + epilogue
+      // All twelve warps take part (the producer and MMA warps are idle by now); the partials
+      // come from shared memory, not TMEM, so any warp may take any columns.
+      void* bits = it + 1 == P.iters ? P.bits_last : nullptr;
+      csk_epilogue<BN, MODE>(a, P.xop[w ^ 1], bits, reinterpret_cast<const float*>(tiles),
+                             P.ws + (size_t)tile * S * BN * TC_BM, (int)s, S,
+                             m_tile, (int64_t)n_tile * BN, c_begin, c_end, warp, lane);
+      if (it + 1 < P.iters) fence_stores_for_tma();
     }
+    if (threadIdx.x == 0) stop_vote[it & 1] = (*vabort != 0 || (multi && ld_acquire_gpu(P.gbar + 2) != 0u)) ? 1 : 0;
+
+    __syncwarp();
+    tc_fence_before();
+    csk_cluster_sync();   // every read of every CTA's partial is done; the votes are in
+    tc_fence_after();
+
+    if (it + 1 == P.iters) break;
+    // Stop together: every CTA of the cluster reads the same votes (a vote of parity it & 1 is
+    // rewritten two iterations later, after two more cluster barriers), so the cluster barriers
+    // above stay matched.
+    if (threadIdx.x == 0) {
+      int stop = 0;
+      for (int r = 0; r < S; ++r) {
+        int v;
+        asm volatile("ld.shared::cluster.u32 %0, [%1];"
+                     : "=r"(v)
+                     : "r"(csk_mapa(smem_u32(&stop_vote[it & 1]), (uint32_t)r))
+                     : "memory");
+        stop |= v;
+      }
+      *stop_all = stop;
+      if (!stop) {
+        __threadfence();
+        red_release_gpu_add(P.gbar, 1u);   // this CTA's part of x^{it+1} is written
+      }
+    }
+    __syncthreads();
+    if (*stop_all) break;
   }
 
-  __syncwarp();
-  tc_fence_before();
-  csk_cluster_sync();   // every CTA's partial tile is in its shared memory
-  tc_fence_after();
-
-  if (*vabort == 0) {
-    // ------------------------------------------------------------------ reduction + epilogue
-    // All twelve warps take part (the producer and MMA warps are idle by now): three groups of
-    // four warps, each over the tile's 128 rows, share the CTA's chunks round-robin.  The rows
-    // come from shared memory, not TMEM, so any warp may take any rows.
-    const int wg = warp >> 2;
-    const int wq = warp & 3;
-    const int row = wq * 32 + lane;
-    const int64_t i = (int64_t)m_tile * TC_BM + row;
-    const bool row_ok = i < a.n;
-    const float cpi = row_ok ? a.cp[i] : 0.0f;
-    const long long cp2 = (MODE == EPI_EVAL && row_ok) ? 2 * (long long)a.cp64[i] : 0;
-    constexpr int NC = BN / 32;
-    const int q0 = (int)((int)s * NC / S), q1 = (int)(((int)s + 1) * NC / S);
-    const uint32_t part_local = smem_u32(tiles);
-    float u[32], v[32], g[32];
-    for (int q = q0 + wg; q < q1; q += CSK_THREADS / 128) {
-      const int c0 = q * 32;
-      const int64_t rbase = (int64_t)n_tile * BN + c0;
-      epi_load<MODE>(a, i, row_ok, rbase, u, v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) g[j] = 0.0f;
-      for (int sp = 0; sp < S; ++sp) {      // split order: the sum does not depend on timing
-        const uint32_t base = csk_mapa(part_local, (uint32_t)sp) + (uint32_t)((c0 * TC_BM + row) * 4);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) g[j] += csk_ld_remote(base + (uint32_t)(j * TC_BM * 4));
+  if (multi) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // the last CTA out restores the words for the next launch (the abort word stays raised
+      // after a failure; the host clears it when it reads the error)
+      if (atomicAdd(P.gbar + 1, 1u) == gridDim.x - 1) {
+        atomicExch(P.gbar, 0u);
+        atomicExch(P.gbar + 1, 0u);
       }
-      epi_apply<MODE>(a, i, row_ok, cpi, cp2, rbase, lane, g, u, v, m_tile * 4 + wq);
     }
   }
-
-  __syncwarp();
-  tc_fence_before();
-  csk_cluster_sync();   // no CTA leaves while another may still read its shared memory
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"((uint32_t)C::TMEM_COLS)
@@ -332,10 +590,11 @@ int tc_csk_factor(int tile_n, int num_tiles, int kblocks, int sms) {
   return 0;
 }
 
-cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,
+cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, int iters, uint64_t timeout_ns,
                           cudaStream_t s) {
-  if (!plan.ready || plan.csk < 2 || plan.csk > 8 || plan.pair) return cudaErrorInvalidValue;
+  if (!plan.ready || plan.csk < 2 || plan.csk > 8 || plan.pair || !plan.csk_ws) return cudaErrorInvalidValue;
   if (mode != EPI_UPDATE && mode != EPI_EVAL) return cudaErrorInvalidValue;
+  if (iters < 1 || (iters > 1 && (mode != EPI_UPDATE || !plan.gbar || which_x > 1 || a.mu))) return cudaErrorInvalidValue;
   // shared-memory attributes (also set by the occupancy query, which a cached decision skips)
   static PerDevice per_device;
   const cudaError_t attr_err = per_device.once([] {
@@ -352,8 +611,22 @@ cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int
   CskParams P;
   memset(&P, 0, sizeof(P));
   P.mapA = plan.mapA;
-  P.mapX = plan.mapX[which_x];
+  if (mode == EPI_UPDATE) {
+    // iteration j reads operand buffer (which_x + j) & 1 and writes the other one
+    P.mapX[0] = plan.mapX[0];
+    P.mapX[1] = plan.mapX[1];
+    P.x0 = which_x & 1;
+    P.xop[which_x & 1] = const_cast<void*>(a.Xin);
+    P.xop[(which_x & 1) ^ 1] = a.Xout;
+    P.bits_last = a.bits_out;
+  } else {
+    P.mapX[0] = plan.mapX[which_x];
+    P.x0 = 0;
+  }
   P.epi = a;
+  P.iters = iters;
+  P.gbar = plan.gbar;
+  P.ws = plan.csk_ws;
   P.n_tiles = (a.B + plan.tile_n - 1) / plan.tile_n;
   P.kblocks = (a.n + TC_BK - 1) / TC_BK;
   P.S = plan.csk;

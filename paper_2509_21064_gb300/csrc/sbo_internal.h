@@ -144,6 +144,8 @@ struct TcPlan {
   int max_splits;
   bool pair;               // CTA-pair kernel (k_tc2.cu): 256 x 256 tiles; tile_n is then 128
   int csk;                 // >= 2: split-K over a cluster of csk CTAs per tile (k_tc3.cu)
+  unsigned int* gbar;      // csk: grid barrier words of the multi-iteration launch (3, zero between launches)
+  float* csk_ws;           // csk: partial tiles exchanged through L2 (>= sms * 256 * 128 floats)
   bool ready;
 };
 // One instance of a grouped launch (several dense problems in one persistent launch).  The
@@ -176,9 +178,11 @@ cudaError_t launch_tc(const TcPlan& plan, int which_x, const CUtensorMap* map_ov
 // k_tc2.cu: CTA-pair variant (update and evaluation epilogues)
 bool tc_pair_supported(int* max_clusters);
 // k_tc3.cu: cluster split-K factor for num_tiles tiles of width tile_n (0: not applicable), and
-// its launch (EPI_UPDATE / EPI_EVAL)
+// its launch (EPI_UPDATE / EPI_EVAL).  An update launch may run `iters` > 1 iterations (operand
+// buffers alternating from which_x, candidates written by the last one when a.bits_out is set),
+// with a grid barrier between iterations (plan.gbar); not with the single-constraint dual.
 int tc_csk_factor(int tile_n, int num_tiles, int kblocks, int sms);
-cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,
+cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, int iters, uint64_t timeout_ns,
                           cudaStream_t s);
 cudaError_t launch_tc_pair(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,
                            cudaStream_t s);

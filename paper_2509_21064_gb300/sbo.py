@@ -20,8 +20,8 @@ STATUS_NAMES = ["SBO_OK", "SBO_EINVAL", "SBO_ENOMEM", "SBO_ECUDA", "SBO_ETIMEOUT
                 "SBO_ERANGE", "SBO_EDEVICE"]
 SBO_FP32, SBO_BF16, SBO_FP8_E4M3 = 0, 1, 2
 SBO_OPT_KERNEL, SBO_OPT_USE_GRAPH, SBO_OPT_TILE_N, SBO_OPT_TIMEOUT_US, SBO_OPT_SPLIT_K, SBO_OPT_AUTOTUNE, \
-    SBO_OPT_PDL, SBO_OPT_DUAL, SBO_OPT_G, SBO_OPT_KEEP_GRAD, SBO_OPT_CSR_FORM, SBO_OPT_EVAL_MODE = \
-    1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12
+    SBO_OPT_PDL, SBO_OPT_DUAL, SBO_OPT_G, SBO_OPT_KEEP_GRAD, SBO_OPT_CSR_FORM, SBO_OPT_EVAL_MODE, \
+    SBO_OPT_STEPS_PER_LAUNCH = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13
 EVAL_MODE_RULE, EVAL_MODE_INLINE, EVAL_MODE_BESIDE = 0, 1, 2
 CSR_FORM_AUTO, CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_STAGED = 0, 1, 2, 3, 4
 CSR_FORM_ROW1_STREAM, CSR_FORM_ROW2_STREAM, CSR_FORM_PIPE2_STREAM = 5, 6, 7

@@ -154,10 +154,12 @@ def test_tcgen05_split_k_tail_tiles(n, B, tile):
     assert normwise(runs[0][20], runs[1][20]).max() <= TOL_MIXED
 
 
-@pytest.mark.parametrize("n,B,tile", [(1000, 256, 1256), (2000, 200, 1128), (700, 100, 1064)])
+@pytest.mark.parametrize("n,B,tile", [(1000, 256, 1256), (2000, 200, 1128), (700, 100, 1064), (1001, 250, 1256),
+                                       (1999, 200, 1128), (702, 100, 1064)])
 def test_tcgen05_cluster_split_k(n, B, tile):
     """Small problems with K split over a thread-block cluster and the partials summed through
-    distributed shared memory in split order (ragged rows and restarts): trajectories within the
+    distributed shared memory in split order (ragged rows and restarts; n = 1001, 702 and 1999
+    leave one, two and three rows in the last group of four rows a lane updates): trajectories within the
     mixed tolerance of the oracle, exact objectives, graph replay identical to direct launches,
     and the same iterates as plain tiles of the same width up to the mixed tolerance."""
     Q, c = W.dense_qubo(n, seed=n + 3)
@@ -180,6 +182,41 @@ def test_tcgen05_cluster_split_k(n, B, tile):
         P.run(30)
         Xp, _ = P.state()
     assert normwise(X, Xp).max() <= TOL_MIXED
+
+
+@pytest.mark.parametrize("n,B,tile", [(1001, 250, 1256), (2000, 256, 1128)])
+def test_cluster_split_k_iterations_per_launch(n, B, tile):
+    """Several GDA iterations in one launch of the cluster split-K kernel (grid barrier between
+    them) against one launch per iteration: bit-identical iterates, duals, per-restart records
+    and minimum trace, with direct launches (T = 37 runs past the evaluation points 10, 20, 30)
+    and graph replay; launches of 3 iterations split blocks of 10 unevenly.  Fewer launches."""
+    Q, c = W.dense_qubo(n, seed=n + 11)
+    p = W.dense_params(Q, restarts=B, iters=400, eval_every=10, seed=5)
+    prm = to_gda_params(p)
+    runs, counts = [], []
+    for per_launch in (1, 3, 0):
+        with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
+            P.set_option(S.SBO_OPT_TILE_N, tile)
+            P.set_option(S.SBO_OPT_STEPS_PER_LAUNCH, per_launch)
+            P.set_option(S.SBO_OPT_USE_GRAPH, 0)
+            P.start(prm)
+            P.run(37)
+            X, Y = P.state()
+            Fr, tr = P.restart_best()
+            direct = (X, Y, Fr, tr, P.trace())
+            P.set_option(S.SBO_OPT_USE_GRAPH, 1)
+            P.start(prm)
+            n0 = P.launch_count()
+            P.run(40)
+            counts.append(P.launch_count() - n0)
+            X, Y = P.state()
+            Fr, tr = P.restart_best()
+            assert P.info()["tile_n"] == tile
+            runs.append(direct + (X, Y, Fr, tr, P.trace()))
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            assert np.array_equal(a, b)
+    assert counts[2] < counts[1] < counts[0]
 
 
 def test_dense_n5000_cluster_split_k_sampled_restarts():
