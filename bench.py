@@ -1079,7 +1079,7 @@ def main():
     ap.add_argument("--parts", type=int, default=3, help="maxkcut workload: number of parts k")
     ap.add_argument("--maxk-alpha", type=float, default=0.01, help="maxkcut workload: primal step (paper: 0.01)")
     ap.add_argument("--cert-iters", type=int, default=20000, help="certificate workload: projected gradient steps")
-    ap.add_argument("--tile", type=int, default=0, choices=[0, 64, 128, 256, 512, 1064, 1128, 1256],
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 64, 128, 256, 512, 1064, 1128, 1256, 2128, 2256],
                     help="tensor-core tile width (0: autotuned); profiling cases only")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time the device loop only (no e2e, no CPU baseline): for profiling cases")

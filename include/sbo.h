@@ -224,9 +224,11 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *   SBO_OPT_TILE_N:     restarts per tensor-core tile: 0 auto, 64, 128 or 256 (one SM per
  *                       128-row tile), 512: CTA pairs (two SMs per 256 x 256 tile), or
  *                       1064, 1128, 1256: width 64, 128, 256 with the K dimension of every tile
- *                       split over a thread-block cluster of 2-8 SMs, reduced in distributed
- *                       shared memory (problems with at most half as many tiles as SMs; others
- *                       fall back to the plain width)
+ *                       split over a thread-block cluster of 2-8 SMs, reduced in split order
+ *                       through L2 (problems with at most half as many tiles as SMs; others
+ *                       fall back to the plain width), or 2128, 2256: the same on CTA pairs, tiles
+ *                       of 256 rows x 128 or 256 restarts with the K dimension split over 2-4
+ *                       pairs (others fall back to plain tiles of 64 or 128)
  *   SBO_OPT_AUTOTUNE:   1 (default): with SBO_OPT_TILE_N = 0, sbo_gda_start times the tcgen05
  *                       update kernel at every tile width on the run's own buffers and keeps
  *                       the fastest; decisions are cached per (device, n, B, SM count) in the
@@ -273,7 +275,7 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       graphs with K >= 2: 0 (default) and 2 on a graph branch beside the next
  *                       block's steps, 1 in line after each block.  Results are identical in both
  *   SBO_OPT_STEPS_PER_LAUNCH: largest number of GDA iterations one launch of the cluster split-K
- *                       kernel runs (tile codes 1064-1256, per-coordinate duals): 0 (default)
+ *                       kernel runs (tile codes 1064-2256, per-coordinate duals): 0 (default)
  *                       4,096, 1 one launch per iteration.  The iterations of a launch meet at a
  *                       grid-wide barrier, which needs every cluster of the launch resident at
  *                       once (the kernel is chosen only where they fit in one wave); work of other

@@ -502,7 +502,25 @@ sbo_status read_err(sbo_problem* p);
 // Widest tile that still gives every SM a tile (else the widest), never wider than needed.
 // Tile codes: 64, 128, 256 restarts per single-CTA tile; 512 CTA pairs (256 x 256 tiles);
 // 1000 + w: width w with split-K over a thread-block cluster (small problems).
-int tile_width(int code) { return code == 512 ? 128 : code >= 1000 ? code - 1000 : code; }
+// Restarts per CTA that the operand map of a tile code stages (its box height).
+int tile_width(int code) {
+  return code == 512 ? 128 : code >= 2000 ? (code - 2000) / 2 : code >= 1000 ? code - 1000 : code;
+}
+
+// Restarts per tile of a tile code.
+int tile_restarts(int code) { return code == 512 ? 256 : code >= 2000 ? code - 2000 : tile_width(code); }
+
+// K splits of the cluster split-K codes for this problem (0: not applicable); plan built for the code.
+int csk_factor_for(const sbo_problem* p, int code, const TcPlan& pl) {
+  if (!p->csk_ws || code < 1000) return 0;
+  const int kblocks = (int)((p->n + 63) / 64);
+  if (code >= 2000) {
+    const int bn = code - 2000;
+    const int pair_tiles = (int)((p->n + 255) / 256) * ((p->B + bn - 1) / bn);
+    return tc_cskp_factor(bn, pair_tiles, kblocks, p->sms);
+  }
+  return tc_csk_factor(tile_width(code), pl.num_tiles, kblocks, p->sms);
+}
 
 int heuristic_tile(const sbo_problem* p) {
   int tn = 256;
@@ -540,7 +558,7 @@ std::string tune_key(const sbo_problem* p) {
   for (auto& ch : name)
     if (ch == ' ') ch = '_';
   std::ostringstream k;
-  k << "v4:" << name << ":sms" << p->sms << ":n" << p->n << ":B" << p->B << ":split" << p->opt_split_k
+  k << "v5:" << name << ":sms" << p->sms << ":n" << p->n << ":B" << p->B << ":split" << p->opt_split_k
     << (p->opt_steps_per_launch == 1 ? ":one" : "");
   return k.str();
 }
@@ -549,7 +567,8 @@ std::string tune_key(const sbo_problem* p) {
 bool valid_tile_code(int t) {
   const int code = t % 10000;
   return code == 64 || code == 128 || code == 256 || code == 512 ||
-         ((code == 1064 || code == 1128 || code == 1256) && t / 10000 >= 2 && t / 10000 <= 8);
+         ((code == 1064 || code == 1128 || code == 1256) && t / 10000 >= 2 && t / 10000 <= 8) ||
+         ((code == 2128 || code == 2256) && t / 10000 >= 2 && t / 10000 <= 4);
 }
 
 bool tune_cache_lookup(const std::string& key, int* tile, bool (*valid)(int) = valid_tile_code) {
@@ -611,9 +630,9 @@ sbo_status tune_tile(sbo_problem* p, int* out) {
   a.Xout = p->Xop[1];
   a.bits_out = nullptr;
   sbo_status st = SBO_OK;
-  for (int tn : {64, 128, 256, 512, 1128, 1256}) {
+  for (int tn : {64, 128, 256, 512, 1128, 1256, 2128, 2256}) {
     const int width = tile_width(tn);
-    if (width > 64 && width / 2 >= p->B) continue;
+    if (tile_restarts(tn) > 64 && tile_restarts(tn) / 2 >= p->B) continue;
     if (tn == 512 && !tc_pair_supported(nullptr)) continue;
     TcPlan pl{};
     std::string why;
@@ -622,7 +641,8 @@ sbo_status tune_tile(sbo_problem* p, int* out) {
       continue;
     pl.pair = tn == 512;
     if (tn >= 1000) {
-      pl.csk = p->csk_ws ? tc_csk_factor(width, pl.num_tiles, (int)((p->n + 63) / 64), p->sms) : 0;
+      pl.csk_pair = tn >= 2000;
+      pl.csk = csk_factor_for(p, tn, pl);
       if (pl.csk < 2) continue;
     }
     attach_workspace(p, &pl);
@@ -675,7 +695,7 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
     for (auto& ch : name)
       if (ch == ' ') ch = '_';
     std::ostringstream k;
-    k << "csr2:" << name << ":sms" << p->sms << ":n" << p->n << ":nnz" << p->nnz << ":deg" << p->max_deg << ":B"
+    k << "csr3:" << name << ":sms" << p->sms << ":n" << p->n << ":nnz" << p->nnz << ":deg" << p->max_deg << ":B"
       << p->B << ":op" << p->op_type << ":g" << p->opt_g;
     key = k.str();
   }
@@ -696,7 +716,7 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
   EpiArgs a = base_args(p);
   a.Xin = p->Xop[0];
   a.Xout = p->Xop[1];
-  a.bits_out = p->bits;
+  a.bits_out = nullptr;   // the run writes candidates in one iteration of K
   int best = CSR_FORM_RULE;
   float best_ms = 1e30f;
   sbo_status st = SBO_OK;
@@ -707,8 +727,14 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
   // E4M3: 15.9 -> 18.4 us per iteration), which launches timed back to back on one buffer do not
   // always show.
   const bool streams = p->n * (int64_t)p->B * 16 * 4 > p->l2_bytes * 3;
-  for (int f : {CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_ROW1_STREAM, CSR_FORM_ROW2_STREAM,
-                CSR_FORM_PIPE2_STREAM}) {
+  // Two rounds over the forms, each form's best round counting, so that a clock or cache transient
+  // during one form's timing does not decide.
+  const int forms[] = {CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_ROW1_STREAM, CSR_FORM_ROW2_STREAM,
+                       CSR_FORM_PIPE2_STREAM};
+  float form_ms[8];
+  for (float& v : form_ms) v = 1e30f;
+  for (int round = 0; round < 2 && st == SBO_OK; ++round)
+  for (int f : forms) {
     if (csr_form_streams(f) && !streams) continue;
     int D, S, rc;
     size_t sm;
@@ -728,7 +754,7 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
                               p->stream, f);
     };
     cudaError_t e = launch();
-    const int reps = 20;
+    const int reps = 10;
     if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
     for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch();
     if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
@@ -737,8 +763,10 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
     if (e != cudaSuccess) { st = cuda_fail(e, "sparse autotuner launch"); break; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) { best_ms = ms; best = f; }
+    form_ms[f] = std::min(form_ms[f], ms);
   }
+  for (int f : forms)
+    if (form_ms[f] < best_ms) { best_ms = form_ms[f]; best = f; }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SBO_OK) return st;
@@ -1108,8 +1136,10 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
     case SBO_OPT_USE_GRAPH: p->opt_graph = value != 0; return SBO_OK;
     case SBO_OPT_TILE_N:
       if (value != 0 && value != 64 && value != 128 && value != 256 && value != 512 && value != 1064 &&
-          value != 1128 && value != 1256)
-        return fail(SBO_EINVAL, "tile_n must be 0, 64, 128, 256, 512 (CTA pairs) or 1064, 1128, 1256 (cluster split-K)");
+          value != 1128 && value != 1256 && value != 2128 && value != 2256)
+        return fail(SBO_EINVAL,
+                    "tile_n must be 0, 64, 128, 256, 512 (CTA pairs), 1064, 1128, 1256 (cluster split-K) or 2128, 2256 "
+                    "(cluster split-K on CTA pairs)");
       p->opt_tile_n = (int)value;
       return SBO_OK;
     case SBO_OPT_AUTOTUNE: p->opt_autotune = value != 0; return SBO_OK;
@@ -1273,8 +1303,11 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
       free_run(p);
       return cuda_fail(e, "grid barrier words");
     }
-    // the cluster split-K kernel serves problems with at most sms / 2 tiles (fewest at width 256)
-    if ((int64_t)((p->n + 127) / 128) * ((p->B + 255) / 256) * 2 <= p->sms &&
+    // the cluster split-K kernel serves problems with at most sms / 2 tiles (fewest at width 256),
+    // on CTA pairs at most sms / 4 tiles of 256 x 256
+    if ((p->opt_tile_n == 0 || p->opt_tile_n >= 1000) &&
+        ((int64_t)((p->n + 127) / 128) * ((p->B + 255) / 256) * 2 <= p->sms ||
+         (int64_t)((p->n + 255) / 256) * ((p->B + 255) / 256) * 4 <= p->sms) &&
         (e = dalloc(&p->csk_ws, (size_t)p->sms * 256 * 128, s)) != cudaSuccess) {
       free_run(p);
       return e == cudaErrorMemoryAllocation ? fail(SBO_ENOMEM, "device allocation of the cluster workspace failed")
@@ -1295,11 +1328,16 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
                      tile_width(tn), &why);
     if (e != cudaSuccess) { free_run(p); return fail(SBO_ECUDA, "tensor-core plan: " + why); }
     p->plan.pair = tn == 512;
+    p->plan.csk = 0;
+    p->plan.csk_pair = false;
     if (tn >= 1000) {
-      p->plan.csk = !p->csk_ws   ? 0
-                    : tuned_csk >= 2 ? tuned_csk
-                                     : tc_csk_factor(tile_width(tn), p->plan.num_tiles, (int)((p->n + 63) / 64), p->sms);
-      if (p->plan.csk < 2) tn = tile_width(tn);   // too many tiles for clusters: plain tiles
+      p->plan.csk_pair = tn >= 2000;
+      p->plan.csk = !p->csk_ws ? 0 : tuned_csk >= 2 ? tuned_csk : csk_factor_for(p, tn, p->plan);
+      if (p->plan.csk < 2) {   // too many tiles for clusters: plain tiles of the same width per CTA
+        p->plan.csk = 0;
+        p->plan.csk_pair = false;
+        tn = tile_width(tn);
+      }
     }
     p->tile_n = tn;
     attach_workspace(p, &p->plan);

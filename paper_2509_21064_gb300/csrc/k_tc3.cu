@@ -48,17 +48,20 @@ constexpr int CSK_THREADS = 384;   // warp 0 TMA, warp 1 TMEM + MMA, warps 4-11 
 constexpr int CSK_SMEM_BUDGET = 196 * 1024;
 constexpr int CSK_MIN_KB = 4;      // k-blocks per CTA at least
 
-template <int BN>
+// BN restarts per tile.  PAIR: the tile is 256 rows x BN restarts on a CTA pair (cta_group::2):
+// each CTA stages its own 128 rows of A and BN / 2 restarts of x per k-block.
+template <int BN, bool PAIR>
 struct CskCfg {
+  static constexpr int H = PAIR ? 2 : 1;                  // CTAs per split
   static constexpr int A_BYTES = TC_BM * TC_BK * 2;
-  static constexpr int B_BYTES = BN * TC_BK * 2;
+  static constexpr int B_BYTES = (BN / H) * TC_BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGES =
       (CSK_SMEM_BUDGET - 2048) / STAGE_BYTES > 8 ? 8 : (CSK_SMEM_BUDGET - 2048) / STAGE_BYTES;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /* align */ + 1024 /* barriers */;
   static constexpr int TMEM_COLS = BN;
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                    ((uint32_t)(TC_BM >> 4) << 24);
+                                    ((uint32_t)((TC_BM * H) >> 4) << 24);
   static_assert(STAGES * STAGE_BYTES >= BN * TC_BM * 4, "the partial tile must fit in the stage buffers");
 };
 
@@ -69,9 +72,9 @@ struct CskParams {
   void* xop[2];            // operand buffers: iteration j reads xop[w] and writes xop[w ^ 1], w = (x0 + j) & 1
   void* bits_last;         // candidates written by the last iteration (null: none)
   unsigned int* gbar;      // grid barrier [arrivals, exits, abort], zero between launches (iters > 1)
-  float* ws;               // partial tiles [tile][split][column][row] (>= tiles * S * BN * 128 floats)
+  float* ws;               // partials [tile][split][CTA of the pair][column][row] (one BN x 128 slice per CTA)
   int x0, iters;
-  int n_tiles, kblocks, S;
+  int n_tiles, kblocks, S; // S: K splits per tile (CTA pairs when paired; the cluster holds S CTAs or pairs)
   uint64_t timeout_ns;     // per iteration
 };
 
@@ -109,8 +112,8 @@ constexpr int CSK_CB = 4;   // restart columns per warp whose loads are in fligh
 // group of four rows go element by element.
 template <int BN, int MODE, int GK, bool SINGLE>
 __device__ __forceinline__ void csk_columns(const EpiArgs& a, void* xout, void* bits, const float* part,
-                                            const float* ws_tile, int s, int S, int m_tile, int64_t r0, int c_begin,
-                                            int c_end, int warp, int lane) {
+                                            const float* ws_tile, int64_t split_stride, int s, int S, int m_tile,
+                                            int64_t r0, int c_begin, int c_end, int warp, int lane) {
   const int row0 = 4 * lane;
   const int64_t i0 = (int64_t)m_tile * TC_BM + row0;
   const int64_t left = (int64_t)a.n - i0;
@@ -162,7 +165,7 @@ __device__ __forceinline__ void csk_columns(const EpiArgs& a, void* xout, void* 
 #pragma unroll
         for (int t = 0; t < CSK_CB; ++t) pv[t] = *reinterpret_cast<const float4*>(part + col[t] * TC_BM + row0);
       } else {
-        const float* wsp = ws_tile + (size_t)sp * BN * TC_BM + row0;
+        const float* wsp = ws_tile + (size_t)sp * split_stride + row0;
 #pragma unroll
         for (int t = 0; t < CSK_CB; ++t) pv[t] = __ldcg(reinterpret_cast<const float4*>(wsp + (size_t)col[t] * TC_BM));
       }
@@ -250,10 +253,11 @@ __device__ __forceinline__ void csk_columns(const EpiArgs& a, void* xout, void* 
 
 template <int BN, int MODE>
 __device__ __forceinline__ void csk_epilogue(const EpiArgs& a, void* xout, void* bits, const float* part,
-                                             const float* ws_tile, int s, int S, int m_tile, int64_t r0, int c_begin,
-                                             int c_end, int warp, int lane) {
-#define CSK_COLUMNS(M, G, SG) \
-  csk_columns<BN, M, G, SG>(a, xout, bits, part, ws_tile, s, S, m_tile, r0, c_begin, c_end, warp, lane)
+                                             const float* ws_tile, int64_t split_stride, int s, int S, int m_tile,
+                                             int64_t r0, int c_begin, int c_end, int warp, int lane) {
+#define CSK_COLUMNS(M, G, SG)                                                                                    \
+  csk_columns<BN, M, G, SG>(a, xout, bits, part, ws_tile, split_stride, s, S, m_tile, r0, c_begin, c_end, warp, \
+                            lane)
   if (MODE == EPI_EVAL) {
     CSK_COLUMNS(EPI_EVAL, G_QUAD, false);
   } else if (a.gkind == G_ENTROPY) {
@@ -296,13 +300,14 @@ __device__ __forceinline__ bool grid_wait(const unsigned int* gbar, unsigned int
   return true;
 }
 
-template <int BN, int MODE>
+template <int BN, int MODE, bool PAIR>
 __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant__ CskParams P) {
-  using C = CskCfg<BN>;
+  using C = CskCfg<BN, PAIR>;
+  constexpr int H = C::H;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* tiles = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(tiles + C::STAGES * C::STAGE_BYTES);
-  uint64_t* full_bar = bars;                   // [STAGES]
+  uint64_t* full_bar = bars;                   // [STAGES] (paired: the leader's counts both CTAs' copies)
   uint64_t* empty_bar = bars + C::STAGES;      // [STAGES]
   uint64_t* tfull_bar = bars + 2 * C::STAGES;  // accumulator complete (one phase per iteration)
   uint64_t* drain_bar = tfull_bar + 1;
@@ -314,15 +319,22 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int S = P.S;
-  const uint32_t s = csk_rank();
-  const int tile = (int)(blockIdx.x / (unsigned)S);
+  const int CL = S * H;                        // CTAs per cluster
+  const uint32_t rank = csk_rank();
+  const int sp_me = (int)rank / H;             // this CTA's K split
+  const int h = (int)rank % H;                 // half of the pair (0: leader, issues the MMAs)
+  const uint32_t lead = rank - (uint32_t)h;
+  const uint16_t pair_mask = (uint16_t)(0x3u << lead);
+  const int tile = (int)(blockIdx.x / (unsigned)CL);
   const int m_tile = tile / P.n_tiles, n_tile = tile % P.n_tiles;
-  const int kb0 = (int)((int64_t)s * P.kblocks / S);
-  const int kb1 = (int)((int64_t)(s + 1) * P.kblocks / S);
+  const int mb = m_tile * H + h;               // 128-row block of A this CTA accumulates
+  const int kb0 = (int)((int64_t)sp_me * P.kblocks / S);
+  const int kb1 = (int)((int64_t)(sp_me + 1) * P.kblocks / S);
   const int nk = kb1 - kb0;
-  // restart columns [c_begin, c_end) of the tile are this CTA's: 32-column chunks s NC/S .. (s+1) NC/S - 1
+  // restart columns [c_begin, c_end) of the tile (its rows of this CTA) are this CTA's:
+  // 32-column chunks sp NC/S .. (sp+1) NC/S - 1
   constexpr int NC = BN / 32;
-  const int c_begin = (int)((int)s * NC / S) * 32, c_end = (int)(((int)s + 1) * NC / S) * 32;
+  const int c_begin = (int)(sp_me * NC / S) * 32, c_end = (int)((sp_me + 1) * NC / S) * 32;
   const EpiArgs& a = P.epi;
   const bool multi = P.iters > 1;
 
@@ -343,16 +355,27 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
     if (multi) tma_prefetch_map(&P.mapX[1]);
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)C::TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (PAIR) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"((uint32_t)C::TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                   "r"((uint32_t)C::TMEM_COLS)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if (PAIR) csk_cluster_sync();   // the pair's barriers are initialised and TMEM allocated in both CTAs
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const volatile int* vabort = abort_flag;
+  auto bwait = [&](uint64_t* bar, uint32_t parity, uint64_t dl) {
+    return PAIR ? mbar_wait_cl(smem_u32(bar), parity, dl, vabort) : mbar_wait(smem_u32(bar), parity, dl, vabort);
+  };
 
   // pipeline positions carried across iterations by the producer and the MMA issuer
   int stage = 0;
@@ -371,12 +394,20 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
         if (ok && it > 0) asm volatile("fence.proxy.async.global;" ::: "memory");
         for (int jk = 0; ok && jk < nk; ++jk) {
           const int kb = kb0 + jk;
-          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1u, deadline, vabort)) { ok = false; break; }
-          const uint32_t fb = smem_u32(&full_bar[stage]);
-          mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
+          if (!bwait(&empty_bar[stage], phase ^ 1u, deadline)) { ok = false; break; }
           uint8_t* sa = tiles + stage * C::STAGE_BYTES;
-          tma_load_2d(smem_u32(sa), &P.mapA, fb, kb * TC_BK, m_tile * TC_BM);
-          tma_load_2d(smem_u32(sa + C::A_BYTES), &P.mapX[w], fb, kb * TC_BK, n_tile * BN);
+          if (PAIR) {
+            // both CTAs' copies complete on the leader's barrier, which the leader arms for both
+            const uint32_t fb = map_to_rank(smem_u32(&full_bar[stage]), lead);
+            if (h == 0) mbar_expect_tx(smem_u32(&full_bar[stage]), (uint32_t)(2 * C::STAGE_BYTES));
+            tma_load_2d_pair(smem_u32(sa), &P.mapA, fb, kb * TC_BK, m_tile * 2 * TC_BM + h * TC_BM);
+            tma_load_2d_pair(smem_u32(sa + C::A_BYTES), &P.mapX[w], fb, kb * TC_BK, n_tile * BN + h * (BN / 2));
+          } else {
+            const uint32_t fb = smem_u32(&full_bar[stage]);
+            mbar_expect_tx(fb, (uint32_t)C::STAGE_BYTES);
+            tma_load_2d(smem_u32(sa), &P.mapA, fb, kb * TC_BK, m_tile * TC_BM);
+            tma_load_2d(smem_u32(sa + C::A_BYTES), &P.mapX[w], fb, kb * TC_BK, n_tile * BN);
+          }
           issued_mask |= 1u << stage;
           issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
           if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
@@ -385,37 +416,55 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
           atomicOr(a.err, ERR_TIMEOUT);
           *abort_flag = 1;
           if (multi) atomicExch(P.gbar + 2, 1u);
-          const uint64_t dl2 = globaltimer_ns() + 200000000ull;
-          const int zero = 0;
-          for (int q = 0; q < C::STAGES; ++q)
-            if (issued_mask & (1u << q)) mbar_wait(smem_u32(&full_bar[q]), (issued_parity >> q) & 1u, dl2, &zero);
+          if (PAIR) {
+            // a pair's copies are counted on the leader's barriers, so neither CTA can watch its own
+            // land: give every copy in flight a generous fixed time instead
+            if (issued_mask) {
+              const uint64_t until = globaltimer_ns() + 2000000ull;
+              while (globaltimer_ns() < until) {
+              }
+            }
+          } else {
+            const uint64_t dl2 = globaltimer_ns() + 200000000ull;
+            const int zero = 0;
+            for (int q = 0; q < C::STAGES; ++q)
+              if (issued_mask & (1u << q)) mbar_wait(smem_u32(&full_bar[q]), (issued_parity >> q) & 1u, dl2, &zero);
+          }
         }
       }
     } else if (warp == 1) {
-      // ---------------------------------------------------------------- MMA issuer
-      if (lane == 0 && *vabort == 0) {
+      // ---------------------------------------------------------------- MMA issuer (pair: the leader)
+      if (lane == 0 && h == 0 && *vabort == 0) {
         bool ok = true;
         for (int jk = 0; jk < nk; ++jk) {
-          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, deadline, vabort)) { ok = false; break; }
+          if (!bwait(&full_bar[stage], phase, deadline)) { ok = false; break; }
           tc_fence_after();
           const uint32_t sa = smem_u32(tiles + stage * C::STAGE_BYTES);
           const uint32_t sb = sa + C::A_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < TC_BK / 16; ++kk)
-            tc_mma(tmem_base, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), C::IDESC,
-                   (jk > 0 || kk > 0) ? 1u : 0u);
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            if (PAIR)
+              mma_pair(tmem_base, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), C::IDESC,
+                       (jk > 0 || kk > 0) ? 1u : 0u);
+            else
+              tc_mma(tmem_base, sw128_desc(sa + kk * 32), sw128_desc(sb + kk * 32), C::IDESC,
+                     (jk > 0 || kk > 0) ? 1u : 0u);
+          }
           issued_any = true;
-          tc_commit(smem_u32(&empty_bar[stage]));
+          if (PAIR) commit_pair_multicast(smem_u32(&empty_bar[stage]), pair_mask);
+          else tc_commit(smem_u32(&empty_bar[stage]));
           if (++stage == C::STAGES) { stage = 0; phase ^= 1u; }
         }
         if (ok) {
-          tc_commit(smem_u32(tfull_bar));
+          if (PAIR) commit_pair_multicast(smem_u32(tfull_bar), pair_mask);
+          else tc_commit(smem_u32(tfull_bar));
         } else {
           atomicOr(a.err, ERR_TIMEOUT);
           *abort_flag = 1;
           if (multi) atomicExch(P.gbar + 2, 1u);
           if (issued_any) {
-            tc_commit(smem_u32(drain_bar));
+            if (PAIR) commit_pair_local(smem_u32(drain_bar));
+            else tc_commit(smem_u32(drain_bar));
             const int zero = 0;
             mbar_wait(smem_u32(drain_bar), 0, globaltimer_ns() + 200000000ull, &zero);
           }
@@ -429,12 +478,14 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
       const int wq = warp & 3;
       const int row = wq * 32 + lane;
       if (*vabort == 0) {
-        if (mbar_wait_warp(smem_u32(tfull_bar), (uint32_t)(it & 1), deadline, vabort, lane)) {
+        const bool ready = PAIR ? mbar_wait_cl_warp(smem_u32(tfull_bar), (uint32_t)(it & 1), deadline, vabort, lane)
+                                : mbar_wait_warp(smem_u32(tfull_bar), (uint32_t)(it & 1), deadline, vabort, lane);
+        if (ready) {
           tc_fence_after();
           // columns this CTA owns stay in its shared memory, the others go to its slice of the
           // workspace in L2, where their owners read them
           float* part = reinterpret_cast<float*>(tiles);
-          float* mine = P.ws + ((size_t)tile * S + s) * BN * TC_BM;
+          float* mine = P.ws + (((size_t)tile * S + sp_me) * H + h) * BN * TC_BM;
           float g[32];
           for (int c0 = wg * (BN / 2); c0 < (wg + 1) * (BN / 2); c0 += 32) {
             tmem_ld32(tmem_base + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, g);
@@ -461,8 +512,8 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
       // come from shared memory, not TMEM, so any warp may take any columns.
       void* bits = it + 1 == P.iters ? P.bits_last : nullptr;
       csk_epilogue<BN, MODE>(a, P.xop[w ^ 1], bits, reinterpret_cast<const float*>(tiles),
-                             P.ws + (size_t)tile * S * BN * TC_BM, (int)s, S,
-                             m_tile, (int64_t)n_tile * BN, c_begin, c_end, warp, lane);
+                             P.ws + ((size_t)tile * S * H + h) * BN * TC_BM, (int64_t)H * BN * TC_BM, sp_me, S, mb,
+                             (int64_t)n_tile * BN, c_begin, c_end, warp, lane);
       if (it + 1 < P.iters) fence_stores_for_tma();
     }
     if (threadIdx.x == 0) stop_vote[it & 1] = (*vabort != 0 || (multi && ld_acquire_gpu(P.gbar + 2) != 0u)) ? 1 : 0;
@@ -478,7 +529,7 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
     // above stay matched.
     if (threadIdx.x == 0) {
       int stop = 0;
-      for (int r = 0; r < S; ++r) {
+      for (int r = 0; r < CL; ++r) {
         int v;
         asm volatile("ld.shared::cluster.u32 %0, [%1];"
                      : "=r"(v)
@@ -509,25 +560,39 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
   }
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"((uint32_t)C::TMEM_COLS)
-                 : "memory");
+    if (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                   "r"((uint32_t)C::TMEM_COLS)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                   "r"((uint32_t)C::TMEM_COLS)
+                   : "memory");
   }
 }
 
-template <int BN, int MODE>
+template <int BN, int MODE, bool PAIR>
 cudaError_t csk_set_attr() {
-  return cudaFuncSetAttribute(k_tc_csk<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, CskCfg<BN>::SMEM);
+  return cudaFuncSetAttribute(k_tc_csk<BN, MODE, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              CskCfg<BN, PAIR>::SMEM);
 }
 
-template <int BN>
-cudaLaunchConfig_t csk_config(int grid, int S, cudaLaunchAttribute* attr, cudaStream_t s) {
+template <int BN, bool PAIR>
+cudaError_t csk_set_attrs() {
+  const cudaError_t e = csk_set_attr<BN, EPI_UPDATE, PAIR>();
+  return e == cudaSuccess ? csk_set_attr<BN, EPI_EVAL, PAIR>() : e;
+}
+
+// cluster: CTAs per cluster (S, or 2 S for pairs)
+template <int BN, bool PAIR>
+cudaLaunchConfig_t csk_config(int grid, int cluster, cudaLaunchAttribute* attr, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(CSK_THREADS);
-  cfg.dynamicSmemBytes = CskCfg<BN>::SMEM;
+  cfg.dynamicSmemBytes = CskCfg<BN, PAIR>::SMEM;
   cfg.stream = s;
   attr->id = cudaLaunchAttributeClusterDimension;
-  attr->val.clusterDim.x = (unsigned)S;
+  attr->val.clusterDim.x = (unsigned)cluster;
   attr->val.clusterDim.y = 1;
   attr->val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -535,13 +600,14 @@ cudaLaunchConfig_t csk_config(int grid, int S, cudaLaunchAttribute* attr, cudaSt
   return cfg;
 }
 
-// Clusters of S CTAs of this kernel that fit on the current device at once (0 if none), queried
-// once per (device, S): the attributes and the occupancy answer belong to the device's context.
-template <int BN>
-int csk_max_clusters(int S) {
+// Clusters of `cluster` CTAs of this kernel that fit on the current device at once (0 if none),
+// queried once per (device, cluster size): the attributes and the occupancy answer belong to the
+// device's context.
+template <int BN, bool PAIR>
+int csk_max_clusters(int cluster) {
   static std::mutex mu;
-  static std::vector<std::pair<int, std::array<int, 9>>> cache;   // (device, answer per S)
-  if (S < 2 || S > 8) return 0;
+  static std::vector<std::pair<int, std::array<int, 9>>> cache;   // (device, answer per cluster size)
+  if (cluster < 2 || cluster > 8) return 0;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   std::lock_guard<std::mutex> lock(mu);
@@ -554,26 +620,27 @@ int csk_max_clusters(int S) {
     cache.push_back({dev, fresh});
     row = &cache.back().second;
   }
-  int& slot = (*row)[S];
+  int& slot = (*row)[cluster];
   if (slot >= 0) return slot;
   slot = 0;
-  if (csk_set_attr<BN, EPI_UPDATE>() != cudaSuccess || csk_set_attr<BN, EPI_EVAL>() != cudaSuccess) {
+  if (csk_set_attrs<BN, PAIR>() != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   cudaLaunchAttribute attr;
-  cudaLaunchConfig_t cfg = csk_config<BN>(S * 16, S, &attr, nullptr);
+  cudaLaunchConfig_t cfg = csk_config<BN, PAIR>(cluster * 16, cluster, &attr, nullptr);
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_tc_csk<BN, EPI_UPDATE>, &cfg) == cudaSuccess) slot = n;
+  if (cudaOccupancyMaxActiveClusters(&n, k_tc_csk<BN, EPI_UPDATE, PAIR>, &cfg) == cudaSuccess) slot = n;
   cudaGetLastError();
   return slot;
 }
 
-template <int BN, int MODE>
+template <int BN, int MODE, bool PAIR>
 cudaError_t csk_launch(const CskParams& P, int tiles, cudaStream_t s) {
+  const int cluster = P.S * (PAIR ? 2 : 1);
   cudaLaunchAttribute attr;
-  cudaLaunchConfig_t cfg = csk_config<BN>(tiles * P.S, P.S, &attr, s);
-  return cudaLaunchKernelEx(&cfg, k_tc_csk<BN, MODE>, P);
+  cudaLaunchConfig_t cfg = csk_config<BN, PAIR>(tiles * cluster, cluster, &attr, s);
+  return cudaLaunchKernelEx(&cfg, k_tc_csk<BN, MODE, PAIR>, P);
 }
 
 }  // namespace
@@ -583,9 +650,21 @@ int tc_csk_factor(int tile_n, int num_tiles, int kblocks, int sms) {
   if (num_tiles < 1 || 2 * num_tiles > sms) return 0;
   for (int S = 8; S >= 2; --S) {
     if (kblocks / S < CSK_MIN_KB || num_tiles * S > sms) continue;
-    const int fit = tile_n == 64 ? csk_max_clusters<64>(S) : tile_n == 128 ? csk_max_clusters<128>(S)
-                                                                           : csk_max_clusters<256>(S);
+    const int fit = tile_n == 64    ? csk_max_clusters<64, false>(S)
+                    : tile_n == 128 ? csk_max_clusters<128, false>(S)
+                                    : csk_max_clusters<256, false>(S);
     if (fit >= num_tiles) return S;   // every cluster resident at once: one wave
+  }
+  return 0;
+}
+
+int tc_cskp_factor(int bn, int pair_tiles, int kblocks, int sms) {
+  if (bn != 128 && bn != 256) return 0;
+  if (pair_tiles < 1 || 4 * pair_tiles > sms) return 0;
+  for (int S = 4; S >= 2; --S) {   // clusters of 2 S <= 8 CTAs (portable size)
+    if (kblocks / S < CSK_MIN_KB || pair_tiles * 2 * S > sms) continue;
+    const int fit = bn == 128 ? csk_max_clusters<128, true>(2 * S) : csk_max_clusters<256, true>(2 * S);
+    if (fit >= pair_tiles) return S;
   }
   return 0;
 }
@@ -593,18 +672,17 @@ int tc_csk_factor(int tile_n, int num_tiles, int kblocks, int sms) {
 cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, int iters, uint64_t timeout_ns,
                           cudaStream_t s) {
   if (!plan.ready || plan.csk < 2 || plan.csk > 8 || plan.pair || !plan.csk_ws) return cudaErrorInvalidValue;
+  if (plan.csk_pair && (plan.csk > 4 || (plan.tile_n != 64 && plan.tile_n != 128))) return cudaErrorInvalidValue;
   if (mode != EPI_UPDATE && mode != EPI_EVAL) return cudaErrorInvalidValue;
   if (iters < 1 || (iters > 1 && (mode != EPI_UPDATE || !plan.gbar || which_x > 1 || a.mu))) return cudaErrorInvalidValue;
   // shared-memory attributes (also set by the occupancy query, which a cached decision skips)
   static PerDevice per_device;
   const cudaError_t attr_err = per_device.once([] {
-    cudaError_t r = cudaSuccess;
-    r = r == cudaSuccess ? csk_set_attr<64, EPI_UPDATE>() : r;
-    r = r == cudaSuccess ? csk_set_attr<64, EPI_EVAL>() : r;
-    r = r == cudaSuccess ? csk_set_attr<128, EPI_UPDATE>() : r;
-    r = r == cudaSuccess ? csk_set_attr<128, EPI_EVAL>() : r;
-    r = r == cudaSuccess ? csk_set_attr<256, EPI_UPDATE>() : r;
-    r = r == cudaSuccess ? csk_set_attr<256, EPI_EVAL>() : r;
+    cudaError_t r = csk_set_attrs<64, false>();
+    r = r == cudaSuccess ? csk_set_attrs<128, false>() : r;
+    r = r == cudaSuccess ? csk_set_attrs<256, false>() : r;
+    r = r == cudaSuccess ? csk_set_attrs<128, true>() : r;
+    r = r == cudaSuccess ? csk_set_attrs<256, true>() : r;
     return r;
   });
   if (attr_err != cudaSuccess) return attr_err;
@@ -627,17 +705,29 @@ cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int
   P.iters = iters;
   P.gbar = plan.gbar;
   P.ws = plan.csk_ws;
-  P.n_tiles = (a.B + plan.tile_n - 1) / plan.tile_n;
   P.kblocks = (a.n + TC_BK - 1) / TC_BK;
   P.S = plan.csk;
   P.timeout_ns = timeout_ns;
+  if (plan.csk_pair) {
+    // tiles of 256 rows x 2 tile_n restarts (the operand map's box holds one CTA's half)
+    const int bn = 2 * plan.tile_n;
+    P.n_tiles = (a.B + bn - 1) / bn;
+    const int tiles = ((a.n + 2 * TC_BM - 1) / (2 * TC_BM)) * P.n_tiles;
+    if (bn == 128)
+      return mode == EPI_UPDATE ? csk_launch<128, EPI_UPDATE, true>(P, tiles, s) : csk_launch<128, EPI_EVAL, true>(P, tiles, s);
+    return mode == EPI_UPDATE ? csk_launch<256, EPI_UPDATE, true>(P, tiles, s) : csk_launch<256, EPI_EVAL, true>(P, tiles, s);
+  }
+  P.n_tiles = (a.B + plan.tile_n - 1) / plan.tile_n;
   const int tiles = ((a.n + TC_BM - 1) / TC_BM) * P.n_tiles;
   switch (plan.tile_n) {
-    case 64: return mode == EPI_UPDATE ? csk_launch<64, EPI_UPDATE>(P, tiles, s) : csk_launch<64, EPI_EVAL>(P, tiles, s);
+    case 64:
+      return mode == EPI_UPDATE ? csk_launch<64, EPI_UPDATE, false>(P, tiles, s) : csk_launch<64, EPI_EVAL, false>(P, tiles, s);
     case 128:
-      return mode == EPI_UPDATE ? csk_launch<128, EPI_UPDATE>(P, tiles, s) : csk_launch<128, EPI_EVAL>(P, tiles, s);
+      return mode == EPI_UPDATE ? csk_launch<128, EPI_UPDATE, false>(P, tiles, s)
+                                : csk_launch<128, EPI_EVAL, false>(P, tiles, s);
     default:
-      return mode == EPI_UPDATE ? csk_launch<256, EPI_UPDATE>(P, tiles, s) : csk_launch<256, EPI_EVAL>(P, tiles, s);
+      return mode == EPI_UPDATE ? csk_launch<256, EPI_UPDATE, false>(P, tiles, s)
+                                : csk_launch<256, EPI_EVAL, false>(P, tiles, s);
   }
 }
 

@@ -143,7 +143,8 @@ struct TcPlan {
   int* counters;           // >= sms * 8 ints, zero before the first launch
   int max_splits;
   bool pair;               // CTA-pair kernel (k_tc2.cu): 256 x 256 tiles; tile_n is then 128
-  int csk;                 // >= 2: split-K over a cluster of csk CTAs per tile (k_tc3.cu)
+  int csk;                 // >= 2: split-K over a cluster of csk CTAs (csk_pair: CTA pairs) per tile (k_tc3.cu)
+  bool csk_pair;           // csk on CTA pairs: tiles of 256 rows x 2 tile_n restarts
   unsigned int* gbar;      // csk: grid barrier words of the multi-iteration launch (3, zero between launches)
   float* csk_ws;           // csk: partial tiles exchanged through L2 (>= sms * 256 * 128 floats)
   bool ready;
@@ -182,6 +183,8 @@ bool tc_pair_supported(int* max_clusters);
 // buffers alternating from which_x, candidates written by the last one when a.bits_out is set),
 // with a grid barrier between iterations (plan.gbar); not with the single-constraint dual.
 int tc_csk_factor(int tile_n, int num_tiles, int kblocks, int sms);
+// CTA pairs: K splits (pairs per cluster, 2-4) for pair_tiles tiles of 256 rows x bn restarts
+int tc_cskp_factor(int bn, int pair_tiles, int kblocks, int sms);
 cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, int iters, uint64_t timeout_ns,
                           cudaStream_t s);
 cudaError_t launch_tc_pair(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,

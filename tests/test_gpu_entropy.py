@@ -68,6 +68,7 @@ def _check(gx, gy, A, cp, p, tol, prec):
     (600, 300, S.SBO_BF16, S.KERNEL_TC, 512, 2e-2),
     (1000, 256, S.SBO_BF16, S.KERNEL_TC, 1256, 2e-2),
     (1003, 200, S.SBO_BF16, S.KERNEL_TC, 1256, 2e-2),
+    (1003, 200, S.SBO_BF16, S.KERNEL_TC, 2256, 2e-2),
 ])
 def test_entropy_dense_parity(n, B, prec, kernel, tile, tol):
     Q, c = W.dense_qubo(n, seed=n + 5)

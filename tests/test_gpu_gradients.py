@@ -45,6 +45,7 @@ BOUNDS = {
     "csk1064": (2e-07, 2e-03, 5e-03, 2e-04),
     "csk1128": (2e-07, 9e-04, 5e-03, 3e-04),
     "csk1256": (2e-07, 2e-03, 4e-03, 2e-04),
+    "cskp2256": (2e-07, 2e-03, 4e-03, 2e-04),
     "csr_fp32": (5e-07, 5e-07, 2e-06, 6e-06),
     "csr_bf16": (8e-08, 5e-03, 2e-02, 2e-04),
     "csr_e4m3": (8e-08, 5e-03, 2e-02, 2e-04),
@@ -85,6 +86,7 @@ KERNELS = {
     "csk1064": ("dense", 700, 100, S.SBO_BF16, S.KERNEL_TC, 1064),
     "csk1128": ("dense", 2000, 200, S.SBO_BF16, S.KERNEL_TC, 1128),
     "csk1256": ("dense", 1000, 256, S.SBO_BF16, S.KERNEL_TC, 1256),
+    "cskp2256": ("dense", 1000, 256, S.SBO_BF16, S.KERNEL_TC, 2256),
     "csr_fp32": ("er", 2000, 256, S.SBO_FP32, 0, 0),
     "csr_bf16": ("er", 2000, 256, S.SBO_BF16, 0, 0),
     "csr_e4m3": ("er", 2000, 256, S.SBO_FP8_E4M3, 0, 0),

@@ -155,11 +155,12 @@ def test_tcgen05_split_k_tail_tiles(n, B, tile):
 
 
 @pytest.mark.parametrize("n,B,tile", [(1000, 256, 1256), (2000, 200, 1128), (700, 100, 1064), (1001, 250, 1256),
-                                       (1999, 200, 1128), (702, 100, 1064)])
+                                       (1999, 200, 1128), (702, 100, 1064), (1001, 250, 2256), (2000, 256, 2128),
+                                       (1999, 200, 2256)])
 def test_tcgen05_cluster_split_k(n, B, tile):
-    """Small problems with K split over a thread-block cluster and the partials summed through
-    distributed shared memory in split order (ragged rows and restarts; n = 1001, 702 and 1999
-    leave one, two and three rows in the last group of four rows a lane updates): trajectories within the
+    """Small problems with K split over a thread-block cluster (2128, 2256: over CTA pairs) and the
+    partials summed in split order (ragged rows and restarts; n = 1001, 702 and 1999 leave one,
+    two and three rows in the last group of four rows a lane updates): trajectories within the
     mixed tolerance of the oracle, exact objectives, graph replay identical to direct launches,
     and the same iterates as plain tiles of the same width up to the mixed tolerance."""
     Q, c = W.dense_qubo(n, seed=n + 3)
@@ -177,14 +178,14 @@ def test_tcgen05_cluster_split_k(n, B, tile):
         X, Y = P.state()
         assert np.array_equal(X, gx[30]) and np.array_equal(Y, gy[30])
     with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
-        P.set_option(S.SBO_OPT_TILE_N, tile - 1000)
+        P.set_option(S.SBO_OPT_TILE_N, tile % 1000)
         P.start(prm)
         P.run(30)
         Xp, _ = P.state()
     assert normwise(X, Xp).max() <= TOL_MIXED
 
 
-@pytest.mark.parametrize("n,B,tile", [(1001, 250, 1256), (2000, 256, 1128)])
+@pytest.mark.parametrize("n,B,tile", [(1001, 250, 1256), (2000, 256, 1128), (1001, 250, 2256)])
 def test_cluster_split_k_iterations_per_launch(n, B, tile):
     """Several GDA iterations in one launch of the cluster split-K kernel (grid barrier between
     them) against one launch per iteration: bit-identical iterates, duals, per-restart records

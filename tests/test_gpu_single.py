@@ -55,6 +55,7 @@ def _dense_case(n, B, prec, kernel, tile=0):
     (600, 300, S.SBO_BF16, S.KERNEL_TC, 512, 2e-2),
     (1000, 256, S.SBO_BF16, S.KERNEL_TC, 1256, 2e-2),
     (1003, 200, S.SBO_BF16, S.KERNEL_TC, 1256, 2e-2),
+    (1003, 200, S.SBO_BF16, S.KERNEL_TC, 2256, 2e-2),
 ])
 def test_single_dual_dense_parity(n, B, prec, kernel, tile, tol):
     Q, c, p, P = _dense_case(n, B, prec, kernel, tile)

@@ -12,10 +12,10 @@ from paper_2509_21064_gb300.build import build as build_lib
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,B,tile", [(8192, 1024, 128), (4096, 256, 1256)])
+@pytest.mark.parametrize("n,B,tile", [(8192, 1024, 128), (4096, 256, 1256), (4096, 256, 2256)])
 def test_bounded_waits_report_timeout_and_the_context_survives(n, B, tile):
-    """tile 128: persistent single-CTA tiles; 1256: K split over thread-block clusters, whose
-    CTAs still reach both cluster barriers after giving up."""
+    """tile 128: persistent single-CTA tiles; 1256, 2256: K split over thread-block clusters (of
+    CTA pairs), whose CTAs still reach every cluster barrier after giving up."""
     build_lib()
     Q, c = W.dense_qubo(n, seed=4)
     p = W.dense_params(Q, restarts=B, iters=100, eval_every=10, seed=2)
