@@ -461,12 +461,13 @@ def test_dense_n5000_bf16_lagrangian_and_autograd():
 
 
 @pytest.mark.parametrize("case", range(3))
-@pytest.mark.parametrize("path", ["tiny", "simt", "tc", "tc512", "tc1064", "tc1128", "tc1256", "csr32", "csr_bf16"])
+@pytest.mark.parametrize("path", ["tiny", "simt", "tc", "tc512", "tc1064", "tc1128", "tc1256", "tc2128", "tc2256",
+                                  "csr32", "csr_bf16"])
 def test_hand_worked_iterations_on_every_kernel(case, path):
     """The hand-worked Algorithm-1 iterations of tests/golden (perturbation rule with both
     boundary equalities, active projection, plain steps) reproduced exactly by every kernel,
     iterates and the gradient d each step used: every number is dyadic and exact in FP32 and BF16.
-    The CTA-pair (512) and cluster split-K (1064, 1128, 1256) kernels need more rows than the
+    The CTA-pair (512) and cluster split-K (1064, 1128, 1256; on CTA pairs 2128, 2256) kernels need more rows than the
     hand-worked problem has: it is embedded in a problem of 600 variables whose other rows and
     columns are zero, so the worked coordinates see exactly the worked sums."""
     import json
@@ -514,6 +515,12 @@ def test_hand_worked_iterations_on_every_kernel(case, path):
             assert np.array_equal(X[0, :m], np.array(g["x"][t], dtype=np.float32)), (t, X[0, :m])
             assert np.array_equal(Y[0, :m], np.array(g["y"][t], dtype=np.float32)), (t, Y[0, :m])
             assert np.array_equal(D[0, :m], np.array(g["d"][t], dtype=np.float32)), (t, D[0, :m])
+        # all T iterations in one call (one launch of the cluster kernels): the same last iterate
+        P.start(prm, x0, y0)
+        P.run(T)
+        X, Y = P.state()
+        assert np.array_equal(X[0, :m], np.array(g["x"][T - 1], dtype=np.float32))
+        assert np.array_equal(Y[0, :m], np.array(g["y"][T - 1], dtype=np.float32))
 
 
 @pytest.mark.parametrize("kind", ["tc", "csr"])
