@@ -635,13 +635,64 @@ int csk_max_clusters(int cluster) {
   return slot;
 }
 
+// Whether the current device takes cooperative launches of clusters: 1 yes, 0 no, -1 not known yet.
+std::mutex coop_mu;
+std::vector<std::pair<int, int>> coop_answer;
+int coop_state(int dev) {
+  std::lock_guard<std::mutex> lock(coop_mu);
+  for (const auto& d : coop_answer)
+    if (d.first == dev) return d.second;
+  return -1;
+}
+void coop_record(int dev, int ok) {
+  std::lock_guard<std::mutex> lock(coop_mu);
+  for (auto& d : coop_answer)
+    if (d.first == dev) { d.second = ok; return; }
+  coop_answer.push_back({dev, ok});
+}
+
+// A launch of several iterations asks to be cooperative: its CTAs wait for one another at the
+// grid barrier, and a cooperative launch is scheduled only when all of them can be resident at
+// once, also beside kernels of other streams that hold SMs.  A device that refuses the attribute
+// together with clusters is remembered and launched plainly (the launch is one wave of clusters
+// either way).  The first attempt is never made during stream capture, where a refused launch
+// would end the capture.
 template <int BN, int MODE, bool PAIR>
 cudaError_t csk_launch(const CskParams& P, int tiles, cudaStream_t s) {
   const int cluster = P.S * (PAIR ? 2 : 1);
-  cudaLaunchAttribute attr;
-  cudaLaunchConfig_t cfg = csk_config<BN, PAIR>(tiles * cluster, cluster, &attr, s);
+  cudaLaunchAttribute attrs[2];
+  cudaLaunchConfig_t cfg = csk_config<BN, PAIR>(tiles * cluster, cluster, &attrs[0], s);
+  if (P.iters > 1) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int known = coop_state(dev);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (known < 0 && (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)) {
+      cudaGetLastError();
+      known = 0;   // decide outside capture; this launch goes plain
+    } else if (known != 0) {
+      attrs[1].id = cudaLaunchAttributeCooperative;
+      attrs[1].val.cooperative = 1;
+      cfg.numAttrs = 2;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_tc_csk<BN, MODE, PAIR>, P);
+      if (known < 0) coop_record(dev, e == cudaSuccess ? 1 : 0);
+      if (e == cudaSuccess || known > 0) return e;
+      cudaGetLastError();
+      cfg.numAttrs = 1;
+    }
+  }
   return cudaLaunchKernelEx(&cfg, k_tc_csk<BN, MODE, PAIR>, P);
 }
+
+}  // namespace
+
+int tc_csk_cooperative() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  return coop_state(dev);
+}
+
+namespace {
 
 }  // namespace
 

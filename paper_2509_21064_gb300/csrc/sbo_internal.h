@@ -185,6 +185,9 @@ bool tc_pair_supported(int* max_clusters);
 int tc_csk_factor(int tile_n, int num_tiles, int kblocks, int sms);
 // CTA pairs: K splits (pairs per cluster, 2-4) for pair_tiles tiles of 256 rows x bn restarts
 int tc_cskp_factor(int bn, int pair_tiles, int kblocks, int sms);
+// Whether multi-iteration cluster launches on the current device are cooperative (1), plain (0) or
+// not launched yet (-1).
+int tc_csk_cooperative();
 cudaError_t launch_tc_csk(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, int iters, uint64_t timeout_ns,
                           cudaStream_t s);
 cudaError_t launch_tc_pair(const TcPlan& plan, int which_x, const EpiArgs& a, int mode, uint64_t timeout_ns,

@@ -220,6 +220,42 @@ def test_cluster_split_k_iterations_per_launch(n, B, tile):
     assert counts[2] < counts[1] < counts[0]
 
 
+def test_cluster_launches_of_two_streams_at_once():
+    """Two multi-iteration launches of the cluster kernel on two streams at once, each needing 120
+    of the SMs, so that they cannot both be resident: each still completes (its launch is
+    scheduled whole; CTAs of a partly resident launch would wait at the grid barrier until the
+    wait limit) and gives the same bits as when it runs alone."""
+    import torch
+    n, B = 5000, 256
+    Q, c = W.dense_qubo(n, seed=21)
+    prms = [to_gda_params(W.dense_params(Q, restarts=B, iters=10**6, eval_every=50, seed=s)) for s in (1, 2)]
+    alone = []
+    for prm in prms:
+        with S.Problem.dense(Q, c, precision=S.SBO_BF16) as P:
+            P.set_option(S.SBO_OPT_TILE_N, 2256)
+            P.set_option(S.SBO_OPT_USE_GRAPH, 0)
+            P.start(prm)
+            P.run(50)
+            alone.append(P.state())
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    probs = [S.Problem.dense(Q, c, precision=S.SBO_BF16, stream=st) for st in streams]
+    try:
+        for P, prm in zip(probs, prms):
+            P.set_option(S.SBO_OPT_TILE_N, 2256)
+            P.set_option(S.SBO_OPT_USE_GRAPH, 0)
+            P.start(prm)
+            P.sync()
+        for P in probs:
+            P.run(50)                 # both enqueued before either is waited for
+        for P, (X0, Y0) in zip(probs, alone):
+            X, Y = P.state()
+            assert P.info()["tile_n"] == 2256
+            assert np.array_equal(X, X0) and np.array_equal(Y, Y0)
+    finally:
+        for P in probs:
+            P.close()
+
+
 def test_dense_n5000_cluster_split_k_sampled_restarts():
     """Dense QUBO n = 5,000, B = 256 with the cluster split-K kernel (width 256, 40 tiles):
     three iterations, restarts 0, 128 and 255 against the oracle on those restarts alone, and
