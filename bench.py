@@ -1072,10 +1072,10 @@ def main():
                     help="dense n=20k (the headline) or a sparse Max-Cut workload (kernel-only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "e4m3"],
                     help="weight/operand precision of a sparse workload")
-    ap.add_argument("--csr-form", type=int, default=0, choices=list(range(8)),
+    ap.add_argument("--csr-form", type=int, default=0, choices=list(range(9)),
                     help="sparse workloads: update form (0 autotuned; 1, 2 one row per warp with 128 / 256 "
                          "restarts; 3 pipelined rows; 4 rows staged by bulk copies; 5-7: 1-3 with L2 "
-                         "eviction priorities)")
+                         "eviction priorities; 8 state resident in shared memory, iterations per launch)")
     ap.add_argument("--no-eval", action="store_true", help="sparse workloads: no evaluations (update launches only)")
     ap.add_argument("--eval-mode", type=int, default=0, choices=[0, 1, 2],
                     help="sparse workloads: evaluation scheduling (0, 2 beside the next block; 1 in line)")

@@ -268,19 +268,24 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       restarts per warp), 4 rows staged in shared memory by bulk copies (a
  *                       producer warp and four consumer warps per CTA), 5, 6, 7 the forms 1, 2, 3
  *                       with L2 eviction priorities for state that overflows L2 (each row's own x
- *                       and y evict-first, the operand written for the next iteration evict-last).
- *                       Results are identical in every form; the single-constraint form
- *                       (SBO_OPT_DUAL = 1) keeps the rule
+ *                       and y evict-first, the operand written for the next iteration evict-last),
+ *                       8 resident: one cooperative CTA per SM keeps its rows' x, y and structure in
+ *                       shared memory for all the iterations of a launch (grid barrier between
+ *                       them; graphs whose state fits, about n B <= 3.6e6 on 152 SMs; evaluations
+ *                       then run after each block, not beside the next; explicit only, not an
+ *                       autotuner candidate).  Results are identical in
+ *                       every form; the single-constraint form (SBO_OPT_DUAL = 1) keeps the rule
  *   SBO_OPT_EVAL_MODE:  scheduling of the evaluations of sparse and Max-k-Cut runs replayed from
  *                       graphs with K >= 2: 0 (default) and 2 on a graph branch beside the next
  *                       block's steps, 1 in line after each block.  Results are identical in both
  *   SBO_OPT_STEPS_PER_LAUNCH: largest number of GDA iterations one launch of the cluster split-K
- *                       kernel runs (tile codes 1064-2256, per-coordinate duals): 0 (default)
+ *                       kernel (tile codes 1064-2256) or of the resident sparse form (SBO_OPT_CSR_FORM
+ *                       8) runs, with per-coordinate duals: 0 (default)
  *                       4,096, 1 one launch per iteration.  The iterations of a launch meet at a
- *                       grid-wide barrier, which needs every cluster of the launch resident at
- *                       once (the kernel is chosen only where they fit in one wave); work of other
- *                       streams that holds SMs longer than SBO_OPT_TIMEOUT_US makes the launch
- *                       return early with SBO_ETIMEOUT.  Results are identical for every value */
+ *                       grid-wide barrier, so such a launch is cooperative (scheduled only when all
+ *                       its CTAs can be resident at once); a wait that outlasts SBO_OPT_TIMEOUT_US
+ *                       makes the launch return early with SBO_ETIMEOUT.  Results are identical for
+ *                       every value */
 enum { SBO_OPT_KERNEL = 1, SBO_OPT_USE_GRAPH = 2, SBO_OPT_TILE_N = 3, SBO_OPT_TIMEOUT_US = 4, SBO_OPT_SPLIT_K = 5,
        SBO_OPT_AUTOTUNE = 6, SBO_OPT_PDL = 7, SBO_OPT_DUAL = 8, SBO_OPT_G = 9, SBO_OPT_KEEP_GRAD = 10,
        SBO_OPT_CSR_FORM = 11, SBO_OPT_EVAL_MODE = 12, SBO_OPT_STEPS_PER_LAUNCH = 13 };

@@ -96,6 +96,7 @@ struct sbo_problem {
   int val_type = 0;
   int64_t nnz = 0;
   int max_deg = 0;             // longest row of A (CSR)
+  int res_nnz_max = 0;         // most nonzeros of A in one CTA's rows of the resident sparse form
   int kparts = 0;              // Max-k-Cut: parts per vertex (FMT_MAXK)
   // linear term
   float* cp = nullptr;
@@ -265,6 +266,9 @@ cudaError_t contract(sbo_problem* p, const EpiArgs& a, int mode, int which_x, cu
     case KER_SIMT: return launch_simt(static_cast<const float*>(p->A), p->lda, a, mode, s);
     case KER_TC: return launch_tc(p->plan, which_x, nullptr, a, mode, timeout_ns(p), s);
     case KER_CSR:
+      if (mode == EPI_UPDATE && p->csr_form == CSR_FORM_RESIDENT && !a.mu)
+        return launch_csr_res(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, which_x, p->Xop, 1,
+                              p->res_nnz_max, p->sms, p->tc_gbar, timeout_ns(p), s);
       if (mode == EPI_UPDATE && p->csr_form == CSR_FORM_STAGED && !a.mu)
         return launch_csr_staged(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, p->max_deg, p->sms,
                                  pdl && p->opt_pdl != 0, timeout_ns(p), s);
@@ -293,7 +297,9 @@ cudaError_t enqueue_step(sbo_problem* p, bool write_bits, cudaStream_t s) {
 // Iterations one launch may run: several for the cluster split-K kernel with per-coordinate
 // duals (grid barrier between them), else one.
 int64_t steps_per_launch(const sbo_problem* p) {
-  if (p->kernel != KER_TC || p->plan.csk < 2 || p->plan.pair || p->single || !p->tc_gbar) return 1;
+  const bool csk = p->kernel == KER_TC && p->plan.csk >= 2 && !p->plan.pair;
+  const bool res = p->kernel == KER_CSR && p->csr_form == CSR_FORM_RESIDENT;
+  if (!(csk || res) || p->single || !p->tc_gbar) return 1;
   return p->opt_steps_per_launch == 0 ? 4096 : p->opt_steps_per_launch;
 }
 
@@ -321,7 +327,10 @@ cudaError_t enqueue_steps(sbo_problem* p, int64_t steps, bool write_bits, cudaSt
     a.Xout = p->Xop[p->cur ^ 1];
     a.bits_out = write_bits && done == steps ? p->bits : nullptr;
     ++p->launches;
-    cudaError_t e = launch_tc_csk(p->plan, p->cur, a, EPI_UPDATE, (int)chunk, timeout_ns(p), s);
+    cudaError_t e = p->kernel == KER_CSR
+                        ? launch_csr_res(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, p->cur, p->Xop,
+                                         (int)chunk, p->res_nnz_max, p->sms, p->tc_gbar, timeout_ns(p), s)
+                        : launch_tc_csk(p->plan, p->cur, a, EPI_UPDATE, (int)chunk, timeout_ns(p), s);
     if (e != cudaSuccess) return e;
     if (chunk & 1) p->cur ^= 1;
   }
@@ -379,8 +388,9 @@ int64_t next_eval_after(const sbo_problem* p, int64_t t) {
 // torus 17.5 us): the fused kernel's registers cost it occupancy.  SBO_OPT_EVAL_MODE 1 forces the
 // evaluation in line.
 bool defer_evals(const sbo_problem* p) {
+  // (not beside the resident form: its cooperative launch holds every SM)
   return (p->kernel == KER_CSR || p->kernel == KER_MAXK) && p->prm.eval_every >= 2 && p->opt_graph &&
-         p->opt_eval_mode != 1;
+         p->opt_eval_mode != 1 && !(p->kernel == KER_CSR && p->csr_form == CSR_FORM_RESIDENT);
 }
 
 // Evaluate the deferred candidates (those of iteration t) on the problem's stream.
@@ -695,7 +705,7 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
     for (auto& ch : name)
       if (ch == ' ') ch = '_';
     std::ostringstream k;
-    k << "csr3:" << name << ":sms" << p->sms << ":n" << p->n << ":nnz" << p->nnz << ":deg" << p->max_deg << ":B"
+    k << "csr4:" << name << ":sms" << p->sms << ":n" << p->n << ":nnz" << p->nnz << ":deg" << p->max_deg << ":B"
       << p->B << ":op" << p->op_type << ":g" << p->opt_g;
     key = k.str();
   }
@@ -729,6 +739,10 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
   const bool streams = p->n * (int64_t)p->B * 16 * 4 > p->l2_bytes * 3;
   // Two rounds over the forms, each form's best round counting, so that a clock or cache transient
   // during one form's timing does not decide.
+  // The resident form (CSR_FORM_RESIDENT) is not a candidate: its updates are faster (Max-Cut ER
+  // n = 2,000, B = 256: 3.8 us per iteration against about 5), but its evaluations cannot run beside
+  // the next block (its cooperative launch holds every SM), which costs more than that in a run
+  // with an evaluation every 10 iterations (5.7 against 5.5 us per iteration, FP32).
   const int forms[] = {CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_ROW1_STREAM, CSR_FORM_ROW2_STREAM,
                        CSR_FORM_PIPE2_STREAM};
   float form_ms[8];
@@ -753,8 +767,8 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
                  : launch_csr(p->rowptr, p->col, p->val, p->val_type, b, p->op_type, EPI_UPDATE, p->opt_pdl != 0,
                               p->stream, f);
     };
-    cudaError_t e = launch();
     const int reps = 10;
+    cudaError_t e = launch();
     if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
     for (int k = 0; k < reps && e == cudaSuccess; ++k) e = launch();
     if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
@@ -1012,6 +1026,11 @@ sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const i
   p->prec = precision;
   p->nnz = (int64_t)cc.size();
   for (int64_t i = 0; i < n; ++i) p->max_deg = std::max<int>(p->max_deg, rp[i + 1] - rp[i]);
+  {
+    const int64_t G = std::min<int64_t>(n, std::max(1, p->sms));   // rows split as k_csr_res splits them
+    for (int64_t b = 0; b < G; ++b)
+      p->res_nnz_max = std::max<int>(p->res_nnz_max, rp[(b + 1) * n / G] - rp[b * n / G]);
+  }
   auto bail = [&](sbo_status s) { free_all(p); delete p; return s; };
   // weights in the storage type (exact by the checks above)
   std::vector<uint8_t> vbytes;
@@ -1162,7 +1181,7 @@ sbo_status sbo_set_option(sbo_problem* p, int32_t option, int64_t value) {
       p->opt_eval_mode = (int)value;
       return SBO_OK;
     case SBO_OPT_CSR_FORM:
-      if (value < 0 || value > CSR_FORM_PIPE2_STREAM) return fail(SBO_EINVAL, "sparse form must be 0..7");
+      if (value < 0 || value > CSR_FORM_RESIDENT) return fail(SBO_EINVAL, "sparse form must be 0..8");
       p->opt_csr_form = (int)value;
       return SBO_OK;
     case SBO_OPT_STEPS_PER_LAUNCH:
@@ -1346,6 +1365,12 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
   }
   p->csr_form = CSR_FORM_RULE;
   if (ker == KER_CSR && !p->single) {
+    // grid barrier words of the resident form (allocated before the autotuner, which times it)
+    if ((e = dalloc(&p->tc_gbar, 3, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->tc_gbar, 0, 3 * sizeof(unsigned int), s)) != cudaSuccess) {
+      free_run(p);
+      return cuda_fail(e, "grid barrier words");
+    }
     if (p->opt_csr_form != 0) {
       p->csr_form = p->opt_csr_form;
     } else if (p->opt_autotune) {
@@ -1358,6 +1383,9 @@ sbo_status sbo_gda_start_xy(sbo_problem* p, const sbo_gda_params* prm, const flo
     size_t sm;
     if (p->csr_form == CSR_FORM_STAGED && !csr_staged_shape(p->ld, p->op_type, p->max_deg, &D, &S, &rc, &sm))
       p->csr_form = CSR_FORM_RULE;
+    int rg;
+    if (p->csr_form == CSR_FORM_RESIDENT && !csr_res_shape(p->n, p->B, p->sms, p->res_nnz_max, &rg, &sm))
+      p->csr_form = CSR_FORM_RULE;   // the state does not fit in shared memory
     p->tile_n = p->csr_form;   // reported by sbo_info
   }
   float* x0d = nullptr;

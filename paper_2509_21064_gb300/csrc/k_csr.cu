@@ -528,4 +528,240 @@ cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* va
   return cudaErrorInvalidValue;
 }
 
+// ---- resident form (CSR_FORM_RESIDENT) -----------------------------------------------------------
+// Small graphs whose state fits in the SMs' shared memory: one cooperative CTA per SM owns the
+// contiguous rows [b n / G, (b+1) n / G) and keeps their x, y and structure (local row offsets,
+// columns, weights) in shared memory for all the iterations of a launch.  An iteration gathers the
+// neighbours' operand x^t from L2 (bypassing L1: the two operand buffers alternate within the
+// launch), applies the same fused update as k_csr in the same order of operations (bit-identical),
+// writes the rows' x^{t+1} operand to global memory and meets the other CTAs at the grid barrier.
+// x and y go back to global memory at the end of the launch.  What it saves against one launch
+// per iteration is the kernel boundary and every load and store of the own state.
+constexpr int RES_THREADS = 1024;
+
+struct ResParams {
+  const int32_t* rowptr;
+  const int32_t* col;
+  const void* val;
+  int vt;
+  EpiArgs a;               // Xin / Xout / bits_out are taken from xop / bits_last
+  void* xop[2];            // iteration j reads xop[(x0 + j) & 1] and writes the other one
+  void* bits_last;         // candidate bytes written by the last iteration (null: none)
+  unsigned int* gbar;      // grid barrier [arrivals, exits, abort] (iters > 1)
+  int x0, iters;
+  int rows_max, nnz_max, Bp;   // shared-memory extents: rows, nonzeros per CTA, restarts per row
+  uint64_t timeout_ns;     // per iteration
+};
+
+template <int OPT>
+__device__ __forceinline__ float4 ldcg4(const void* p, int64_t idx) {
+  if (OPT == OP_F32) return __ldcg(reinterpret_cast<const float4*>(static_cast<const float*>(p) + idx));
+  const uint2 raw = __ldcg(reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(p) + idx));
+  const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+  const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+  return make_float4(__low2float(lo), __high2float(lo), __low2float(hi), __high2float(hi));
+}
+
+size_t res_smem_bytes(int rows_max, int nnz_max, int Bp) {
+  return (size_t)rows_max * Bp * 8 + (size_t)(rows_max + 1) * 4 + (size_t)nnz_max * 8 + 16;
+}
+
+template <int OPT, int GK>
+__global__ void __launch_bounds__(RES_THREADS, 1) k_csr_res(const __grid_constant__ ResParams P) {
+  extern __shared__ __align__(16) uint8_t res_smem[];
+  __shared__ int s_stop;
+  const EpiArgs& a = P.a;
+  const int n = a.n, B = a.B, Bp = P.Bp;
+  const int64_t ld = a.ld;
+  const int G = (int)gridDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+  const int r_begin = (int)((int64_t)blockIdx.x * n / G), r_end = (int)((int64_t)(blockIdx.x + 1) * n / G);
+  const int R = r_end - r_begin;
+  float* xs = reinterpret_cast<float*>(res_smem);                 // [rows_max][Bp]
+  float* ys = xs + (size_t)P.rows_max * Bp;                       // [rows_max][Bp]
+  int* rp = reinterpret_cast<int*>(ys + (size_t)P.rows_max * Bp);   // [rows_max + 1]
+  int* cs = rp + P.rows_max + 1;                                  // [nnz_max]
+  float* wv = reinterpret_cast<float*>(cs + P.nnz_max);           // [nnz_max]
+
+  // structure and state of the owned rows
+  const int e_begin = __ldg(P.rowptr + r_begin);
+  const int e_count = __ldg(P.rowptr + r_end) - e_begin;
+  for (int t = tid; t <= R; t += blockDim.x) rp[t] = __ldg(P.rowptr + r_begin + t) - e_begin;
+  for (int t = tid; t < e_count; t += blockDim.x) {
+    cs[t] = __ldg(P.col + e_begin + t);
+    wv[t] = load_val(P.val, e_begin + t, P.vt);
+  }
+  const float* xsrc = a.Xm ? a.Xm : static_cast<const float*>(P.xop[P.x0]);   // FP32 operand: x itself
+  const int q4 = Bp / 4;
+  for (int t = tid; t < R * q4; t += blockDim.x) {
+    const int il = t / q4, r = 4 * (t % q4);
+    const int64_t idx = (int64_t)(r_begin + il) * ld + r;
+    *reinterpret_cast<float4*>(xs + (size_t)il * Bp + r) = __ldcg(reinterpret_cast<const float4*>(xsrc + idx));
+    *reinterpret_cast<float4*>(ys + (size_t)il * Bp + r) = __ldcg(reinterpret_cast<const float4*>(a.Y + idx));
+  }
+  if (tid == 0) s_stop = 0;
+  __syncthreads();
+
+  const int chunks = (B + 127) / 128;
+  const int items = R * chunks;
+  for (int it = 0; it < P.iters; ++it) {
+    const int w = (P.x0 + it) & 1;
+    const void* xin = P.xop[w];
+    void* xout = P.xop[w ^ 1];
+    uint8_t* bits = it + 1 == P.iters ? static_cast<uint8_t*>(P.bits_last) : nullptr;
+    if (it > 0) {
+      // x^{it} is complete once every CTA has arrived after iteration it - 1
+      if (tid == 0) {
+        const bool ok = grid_wait(P.gbar, (unsigned int)it * (unsigned int)G, globaltimer_ns() + P.timeout_ns);
+        if (!ok) {
+          atomicOr(a.err, ERR_TIMEOUT);
+          atomicExch(P.gbar + 2, 1u);
+        }
+        s_stop = ok ? 0 : 1;
+      }
+      __syncthreads();
+      if (s_stop) break;
+    }
+    for (int item = warp; item < items; item += nw) {
+      const int il = item / chunks;
+      const int r0 = (item % chunks) * 128 + 4 * lane;
+      if (r0 >= B) continue;
+      const int64_t i = r_begin + il;
+      const float cpi = a.cp[i];
+      const int eb = rp[il], ee = rp[il + 1];
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+      for (int e = eb; e < ee; ++e) {
+        const int64_t j = cs[e];
+        const float wgt = wv[e];
+        const float4 xv = ldcg4<OPT>(xin, j * ld + r0);
+        acc.x = fmaf(wgt, xv.x, acc.x);
+        acc.y = fmaf(wgt, xv.y, acc.y);
+        acc.z = fmaf(wgt, xv.z, acc.z);
+        acc.w = fmaf(wgt, xv.w, acc.w);
+      }
+      float* xp = xs + (size_t)il * Bp + r0;
+      float* yp = ys + (size_t)il * Bp + r0;
+      const float4 xo = *reinterpret_cast<const float4*>(xp);
+      const float4 yo = *reinterpret_cast<const float4*>(yp);
+      const int64_t idx = i * ld + r0;
+      float4 xn4, yn4;
+      uint32_t bw = 0u;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float x = comp(xo, k), y = comp(yo, k);
+        const float gx = g_val(x, GK);
+        const float d = comp(acc, k) + cpi + y * g_der(x, GK);
+        float yn;
+        const float xn = pdbo_update(x, y, d, gx, a.alpha, a.beta, a.delta, a.grad_tol, &yn);
+        const bool live = r0 + k < B;   // padding restarts keep their zeros
+        if (a.Gd) a.Gd[idx + k] = live ? d : 0.0f;
+        set_comp(xn4, k, live ? xn : 0.0f);
+        set_comp(yn4, k, live ? yn : 0.0f);
+        bw |= (uint32_t)(live && xn > 0.5f) << (8 * k);
+      }
+      *reinterpret_cast<float4*>(xp) = xn4;
+      *reinterpret_cast<float4*>(yp) = yn4;
+      store4<OPT>(xout, idx, xn4);
+      if (bits) *reinterpret_cast<uint32_t*>(bits + idx) = bw;
+    }
+    if (it + 1 < P.iters) {
+      // publish this CTA's rows of x^{it+1}: the barrier orders every thread's stores before
+      // thread 0's release
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        red_release_gpu_add(P.gbar, 1u);
+      }
+    }
+  }
+  // the state goes back to global memory (x in the FP32 operand buffer already when there is no
+  // master copy)
+  __syncthreads();
+  for (int t = tid; t < R * q4; t += blockDim.x) {
+    const int il = t / q4, r = 4 * (t % q4);
+    const int64_t idx = (int64_t)(r_begin + il) * ld + r;
+    if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = *reinterpret_cast<const float4*>(xs + (size_t)il * Bp + r);
+    *reinterpret_cast<float4*>(a.Y + idx) = *reinterpret_cast<const float4*>(ys + (size_t)il * Bp + r);
+  }
+  if (P.iters > 1 && tid == 0) {
+    // the last CTA out restores the barrier words for the next launch (the abort word stays
+    // raised after a failure; the host clears it when it reads the error)
+    if (atomicAdd(P.gbar + 1, 1u) == gridDim.x - 1) {
+      atomicExch(P.gbar, 0u);
+      atomicExch(P.gbar + 1, 0u);
+    }
+  }
+}
+
+// Whether the resident form serves this problem: the update with one dual per coordinate, and
+// the largest CTA's rows and nonzeros fit in shared memory.  grid: CTAs (one per SM, at most n).
+bool csr_res_shape(int64_t n, int B, int sms, int nnz_max, int* grid, size_t* smem) {
+  if (n < 1 || sms < 1) return false;
+  const int G = (int)std::min<int64_t>(n, sms);
+  const int rows_max = (int)((n + G - 1) / G);
+  const int Bp = (B + 3) / 4 * 4;
+  const size_t bytes = res_smem_bytes(rows_max, nnz_max, Bp);
+  if (bytes > 200 * 1024 + 16) return false;
+  *grid = G;
+  *smem = bytes;
+  return true;
+}
+
+cudaError_t launch_csr_res(const int32_t* rowptr, const int32_t* col, const void* val, int val_type, const EpiArgs& a,
+                           int op_type, int which_x, void* const xop[2], int iters, int nnz_max, int sms,
+                           unsigned int* gbar, uint64_t timeout_ns, cudaStream_t s) {
+  int G = 0;
+  size_t smem = 0;
+  if (a.mu || a.ld % 8 != 0 || iters < 1 || (iters > 1 && !gbar) || which_x < 0 || which_x > 1 ||
+      !csr_res_shape(a.n, a.B, sms, nnz_max, &G, &smem))
+    return cudaErrorInvalidValue;
+  ResParams P;
+  memset(&P, 0, sizeof(P));
+  P.rowptr = rowptr;
+  P.col = col;
+  P.val = val;
+  P.vt = val_type;
+  P.a = a;
+  P.xop[0] = xop[0];
+  P.xop[1] = xop[1];
+  P.bits_last = a.bits_out;
+  P.gbar = gbar;
+  P.x0 = which_x;
+  P.iters = iters;
+  P.rows_max = (int)((a.n + G - 1) / G);
+  P.nnz_max = nnz_max;
+  P.Bp = (a.B + 3) / 4 * 4;
+  P.timeout_ns = timeout_ns;
+  const bool ent = a.gkind == G_ENTROPY;
+  void (*kern)(const ResParams) = op_type == OP_F32 ? (ent ? k_csr_res<OP_F32, G_ENTROPY> : k_csr_res<OP_F32, G_QUAD>)
+                                                    : (ent ? k_csr_res<OP_BF16, G_ENTROPY> : k_csr_res<OP_BF16, G_QUAD>);
+  static PerDevice per_device;   // the shared-memory limit of the four kernels, once per device
+  const cudaError_t e = per_device.once([] {
+    const int lim = 200 * 1024 + 16;
+    cudaError_t r = cudaFuncSetAttribute(k_csr_res<OP_F32, G_QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_csr_res<OP_F32, G_ENTROPY>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_csr_res<OP_BF16, G_QUAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_csr_res<OP_BF16, G_ENTROPY>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    return r;
+  });
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(RES_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  // cooperative: the CTAs wait for one another at the grid barrier, so the launch must be
+  // scheduled whole
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeCooperative;
+  attr.val.cooperative = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = iters > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, P);
+}
+
 }  // namespace sbo

@@ -270,36 +270,6 @@ __device__ __forceinline__ void csk_epilogue(const EpiArgs& a, void* xout, void*
 #undef CSK_COLUMNS
 }
 
-// ---- grid barrier between the iterations of one launch ------------------------------------------
-// Every CTA of the launch is resident at once (the launch is one wave of clusters), so CTAs may
-// wait for one another.  Arrivals only grow within a launch: barrier k (before iteration k) is
-// passed once k * gridDim.x arrivals are counted.  The last CTA to leave the kernel sets the
-// words back to zero for the next launch.  A CTA that gives up waiting raises the abort word,
-// which ends every other CTA's waits too.
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_gpu_add(unsigned int* p, unsigned int v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-// Orders this thread's earlier generic-proxy stores before later async-proxy (TMA) reads of other
-// CTAs, then before the release that publishes them.
-__device__ __forceinline__ void fence_stores_for_tma() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-  __threadfence();
-}
-__device__ __forceinline__ bool grid_wait(const unsigned int* gbar, unsigned int target, uint64_t deadline) {
-  uint32_t spins = 0;
-  while (ld_acquire_gpu(gbar) < target) {
-    if (ld_acquire_gpu(gbar + 2) != 0u) return false;
-    if ((++spins & 15u) == 0u && globaltimer_ns() > deadline) return false;
-    __nanosleep(64);
-  }
-  return true;
-}
-
 template <int BN, int MODE, bool PAIR>
 __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant__ CskParams P) {
   using C = CskCfg<BN, PAIR>;

@@ -95,11 +95,22 @@ cudaError_t launch_tiny(const TinyArgs& a, cudaStream_t s);
 // staged in shared memory; the *_STREAM forms are the first three with L2 eviction priorities on
 // the own state (evict-first x and y, evict-last operand), for state that overflows L2.
 enum CsrForm : int { CSR_FORM_RULE = 0, CSR_FORM_ROW1 = 1, CSR_FORM_ROW2 = 2, CSR_FORM_PIPE2 = 3, CSR_FORM_STAGED = 4,
-                     CSR_FORM_ROW1_STREAM = 5, CSR_FORM_ROW2_STREAM = 6, CSR_FORM_PIPE2_STREAM = 7 };
+                     CSR_FORM_ROW1_STREAM = 5, CSR_FORM_ROW2_STREAM = 6, CSR_FORM_PIPE2_STREAM = 7,
+                     CSR_FORM_RESIDENT = 8 };
 inline bool csr_form_streams(int form) { return form >= CSR_FORM_ROW1_STREAM && form <= CSR_FORM_PIPE2_STREAM; }
 inline int csr_form_base(int form) { return csr_form_streams(form) ? form - 4 : form; }
 cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* val, int val_type,
                        const EpiArgs& a, int op_type, int mode, bool pdl, cudaStream_t s, int form = CSR_FORM_RULE);
+// Resident form of the sparse update (k_csr.cu): the state of each CTA's rows stays in shared
+// memory for `iters` iterations (one cooperative CTA per SM, grid barrier between iterations;
+// operand buffers xop alternate from which_x, candidate bytes written by the last iteration when
+// a.bits_out is set).  csr_res_shape: whether a graph with n rows, B restarts and at most nnz_max
+// nonzeros in any CTA's rows (rows split evenly over min(n, sms) CTAs) fits, with its grid and
+// shared memory.
+bool csr_res_shape(int64_t n, int B, int sms, int nnz_max, int* grid, size_t* smem);
+cudaError_t launch_csr_res(const int32_t* rowptr, const int32_t* col, const void* val, int val_type, const EpiArgs& a,
+                           int op_type, int which_x, void* const xop[2], int iters, int nnz_max, int sms,
+                           unsigned int* gbar, uint64_t timeout_ns, cudaStream_t s);
 int csr_partial_rows(int64_t n, int B);
 // k_csr_staged.cu: the update with every row's operands staged in shared memory by bulk copies
 // (CSR_FORM_STAGED); max_deg is the largest row length of A.  csr_staged_shape reports its stage

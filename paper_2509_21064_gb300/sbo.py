@@ -24,7 +24,7 @@ SBO_OPT_KERNEL, SBO_OPT_USE_GRAPH, SBO_OPT_TILE_N, SBO_OPT_TIMEOUT_US, SBO_OPT_S
     SBO_OPT_STEPS_PER_LAUNCH = 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13
 EVAL_MODE_RULE, EVAL_MODE_INLINE, EVAL_MODE_BESIDE = 0, 1, 2
 CSR_FORM_AUTO, CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_STAGED = 0, 1, 2, 3, 4
-CSR_FORM_ROW1_STREAM, CSR_FORM_ROW2_STREAM, CSR_FORM_PIPE2_STREAM = 5, 6, 7
+CSR_FORM_ROW1_STREAM, CSR_FORM_ROW2_STREAM, CSR_FORM_PIPE2_STREAM, CSR_FORM_RESIDENT = 5, 6, 7, 8
 G_QUADRATIC, G_ENTROPY = 0, 1
 DUAL_COORDINATE, DUAL_SINGLE = 0, 1
 KERNEL_AUTO, KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_CSR, KERNEL_MAXK = 0, 1, 2, 3, 4, 5

@@ -1,8 +1,9 @@
 """Every form of the sparse update kernel (SBO_OPT_CSR_FORM: one row per warp with 128 or 256
-restarts, pipelined rows, each of them with or without L2 eviction priorities, rows staged in shared
-memory by bulk copies) computes the same sums in the same order, so all of them give bit-identical
-runs; the staged form is also held to the FP64
-oracle.  The graphs cover ragged restart chunks (B = 200), two chunks of restarts per row (B = 600,
+restarts, pipelined rows, each of them with or without L2 eviction priorities, the state resident in
+shared memory over several iterations per launch, rows staged in shared memory by bulk copies)
+computes the same sums in the same order, so all of them give bit-identical runs; the staged form
+is also held to the FP64 oracle.  The resident form serves the graphs whose state fits in shared
+memory (ER and hubs here; the torus at B = 600 falls back to the rule).  The graphs cover ragged restart chunks (B = 200), two chunks of restarts per row (B = 600,
 the second one short), isolated vertices, and hub vertices whose rows span several stages."""
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ from _helpers import gpu_trajectory, normwise, oracle_trajectory, to_gda_params
 pytestmark = pytest.mark.gpu
 
 FORMS = [S.CSR_FORM_ROW1, S.CSR_FORM_ROW2, S.CSR_FORM_PIPE2, S.CSR_FORM_ROW1_STREAM, S.CSR_FORM_ROW2_STREAM,
-         S.CSR_FORM_PIPE2_STREAM, S.CSR_FORM_STAGED]
+         S.CSR_FORM_PIPE2_STREAM, S.CSR_FORM_RESIDENT, S.CSR_FORM_STAGED]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -97,3 +98,37 @@ def test_autotuned_form_is_reported_and_kept():
         P.run(20)
         X1, Y1 = P.state()
     assert np.array_equal(X, X1) and np.array_equal(Y, Y1)
+
+
+def test_resident_form_is_used_where_it_fits_and_keeps_its_bits_across_launch_sizes():
+    """The resident form on Max-Cut ER n = 2,000, B = 256 (the benchmark's small graph): reported by
+    sbo_info, and the same bits with one launch per iteration, 3 iterations per launch and whole
+    blocks per launch, with and without graphs (T = 37 crosses the evaluations at 10, 20, 30)."""
+    n = 2000
+    i, j, w = W.maxcut_er(n, 6.0, seed=0)
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    prm = to_gda_params(W.graph_params("maxcut", restarts=256, iters=3000, eval_every=10, seed=0))
+    runs = []
+    for per_launch in (1, 3, 0):
+        for graph in (0, 1):
+            with S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32) as P:
+                P.set_option(S.SBO_OPT_CSR_FORM, S.CSR_FORM_RESIDENT)
+                P.set_option(S.SBO_OPT_STEPS_PER_LAUNCH, per_launch)
+                P.set_option(S.SBO_OPT_USE_GRAPH, graph)
+                P.start(prm)
+                assert P.info()["tile_n"] == S.CSR_FORM_RESIDENT
+                P.run(37)
+                X, Y = P.state()
+                Fr, tr = P.restart_best()
+                runs.append((X, Y, Fr, tr, P.trace()))
+    with S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32) as P:
+        P.set_option(S.SBO_OPT_CSR_FORM, S.CSR_FORM_ROW1)
+        P.start(prm)
+        P.run(37)
+        X, Y = P.state()
+        Fr, tr = P.restart_best()
+        runs.append((X, Y, Fr, tr, P.trace()))
+    for r in runs[1:]:
+        for a, b in zip(runs[0], r):
+            assert np.array_equal(a, b)
+

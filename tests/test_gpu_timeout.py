@@ -40,3 +40,35 @@ def test_bounded_waits_report_timeout_and_the_context_survives(n, B, tile):
         P2.run(20)
         X2, Y2 = P2.state()
     assert np.array_equal(X, X2) and np.array_equal(Y, Y2)
+
+
+def test_resident_sparse_form_times_out_and_recovers():
+    """The resident sparse form (grid barrier between the iterations of a launch) with a 1 us
+    budget on its only wait, the grid barrier: the launch either gives up (the host then reads
+    SBO_ETIMEOUT) or every CTA arrived in time; either way it returns, and the handle then runs
+    normally and matches another form bit for bit."""
+    build_lib()
+    n = 2000
+    i, j, w = W.maxcut_er(n, 6.0, seed=1)
+    rowptr, col, val, c = W.maxcut_qubo(n, i, j, w)
+    prm = S.params(**W.graph_params("maxcut", restarts=256, iters=100, eval_every=10, seed=2).asdict())
+    with S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32) as P:
+        P.set_option(S.SBO_OPT_CSR_FORM, S.CSR_FORM_RESIDENT)
+        P.set_option(S.SBO_OPT_TIMEOUT_US, 1)
+        P.start(prm)
+        P.run(10)
+        try:
+            P.sync()
+        except S.SboError as e:
+            assert e.status == S.SBO_ETIMEOUT
+        P.set_option(S.SBO_OPT_TIMEOUT_US, 4_000_000)
+        P.start(prm)
+        P.run(20)
+        X, Y = P.state()
+    with S.Problem.csr(n, rowptr, col, val, c, precision=S.SBO_FP32) as P2:
+        P2.set_option(S.SBO_OPT_CSR_FORM, S.CSR_FORM_ROW1)
+        P2.start(prm)
+        P2.run(20)
+        X2, Y2 = P2.state()
+    assert np.array_equal(X, X2) and np.array_equal(Y, Y2)
+
