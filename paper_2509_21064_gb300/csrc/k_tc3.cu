@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
   uint64_t* drain_bar = tfull_bar + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain_bar + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-  int* stop_vote = abort_flag + 1;             // [2] this CTA's vote to stop, by iteration parity
+  int* stop_vote = abort_flag + 1;             // [2] the cluster's votes to stop, by iteration parity
   int* stop_all = abort_flag + 3;              // the cluster's decision, broadcast in the CTA
 
   const int warp = threadIdx.x >> 5;
@@ -486,7 +486,15 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
                              (int64_t)n_tile * BN, c_begin, c_end, warp, lane);
       if (it + 1 < P.iters) fence_stores_for_tma();
     }
-    if (threadIdx.x == 0) stop_vote[it & 1] = (*vabort != 0 || (multi && ld_acquire_gpu(P.gbar + 2) != 0u)) ? 1 : 0;
+    // Stop together: a CTA that must stop ORs its vote into the vote word of this parity in every
+    // CTA of the cluster before the barrier below, so that after it every CTA reads the same
+    // decision from its own word (rewritten two iterations later, after two more cluster
+    // barriers) and the cluster barriers stay matched.  Nothing is sent when no CTA stops.
+    if (threadIdx.x == 0 && (*vabort != 0 || (multi && ld_acquire_gpu(P.gbar + 2) != 0u))) {
+      for (int r = 0; r < CL; ++r)
+        asm volatile("red.shared::cluster.or.b32 [%0], 1;" ::"r"(csk_mapa(smem_u32(&stop_vote[it & 1]), (uint32_t)r))
+                     : "memory");
+    }
 
     __syncwarp();
     tc_fence_before();
@@ -494,24 +502,14 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
     tc_fence_after();
 
     if (it + 1 == P.iters) break;
-    // Stop together: every CTA of the cluster reads the same votes (a vote of parity it & 1 is
-    // rewritten two iterations later, after two more cluster barriers), so the cluster barriers
-    // above stay matched.
     if (threadIdx.x == 0) {
-      int stop = 0;
-      for (int r = 0; r < CL; ++r) {
-        int v;
-        asm volatile("ld.shared::cluster.u32 %0, [%1];"
-                     : "=r"(v)
-                     : "r"(csk_mapa(smem_u32(&stop_vote[it & 1]), (uint32_t)r))
-                     : "memory");
-        stop |= v;
-      }
+      volatile int* vote = stop_vote + (it & 1);
+      const int stop = *vote;
+      *vote = 0;   // ready for iteration it + 2
       *stop_all = stop;
-      if (!stop) {
-        __threadfence();
-        red_release_gpu_add(P.gbar, 1u);   // this CTA's part of x^{it+1} is written
-      }
+      // this CTA's part of x^{it+1} is written: every thread fenced its stores before the cluster
+      // barrier, which orders them before this release
+      if (!stop) red_release_gpu_add(P.gbar, 1u);
     }
     __syncthreads();
     if (*stop_all) break;
