@@ -152,6 +152,7 @@ struct sbo_problem {
   cudaGraphExec_t gexec_nv[2] = {nullptr, nullptr};   // K steps, no evaluation
   cudaGraphExec_t gexec_ov[2] = {nullptr, nullptr};   // pending evaluation beside K steps
   bool eval_pending = false;
+  bool eval_fused = false;   // the last update launch also added the candidates' objective into F2
   int64_t graph_blocks_seen = 0;   // eligible K-blocks so far: a graph is captured for the second
   // Lagrangian scratch (BF16 operand)
   void* lag_op = nullptr;
@@ -166,6 +167,7 @@ void free_run(sbo_problem* p) {
     for (int k = 0; k < 2; ++k)
       if (set[k]) { cudaGraphExecDestroy(set[k]); set[k] = nullptr; }
   p->eval_pending = false;
+  p->eval_fused = false;
   dfree(p->Xm, p->stream);
   dfree(p->Y, p->stream);
   dfree(p->Gd, p->stream);
@@ -267,7 +269,7 @@ cudaError_t contract(sbo_problem* p, const EpiArgs& a, int mode, int which_x, cu
     case KER_TC: return launch_tc(p->plan, which_x, nullptr, a, mode, timeout_ns(p), s);
     case KER_CSR:
       if (mode == EPI_UPDATE && p->csr_form == CSR_FORM_RESIDENT && !a.mu)
-        return launch_csr_res(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, which_x, p->Xop, 1,
+        return launch_csr_res(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, which_x, p->Xop, 1, false,
                               p->res_nnz_max, p->sms, p->tc_gbar, timeout_ns(p), s);
       if (mode == EPI_UPDATE && p->csr_form == CSR_FORM_STAGED && !a.mu)
         return launch_csr_staged(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, p->max_deg, p->sms,
@@ -326,12 +328,16 @@ cudaError_t enqueue_steps(sbo_problem* p, int64_t steps, bool write_bits, cudaSt
     a.Xin = p->Xop[p->cur];
     a.Xout = p->Xop[p->cur ^ 1];
     a.bits_out = write_bits && done == steps ? p->bits : nullptr;
+    // the resident sparse form evaluates the candidates it writes inside the same launch; the
+    // evaluation that follows then only commits them
+    const bool fuse = p->kernel == KER_CSR && a.bits_out != nullptr;
     ++p->launches;
     cudaError_t e = p->kernel == KER_CSR
                         ? launch_csr_res(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, p->cur, p->Xop,
-                                         (int)chunk, p->res_nnz_max, p->sms, p->tc_gbar, timeout_ns(p), s)
+                                         (int)chunk, fuse, p->res_nnz_max, p->sms, p->tc_gbar, timeout_ns(p), s)
                         : launch_tc_csk(p->plan, p->cur, a, EPI_UPDATE, (int)chunk, timeout_ns(p), s);
     if (e != cudaSuccess) return e;
+    if (fuse) p->eval_fused = true;
     if (chunk & 1) p->cur ^= 1;
   }
   return cudaSuccess;
@@ -361,10 +367,15 @@ CommitArgs commit_args(const sbo_problem* p) {
 
 // Exact objective of the bits written by the last step, then best bookkeeping.
 cudaError_t enqueue_eval(sbo_problem* p, int64_t add, cudaStream_t s, bool pdl = true) {
-  EpiArgs a = base_args(p);
-  a.Xin = p->bits;
-  cudaError_t e = contract(p, a, EPI_EVAL, 2, s, pdl);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (p->eval_fused) {
+    p->eval_fused = false;   // the objective was computed by the launch that wrote the candidates
+  } else {
+    EpiArgs a = base_args(p);
+    a.Xin = p->bits;
+    e = contract(p, a, EPI_EVAL, 2, s, pdl);
+    if (e != cudaSuccess) return e;
+  }
   e = launch_eval_commit(commit_args(p), add, s);
   ++p->launches;
   return e;
@@ -741,8 +752,9 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
   // during one form's timing does not decide.
   // The resident form (CSR_FORM_RESIDENT) is not a candidate: its updates are faster (Max-Cut ER
   // n = 2,000, B = 256: 3.8 us per iteration against about 5), but its evaluations cannot run beside
-  // the next block (its cooperative launch holds every SM), which costs more than that in a run
-  // with an evaluation every 10 iterations (5.7 against 5.5 us per iteration, FP32).
+  // the next block (its cooperative launch holds every SM); even with the objective computed in
+  // the launch, a run with an evaluation every 10 iterations measured 5.6 against 5.5 us per
+  // iteration (FP32).
   const int forms[] = {CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_ROW1_STREAM, CSR_FORM_ROW2_STREAM,
                        CSR_FORM_PIPE2_STREAM};
   float form_ms[8];
@@ -1463,7 +1475,8 @@ sbo_status sbo_gda_run(sbo_problem* p, int64_t iters) {
       }
       cudaError_t e = cudaGraphLaunch(slot[par], p->stream);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-      p->launches += step_launches(p, K) + (kind == BLOCK_DEFER ? 0 : 2);
+      const bool fused = p->kernel == KER_CSR && p->csr_form == CSR_FORM_RESIDENT && !p->single;
+      p->launches += step_launches(p, K) + (kind == BLOCK_DEFER ? 0 : fused ? 1 : 2);
       if (K & 1) p->cur ^= 1;
       if (kind == BLOCK_BESIDE) {   // the pending candidates of the block's first iteration
         p->t_last_eval = p->t;

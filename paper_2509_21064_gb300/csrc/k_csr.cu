@@ -550,6 +550,7 @@ struct ResParams {
   unsigned int* gbar;      // grid barrier [arrivals, exits, abort] (iters > 1)
   int x0, iters;
   int rows_max, nnz_max, Bp;   // shared-memory extents: rows, nonzeros per CTA, restarts per row
+  int eval_last;           // after the last iteration: the exact objective of its candidates into a.F2
   uint64_t timeout_ns;     // per iteration
 };
 
@@ -563,7 +564,9 @@ __device__ __forceinline__ float4 ldcg4(const void* p, int64_t idx) {
 }
 
 size_t res_smem_bytes(int rows_max, int nnz_max, int Bp) {
-  return (size_t)rows_max * Bp * 8 + (size_t)(rows_max + 1) * 4 + (size_t)nnz_max * 8 + 16;
+  // x, y [rows][Bp] FP32; 2F per restart (int64) for the fused evaluation; row offsets, columns,
+  // weights
+  return (size_t)rows_max * Bp * 8 + (size_t)Bp * 8 + (size_t)(rows_max + 1) * 4 + (size_t)nnz_max * 8 + 16;
 }
 
 template <int OPT, int GK>
@@ -579,7 +582,8 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_csr_res(const __grid_constan
   const int R = r_end - r_begin;
   float* xs = reinterpret_cast<float*>(res_smem);                 // [rows_max][Bp]
   float* ys = xs + (size_t)P.rows_max * Bp;                       // [rows_max][Bp]
-  int* rp = reinterpret_cast<int*>(ys + (size_t)P.rows_max * Bp);   // [rows_max + 1]
+  long long* f2s = reinterpret_cast<long long*>(ys + (size_t)P.rows_max * Bp);   // [Bp]
+  int* rp = reinterpret_cast<int*>(f2s + Bp);                     // [rows_max + 1]
   int* cs = rp + P.rows_max + 1;                                  // [nnz_max]
   float* wv = reinterpret_cast<float*>(cs + P.nnz_max);           // [nnz_max]
 
@@ -675,6 +679,56 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_csr_res(const __grid_constan
       }
     }
   }
+  if (P.eval_last) {
+    // The exact objective of the last iteration's candidates, as the evaluation kernel computes it
+    // (integer weights times candidate bytes, 2F = sum_i b_i (sum_j A_ij b_j + 2 c'_i)), once every
+    // CTA's candidates are written: one more arrival at the grid barrier.
+    __syncthreads();
+    if (tid == 0) {
+      bool ok = s_stop == 0;
+      if (ok) {
+        __threadfence();
+        red_release_gpu_add(P.gbar, 1u);
+        ok = grid_wait(P.gbar, (unsigned int)P.iters * (unsigned int)G, globaltimer_ns() + P.timeout_ns);
+        if (!ok) {
+          atomicOr(a.err, ERR_TIMEOUT);
+          atomicExch(P.gbar + 2, 1u);
+        }
+      }
+      s_stop = ok ? 0 : 1;
+    }
+    for (int t = tid; t < Bp; t += blockDim.x) f2s[t] = 0;
+    __syncthreads();
+    if (!s_stop) {
+      const uint8_t* cand = static_cast<const uint8_t*>(P.bits_last);
+      for (int item = warp; item < items; item += nw) {
+        const int il = item / chunks;
+        const int r0 = (item % chunks) * 128 + 4 * lane;
+        if (r0 >= B) continue;
+        const int64_t i = r_begin + il;
+        const long long cp2 = 2 * (long long)a.cp64[i];
+        int ai[4] = {0, 0, 0, 0};
+        for (int e = rp[il]; e < rp[il + 1]; ++e) {
+          const int64_t j = cs[e];
+          const int wint = __float2int_rn(wv[e]);
+          const uint32_t word = __ldcg(reinterpret_cast<const unsigned int*>(cand + j * ld + r0));
+#pragma unroll
+          for (int k = 0; k < 4; ++k) ai[k] += wint * (int)((word >> (8 * k)) & 1u);
+        }
+        const float* xp = xs + (size_t)il * Bp + r0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (r0 + k < B && xp[k] > 0.5f) {   // the row's own candidate, as the update wrote it
+            const long long v = (long long)ai[k] + cp2;
+            if (v != 0) atomicAdd(reinterpret_cast<unsigned long long*>(&f2s[r0 + k]), (unsigned long long)v);
+          }
+        }
+      }
+      __syncthreads();
+      for (int t = tid; t < B; t += blockDim.x)
+        if (f2s[t] != 0) atomicAdd(&a.F2[t], (unsigned long long)f2s[t]);
+    }
+  }
   // the state goes back to global memory (x in the FP32 operand buffer already when there is no
   // master copy)
   __syncthreads();
@@ -684,7 +738,7 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_csr_res(const __grid_constan
     if (a.Xm) *reinterpret_cast<float4*>(a.Xm + idx) = *reinterpret_cast<const float4*>(xs + (size_t)il * Bp + r);
     *reinterpret_cast<float4*>(a.Y + idx) = *reinterpret_cast<const float4*>(ys + (size_t)il * Bp + r);
   }
-  if (P.iters > 1 && tid == 0) {
+  if ((P.iters > 1 || P.eval_last) && tid == 0) {
     // the last CTA out restores the barrier words for the next launch (the abort word stays
     // raised after a failure; the host clears it when it reads the error)
     if (atomicAdd(P.gbar + 1, 1u) == gridDim.x - 1) {
@@ -709,12 +763,12 @@ bool csr_res_shape(int64_t n, int B, int sms, int nnz_max, int* grid, size_t* sm
 }
 
 cudaError_t launch_csr_res(const int32_t* rowptr, const int32_t* col, const void* val, int val_type, const EpiArgs& a,
-                           int op_type, int which_x, void* const xop[2], int iters, int nnz_max, int sms,
-                           unsigned int* gbar, uint64_t timeout_ns, cudaStream_t s) {
+                           int op_type, int which_x, void* const xop[2], int iters, bool eval_last, int nnz_max,
+                           int sms, unsigned int* gbar, uint64_t timeout_ns, cudaStream_t s) {
   int G = 0;
   size_t smem = 0;
-  if (a.mu || a.ld % 8 != 0 || iters < 1 || (iters > 1 && !gbar) || which_x < 0 || which_x > 1 ||
-      !csr_res_shape(a.n, a.B, sms, nnz_max, &G, &smem))
+  if (a.mu || a.ld % 8 != 0 || iters < 1 || ((iters > 1 || eval_last) && !gbar) || which_x < 0 || which_x > 1 ||
+      (eval_last && (!a.bits_out || !a.F2 || !a.cp64)) || !csr_res_shape(a.n, a.B, sms, nnz_max, &G, &smem))
     return cudaErrorInvalidValue;
   ResParams P;
   memset(&P, 0, sizeof(P));
@@ -732,6 +786,7 @@ cudaError_t launch_csr_res(const int32_t* rowptr, const int32_t* col, const void
   P.rows_max = (int)((a.n + G - 1) / G);
   P.nnz_max = nnz_max;
   P.Bp = (a.B + 3) / 4 * 4;
+  P.eval_last = eval_last ? 1 : 0;
   P.timeout_ns = timeout_ns;
   const bool ent = a.gkind == G_ENTROPY;
   void (*kern)(const ResParams) = op_type == OP_F32 ? (ent ? k_csr_res<OP_F32, G_ENTROPY> : k_csr_res<OP_F32, G_QUAD>)
@@ -760,7 +815,7 @@ cudaError_t launch_csr_res(const int32_t* rowptr, const int32_t* col, const void
   attr.id = cudaLaunchAttributeCooperative;
   attr.val.cooperative = 1;
   cfg.attrs = &attr;
-  cfg.numAttrs = iters > 1 ? 1 : 0;
+  cfg.numAttrs = (iters > 1 || eval_last) ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, P);
 }
 

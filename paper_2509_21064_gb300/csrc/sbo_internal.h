@@ -108,9 +108,11 @@ cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* va
 // nonzeros in any CTA's rows (rows split evenly over min(n, sms) CTAs) fits, with its grid and
 // shared memory.
 bool csr_res_shape(int64_t n, int B, int sms, int nnz_max, int* grid, size_t* smem);
+// eval_last: after the last iteration, the exact objective of its candidates (a.bits_out) is added
+// into a.F2 as the evaluation kernel would add it (the commit kernel then reads and clears F2).
 cudaError_t launch_csr_res(const int32_t* rowptr, const int32_t* col, const void* val, int val_type, const EpiArgs& a,
-                           int op_type, int which_x, void* const xop[2], int iters, int nnz_max, int sms,
-                           unsigned int* gbar, uint64_t timeout_ns, cudaStream_t s);
+                           int op_type, int which_x, void* const xop[2], int iters, bool eval_last, int nnz_max,
+                           int sms, unsigned int* gbar, uint64_t timeout_ns, cudaStream_t s);
 int csr_partial_rows(int64_t n, int B);
 // k_csr_staged.cu: the update with every row's operands staged in shared memory by bulk copies
 // (CSR_FORM_STAGED); max_deg is the largest row length of A.  csr_staged_shape reports its stage
