@@ -105,17 +105,18 @@ __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w 
 constexpr int CSK_WARPS = CSK_THREADS / 32;
 constexpr int CSK_CB = 4;   // restart columns per warp whose loads are in flight together
 
-// Reduction and epilogue of tile columns [c_begin, c_end) (restarts r0 + c).  Warp w takes the
-// columns c_begin + w + CSK_WARPS t; lane l holds tile rows 4l .. 4l+3 (variables i0 .. i0+3).
+// Reduction and epilogue of tile columns [c_begin, c_end) (restarts r0 + c) of the 128 rows of
+// block row_block (variables 128 row_block ..).  Warp w takes the columns c_begin + w + CSK_WARPS t;
+// lane l holds rows 4l .. 4l+3 of the block (variables i0 .. i0+3).
 // The S partials of a column are summed in split order.  The state rows are padded to a multiple
 // of 8 elements, so the 16-byte loads at i0 < n stay inside the row; stores of the last, partial
 // group of four rows go element by element.
 template <int BN, int MODE, int GK, bool SINGLE>
 __device__ __forceinline__ void csk_columns(const EpiArgs& a, void* xout, void* bits, const float* part,
-                                            const float* ws_tile, int64_t split_stride, int s, int S, int m_tile,
+                                            const float* ws_tile, int64_t split_stride, int s, int S, int row_block,
                                             int64_t r0, int c_begin, int c_end, int warp, int lane) {
   const int row0 = 4 * lane;
-  const int64_t i0 = (int64_t)m_tile * TC_BM + row0;
+  const int64_t i0 = (int64_t)row_block * TC_BM + row0;
   const int64_t left = (int64_t)a.n - i0;
   const int nv = left <= 0 ? 0 : left >= 4 ? 4 : (int)left;   // valid rows of this lane
   float cpv[4];
@@ -244,7 +245,7 @@ __device__ __forceinline__ void csk_columns(const EpiArgs& a, void* xout, void* 
           // partial sums of g(x^t) over 32 rows (eight lanes), one row of partials per 32 rows
 #pragma unroll
           for (int o = 1; o < 8; o <<= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o);
-          if ((lane & 7) == 0) a.gpart[(int64_t)(m_tile * 4 + (lane >> 3)) * a.gpart_ld + r] = gsum;
+          if ((lane & 7) == 0) a.gpart[(int64_t)(row_block * 4 + (lane >> 3)) * a.gpart_ld + r] = gsum;
         }
       }
     }
@@ -253,10 +254,10 @@ __device__ __forceinline__ void csk_columns(const EpiArgs& a, void* xout, void* 
 
 template <int BN, int MODE>
 __device__ __forceinline__ void csk_epilogue(const EpiArgs& a, void* xout, void* bits, const float* part,
-                                             const float* ws_tile, int64_t split_stride, int s, int S, int m_tile,
+                                             const float* ws_tile, int64_t split_stride, int s, int S, int row_block,
                                              int64_t r0, int c_begin, int c_end, int warp, int lane) {
 #define CSK_COLUMNS(M, G, SG)                                                                                    \
-  csk_columns<BN, M, G, SG>(a, xout, bits, part, ws_tile, split_stride, s, S, m_tile, r0, c_begin, c_end, warp, \
+  csk_columns<BN, M, G, SG>(a, xout, bits, part, ws_tile, split_stride, s, S, row_block, r0, c_begin, c_end, warp, \
                             lane)
   if (MODE == EPI_EVAL) {
     CSK_COLUMNS(EPI_EVAL, G_QUAD, false);
@@ -441,9 +442,10 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
         }
       }
     } else if (warp >= 4) {
-      // ---------------------------------------------------------------- partial tile -> smem
+      // ---------------------------------------------------------------- partial tile out
       // Every MMA of this CTA's iteration has completed when tfull fires, so the stage buffers are
-      // idle: the accumulator (lane = row) goes to part[column][row].
+      // idle: the accumulator (lane = row) goes out column-major, [column][row], to the stage
+      // buffers for the columns this CTA owns and to its workspace slice in L2 for the others.
       const int wg = (warp - 4) >> 2;
       const int wq = warp & 3;
       const int row = wq * 32 + lane;
