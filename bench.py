@@ -426,7 +426,7 @@ def run_ours(args):
     # the next step's upload and canonicalisation (the create call returns once they are done)
     # overlap this step's iterations; every step still copies its own Q and reads back its own
     # result inside the timed region.
-    e2e_steps = max(2, min(args.steps, 8))
+    e2e_steps = max(2, min(args.steps, 4))
     prm_e2e = S.params(**{**p.asdict(), "iters": K_EVAL})
     streams = [stream, torch.cuda.Stream(device=dev)]
     torch.cuda.synchronize(dev)
