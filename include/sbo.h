@@ -269,11 +269,12 @@ sbo_status sbo_lagrangian_noalloc(sbo_problem* p, int32_t B, const float* X_dev,
  *                       producer warp and four consumer warps per CTA), 5, 6, 7 the forms 1, 2, 3
  *                       with L2 eviction priorities for state that overflows L2 (each row's own x
  *                       and y evict-first, the operand written for the next iteration evict-last),
- *                       8 resident: one cooperative CTA per SM keeps its rows' x, y and structure in
- *                       shared memory for all the iterations of a launch (grid barrier between
- *                       them; graphs whose state fits, about n B <= 3.6e6 on 152 SMs; evaluations
- *                       then run after each block, not beside the next; explicit only, not an
- *                       autotuner candidate).  Results are identical in
+ *                       8 resident: one cooperative CTA per SM (seven SMs in eight) keeps its rows'
+ *                       x, y and structure in shared memory for all the iterations of a launch
+ *                       (grid barrier between them; graphs whose state fits, about n B <= 3e6 on
+ *                       152 SMs; the evaluations beside the next block keep to the SMs left free;
+ *                       explicit only, not an autotuner candidate).
+ *                       Results are identical in
  *                       every form; the single-constraint form (SBO_OPT_DUAL = 1) keeps the rule
  *   SBO_OPT_EVAL_MODE:  scheduling of the evaluations of sparse and Max-k-Cut runs replayed from
  *                       graphs with K >= 2: 0 (default) and 2 on a graph branch beside the next

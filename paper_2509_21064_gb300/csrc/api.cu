@@ -151,6 +151,7 @@ struct sbo_problem {
   // evaluates what is pending (flush_pending).
   cudaGraphExec_t gexec_nv[2] = {nullptr, nullptr};   // K steps, no evaluation
   cudaGraphExec_t gexec_ov[2] = {nullptr, nullptr};   // pending evaluation beside K steps
+  int64_t graph_launches[3][2] = {{0, 0}, {0, 0}, {0, 0}};   // kernel launches of each captured block
   bool eval_pending = false;
   bool eval_fused = false;   // the last update launch also added the candidates' objective into F2
   int64_t graph_blocks_seen = 0;   // eligible K-blocks so far: a graph is captured for the second
@@ -305,14 +306,9 @@ int64_t steps_per_launch(const sbo_problem* p) {
   return p->opt_steps_per_launch == 0 ? 4096 : p->opt_steps_per_launch;
 }
 
-// Update launches that `steps` iterations take.
-int64_t step_launches(const sbo_problem* p, int64_t steps) {
-  const int64_t per = steps_per_launch(p);
-  return per > 1 ? (steps + per - 1) / per : steps * (p->single ? 2 : 1);
-}
-
-// `steps` iterations; the last one writes the candidate bits when write_bits.
-cudaError_t enqueue_steps(sbo_problem* p, int64_t steps, bool write_bits, cudaStream_t s) {
+// `steps` iterations; the last one writes the candidate bits when write_bits.  fuse_eval: the
+// evaluation follows on this stream, so the resident sparse form may compute it in its launch.
+cudaError_t enqueue_steps(sbo_problem* p, int64_t steps, bool write_bits, cudaStream_t s, bool fuse_eval = false) {
   const int64_t per = steps_per_launch(p);
   if (per <= 1) {
     for (int64_t k = 0; k < steps; ++k) {
@@ -330,7 +326,7 @@ cudaError_t enqueue_steps(sbo_problem* p, int64_t steps, bool write_bits, cudaSt
     a.bits_out = write_bits && done == steps ? p->bits : nullptr;
     // the resident sparse form evaluates the candidates it writes inside the same launch; the
     // evaluation that follows then only commits them
-    const bool fuse = p->kernel == KER_CSR && a.bits_out != nullptr;
+    const bool fuse = fuse_eval && p->kernel == KER_CSR && a.bits_out != nullptr;
     ++p->launches;
     cudaError_t e = p->kernel == KER_CSR
                         ? launch_csr_res(p->rowptr, p->col, p->val, p->val_type, a, p->op_type, p->cur, p->Xop,
@@ -399,9 +395,9 @@ int64_t next_eval_after(const sbo_problem* p, int64_t t) {
 // torus 17.5 us): the fused kernel's registers cost it occupancy.  SBO_OPT_EVAL_MODE 1 forces the
 // evaluation in line.
 bool defer_evals(const sbo_problem* p) {
-  // (not beside the resident form: its cooperative launch holds every SM)
+  // (the resident sparse form's cooperative launch leaves an eighth of the SMs to the evaluation)
   return (p->kernel == KER_CSR || p->kernel == KER_MAXK) && p->prm.eval_every >= 2 && p->opt_graph &&
-         p->opt_eval_mode != 1 && !(p->kernel == KER_CSR && p->csr_form == CSR_FORM_RESIDENT);
+         p->opt_eval_mode != 1;
 }
 
 // Evaluate the deferred candidates (those of iteration t) on the problem's stream.
@@ -418,7 +414,7 @@ sbo_status flush_pending(sbo_problem* p) {
 sbo_status run_direct(sbo_problem* p, int64_t steps, bool eval_at_end) {
   sbo_status st = flush_pending(p);
   if (st != SBO_OK) return st;
-  cudaError_t e0 = enqueue_steps(p, steps, eval_at_end, p->stream);
+  cudaError_t e0 = enqueue_steps(p, steps, eval_at_end, p->stream, eval_at_end);
   if (e0 != cudaSuccess) return cuda_fail(e0, "GDA step launch");
   p->t += steps;
   if (eval_at_end) {
@@ -452,16 +448,17 @@ sbo_status capture_block(sbo_problem* p, int parity, int kind) {
     if (err == cudaSuccess) err = cudaEventRecord(p->ev_join, p->cap_side);
   }
   if (kind == BLOCK_BESIDE) {
-    for (int64_t s = 0; s < K && err == cudaSuccess; ++s) {
-      if (s + 1 == K) err = cudaStreamWaitEvent(p->cap_stream, p->ev_join, 0);
-      if (err == cudaSuccess) err = enqueue_step(p, s + 1 == K, p->cap_stream);
-    }
+    // the first K - 1 steps beside the evaluation, the last one (which writes new candidates) after it
+    if (err == cudaSuccess) err = enqueue_steps(p, K - 1, false, p->cap_stream);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(p->cap_stream, p->ev_join, 0);
+    if (err == cudaSuccess) err = enqueue_steps(p, 1, true, p->cap_stream);
   } else if (err == cudaSuccess) {
-    err = enqueue_steps(p, K, true, p->cap_stream);
+    err = enqueue_steps(p, K, true, p->cap_stream, kind == BLOCK_EVAL);
   }
   if (err == cudaSuccess && kind == BLOCK_EVAL) err = enqueue_eval(p, K, p->cap_stream);
   cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
   p->cur = saved_cur;
+  p->graph_launches[kind][parity] = p->launches - saved_launches;   // counted again at every replay
   p->launches = saved_launches;
   if (err != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -716,7 +713,7 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
     for (auto& ch : name)
       if (ch == ' ') ch = '_';
     std::ostringstream k;
-    k << "csr4:" << name << ":sms" << p->sms << ":n" << p->n << ":nnz" << p->nnz << ":deg" << p->max_deg << ":B"
+    k << "csr5:" << name << ":sms" << p->sms << ":n" << p->n << ":nnz" << p->nnz << ":deg" << p->max_deg << ":B"
       << p->B << ":op" << p->op_type << ":g" << p->opt_g;
     key = k.str();
   }
@@ -750,11 +747,10 @@ sbo_status tune_csr_form(sbo_problem* p, int* out) {
   const bool streams = p->n * (int64_t)p->B * 16 * 4 > p->l2_bytes * 3;
   // Two rounds over the forms, each form's best round counting, so that a clock or cache transient
   // during one form's timing does not decide.
-  // The resident form (CSR_FORM_RESIDENT) is not a candidate: its updates are faster (Max-Cut ER
-  // n = 2,000, B = 256: 3.8 us per iteration against about 5), but its evaluations cannot run beside
-  // the next block (its cooperative launch holds every SM); even with the objective computed in
-  // the launch, a run with an evaluation every 10 iterations measured 5.6 against 5.5 us per
-  // iteration (FP32).
+  // The resident form (CSR_FORM_RESIDENT) is not a candidate: its updates alone are faster (Max-Cut
+  // ER n = 2,000, B = 256: 3.8 against about 4.8 us per iteration), which is what these trials time,
+  // but over a run with an evaluation every 10 iterations it measured slower in FP32 (5.8 against
+  // 5.45 us per iteration with form 1) and faster in BF16 (5.0-5.2 against about 5.4).
   const int forms[] = {CSR_FORM_ROW1, CSR_FORM_ROW2, CSR_FORM_PIPE2, CSR_FORM_ROW1_STREAM, CSR_FORM_ROW2_STREAM,
                        CSR_FORM_PIPE2_STREAM};
   float form_ms[8];
@@ -1039,7 +1035,7 @@ sbo_status sbo_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const i
   p->nnz = (int64_t)cc.size();
   for (int64_t i = 0; i < n; ++i) p->max_deg = std::max<int>(p->max_deg, rp[i + 1] - rp[i]);
   {
-    const int64_t G = std::min<int64_t>(n, std::max(1, p->sms));   // rows split as k_csr_res splits them
+    const int64_t G = csr_res_grid(n, p->sms);   // rows split as k_csr_res splits them
     for (int64_t b = 0; b < G; ++b)
       p->res_nnz_max = std::max<int>(p->res_nnz_max, rp[(b + 1) * n / G] - rp[b * n / G]);
   }
@@ -1475,8 +1471,7 @@ sbo_status sbo_gda_run(sbo_problem* p, int64_t iters) {
       }
       cudaError_t e = cudaGraphLaunch(slot[par], p->stream);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-      const bool fused = p->kernel == KER_CSR && p->csr_form == CSR_FORM_RESIDENT && !p->single;
-      p->launches += step_launches(p, K) + (kind == BLOCK_DEFER ? 0 : fused ? 1 : 2);
+      p->launches += p->graph_launches[kind][par];
       if (K & 1) p->cur ^= 1;
       if (kind == BLOCK_BESIDE) {   // the pending candidates of the block's first iteration
         p->t_last_eval = p->t;

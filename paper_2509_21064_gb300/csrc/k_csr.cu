@@ -492,6 +492,9 @@ static cudaError_t launch_csr_v(const int32_t* rowptr, const int32_t* col, const
     // flight
     const int64_t wave = std::max<int64_t>(1, CSR_WAVES * csr_resident_blocks(kern) / chunks);
     if (want > wave) want = wave;
+    // beside the resident form's cooperative launch, the evaluation keeps to about the eighth of
+    // the SMs that launch leaves free
+    if (MODE == EPI_EVAL && form == CSR_FORM_RESIDENT) want = std::min<int64_t>(want, std::max<int64_t>(1, wave / 8));
   }
   if (MODE != EPI_UPDATE || a.mu) {
     // bounds the closing atomics (evaluation) or the rows of partial sums (single-constraint form)
@@ -519,7 +522,7 @@ cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* va
                              : launch_csr_v<EPI_UPDATE, OP_BF16>(rowptr, col, val, val_type, a, form, pdl, s);
   }
   if (mode == EPI_EVAL) {
-    return launch_csr_v<EPI_EVAL, OP_U8>(rowptr, col, val, val_type, a, 0, pdl, s);   // candidate bytes
+    return launch_csr_v<EPI_EVAL, OP_U8>(rowptr, col, val, val_type, a, form, pdl, s);   // candidate bytes
   }
   if (mode == EPI_LAGR) {
     return op_type == OP_F32 ? launch_csr_v<EPI_LAGR, OP_F32>(rowptr, col, val, val_type, a, 0, pdl, s)
@@ -529,9 +532,11 @@ cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* va
 }
 
 // ---- resident form (CSR_FORM_RESIDENT) -----------------------------------------------------------
-// Small graphs whose state fits in the SMs' shared memory: one cooperative CTA per SM owns the
-// contiguous rows [b n / G, (b+1) n / G) and keeps their x, y and structure (local row offsets,
-// columns, weights) in shared memory for all the iterations of a launch.  An iteration gathers the
+// Small graphs whose state fits in the SMs' shared memory: G = csr_res_grid(n, SMs) cooperative
+// CTAs, one per SM (an eighth of the SMs stays free, for the previous block's evaluation on a graph
+// branch beside the launch); CTA b owns the contiguous rows [b n / G, (b+1) n / G) and keeps their
+// x, y and structure (local row offsets, columns, weights) in shared memory for all the iterations
+// of a launch.  An iteration gathers the
 // neighbours' operand x^t from L2 (bypassing L1: the two operand buffers alternate within the
 // launch), applies the same fused update as k_csr in the same order of operations (bit-identical),
 // writes the rows' x^{t+1} operand to global memory and meets the other CTAs at the grid barrier.
@@ -750,9 +755,14 @@ __global__ void __launch_bounds__(RES_THREADS, 1) k_csr_res(const __grid_constan
 
 // Whether the resident form serves this problem: the update with one dual per coordinate, and
 // the largest CTA's rows and nonzeros fit in shared memory.  grid: CTAs (one per SM, at most n).
+int csr_res_grid(int64_t n, int sms) {
+  const int64_t g = std::max(1, sms - sms / 8);   // an eighth of the SMs stays free for the evaluation beside it
+  return (int)std::max<int64_t>(1, std::min<int64_t>(n, g));
+}
+
 bool csr_res_shape(int64_t n, int B, int sms, int nnz_max, int* grid, size_t* smem) {
   if (n < 1 || sms < 1) return false;
-  const int G = (int)std::min<int64_t>(n, sms);
+  const int G = csr_res_grid(n, sms);
   const int rows_max = (int)((n + G - 1) / G);
   const int Bp = (B + 3) / 4 * 4;
   const size_t bytes = res_smem_bytes(rows_max, nnz_max, Bp);

@@ -108,6 +108,8 @@ cudaError_t launch_csr(const int32_t* rowptr, const int32_t* col, const void* va
 // nonzeros in any CTA's rows (rows split evenly over min(n, sms) CTAs) fits, with its grid and
 // shared memory.
 bool csr_res_shape(int64_t n, int B, int sms, int nnz_max, int* grid, size_t* smem);
+// CTAs of the resident form: min(n, sms - sms / 8), so that an evaluation can run beside it.
+int csr_res_grid(int64_t n, int sms);
 // eval_last: after the last iteration, the exact objective of its candidates (a.bits_out) is added
 // into a.F2 as the evaluation kernel would add it (the commit kernel then reads and clears F2).
 cudaError_t launch_csr_res(const int32_t* rowptr, const int32_t* col, const void* val, int val_type, const EpiArgs& a,
