@@ -15,8 +15,8 @@
 //     (so the sum does not depend on timing) and applies the PDBO update / exact objective to
 //     them.  Each warp takes whole restart columns (all 128 rows, four consecutive rows per
 //     lane): every partial read, state load and state store of a warp is one contiguous 512-byte
-//     run of 16-byte accesses, and a batch of columns issues all its loads before any is used;
-//   * a second cluster barrier keeps every CTA's shared memory alive until all reads are done.
+//     run of 16-byte accesses, and a batch of columns issues all its loads before any is used.
+//     No CTA reads another's shared memory, so one cluster barrier per iteration suffices.
 // Pulling the partials from the peers' shared memory (ld.shared::cluster.v4, the same pipelined
 // rounds) measured slower than the L2 path: 6.5 against 5.2 us of epilogue per iteration at
 // n = 5,000, B = 256, and 5.0 against 3.0 us at n = 2,000.
@@ -29,9 +29,9 @@
 //
 // Every wait is bounded (globaltimer budget per iteration).  A CTA that gives up sets
 // ERR_TIMEOUT, raises the launch's abort word, drains its own copies and MMAs and skips the
-// reduction; the CTAs of a cluster decide together, from votes exchanged in shared memory,
-// whether to stop after an iteration, so the cluster barriers stay matched and every CTA
-// returns in bounded time.
+// reduction; the CTAs of a cluster decide together at each iteration's cluster barrier, from
+// votes pushed into every CTA's shared memory before it, whether to stop, so the cluster barriers
+// stay matched and every CTA returns in bounded time.
 #include <cudaTypedefs.h>
 
 #include <array>
@@ -473,21 +473,6 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
       }
     }
 
-    __syncwarp();
-    tc_fence_before();
-    csk_cluster_sync();   // every CTA's partial tile is in its shared memory
-    tc_fence_after();
-
-    if (*vabort == 0) {
-      // -------------------------------------------------------------- reduction + epilogue
-      // All twelve warps take part (the producer and MMA warps are idle by now); the partials
-      // come from shared memory, not TMEM, so any warp may take any columns.
-      void* bits = it + 1 == P.iters ? P.bits_last : nullptr;
-      csk_epilogue<BN, MODE>(a, P.xop[w ^ 1], bits, reinterpret_cast<const float*>(tiles),
-                             P.ws + ((size_t)tile * S * H + h) * BN * TC_BM, (int64_t)H * BN * TC_BM, sp_me, S, mb,
-                             (int64_t)n_tile * BN, c_begin, c_end, warp, lane);
-      if (it + 1 < P.iters) fence_stores_for_tma();
-    }
     // Stop together: a CTA that must stop ORs its vote into the vote word of this parity in every
     // CTA of the cluster before the barrier below, so that after it every CTA reads the same
     // decision from its own word (rewritten two iterations later, after two more cluster
@@ -500,21 +485,30 @@ __global__ void __launch_bounds__(CSK_THREADS, 1) k_tc_csk(const __grid_constant
 
     __syncwarp();
     tc_fence_before();
-    csk_cluster_sync();   // every read of every CTA's partial is done; the votes are in
+    csk_cluster_sync();   // every CTA's partial tile is out; the votes are in
     tc_fence_after();
-
-    if (it + 1 == P.iters) break;
     if (threadIdx.x == 0) {
       volatile int* vote = stop_vote + (it & 1);
-      const int stop = *vote;
+      *stop_all = *vote;
       *vote = 0;   // ready for iteration it + 2
-      *stop_all = stop;
-      // this CTA's part of x^{it+1} is written: every thread fenced its stores before the cluster
-      // barrier, which orders them before this release
-      if (!stop) red_release_gpu_add(P.gbar, 1u);
     }
     __syncthreads();
-    if (*stop_all) break;
+    if (*stop_all) break;   // every CTA of the cluster leaves here, before any later cluster barrier
+
+    // ---------------------------------------------------------------- reduction + epilogue
+    // All twelve warps take part (the producer and MMA warps are idle by now); the partials come
+    // from shared memory and L2, not TMEM, so any warp may take any columns.  No CTA reads
+    // another's shared memory from here on: the next cluster barrier is the next iteration's.
+    void* bits = it + 1 == P.iters ? P.bits_last : nullptr;
+    csk_epilogue<BN, MODE>(a, P.xop[w ^ 1], bits, reinterpret_cast<const float*>(tiles),
+                           P.ws + ((size_t)tile * S * H + h) * BN * TC_BM, (int64_t)H * BN * TC_BM, sp_me, S, mb,
+                           (int64_t)n_tile * BN, c_begin, c_end, warp, lane);
+    if (it + 1 == P.iters) break;
+    fence_stores_for_tma();
+    // this CTA's part of x^{it+1} is written: every thread fenced its stores before this barrier,
+    // which orders them before thread 0's release; its own shared-memory partials are read
+    __syncthreads();
+    if (threadIdx.x == 0) red_release_gpu_add(P.gbar, 1u);
   }
 
   if (multi) {
